@@ -1,0 +1,203 @@
+"""FP64 CPU oracle of the GiLA k-hop Fruchterman-Reingold step.
+
+TEST INFRASTRUCTURE ONLY. This package restates, in plain C (gila_oracle.c,
+FP64, OpenMP over vertices with a fixed per-vertex summation order), what
+the paper defines: the k-neighbourhoods of Section 4.5, the forces of
+Section 3.1 and the synchronous capped move of Sections 3.1 and 4.5. It is
+used by the tests, the smoke check and the benchmark's CPU-baseline leg, and
+by nothing else; it shares no code with the CUDA library.
+
+Functions take graphs as (n, row_ptr int64[n+1], col_idx int32[nnz]) and
+placements as float64[n, 2].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gila_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SCHED_LINEAR = 0
+SCHED_GEOM = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile gila_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP,
+    strict IEEE: no fast-math, no FMA contraction)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        I64 = ctypes.c_int64
+        I = ctypes.c_int
+        D = ctypes.c_double
+        lib.oracle_threads.restype = I
+        lib.oracle_set_threads.argtypes = [I]
+        lib.oracle_khop_count.restype = I64
+        lib.oracle_khop_count.argtypes = [I64, P, P, I, P]
+        lib.oracle_khop_fill.restype = I
+        lib.oracle_khop_fill.argtypes = [I64, P, P, I, P, P]
+        lib.oracle_khop_rows.restype = I64
+        lib.oracle_khop_rows.argtypes = [I64, P, P, I, I64, P, P, P, I64]
+        lib.oracle_forces.argtypes = [I64, P, P, P, P, P, D, I, I, I64, P, P]
+        lib.oracle_step.argtypes = [I64, P, P, P, P, P, D, I, I, D, P, P]
+        lib.oracle_temperature.restype = D
+        lib.oracle_temperature.argtypes = [I, D, I, I]
+        lib.oracle_default_t0.restype = D
+        lib.oracle_default_t0.argtypes = [I, I64, D, P]
+        lib.oracle_run.restype = I
+        lib.oracle_run.argtypes = [I64, P, P, P, P, P, D, I, I, I, D, I, P]
+        lib.oracle_metrics.argtypes = [I64, P, P, P, P, P, D, I, I, P]
+        _lib = lib
+        return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _csr(n, row_ptr, col_idx):
+    row = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col_idx, dtype=np.int32)
+    assert row.shape[0] == n + 1
+    return row, col
+
+
+def _pos(pos, n):
+    p = np.ascontiguousarray(pos, dtype=np.float64).reshape(n, 2)
+    return p
+
+
+def threads() -> int:
+    return _load().oracle_threads()
+
+
+def set_threads(t: int) -> None:
+    _load().oracle_set_threads(int(t))
+
+
+def khop(n, row_ptr, col_idx, k):
+    """k-hop lists N_v(k) (Section 4.5): (krow int64[n+1], kcol int32[nnz]),
+    rows ascending, v excluded."""
+    lib = _load()
+    row, col = _csr(n, row_ptr, col_idx)
+    counts = np.zeros(max(n, 1), dtype=np.int64)
+    lib.oracle_khop_count(n, _p(row), _p(col), int(k), _p(counts))
+    krow = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts[:n], out=krow[1:])
+    kcol = np.zeros(max(int(krow[-1]), 1), dtype=np.int32)
+    rc = lib.oracle_khop_fill(n, _p(row), _p(col), int(k), _p(krow), _p(kcol))
+    if rc != 0:
+        raise RuntimeError("oracle_khop_fill: inconsistent row lengths")
+    return krow, kcol[: int(krow[-1])]
+
+
+def khop_rows(n, row_ptr, col_idx, k, sources):
+    """N_v(k) for the listed sources only: (counts int64[s], concatenated
+    sorted rows int32[sum counts])."""
+    lib = _load()
+    row, col = _csr(n, row_ptr, col_idx)
+    src = np.ascontiguousarray(sources, dtype=np.int64)
+    counts = np.zeros(max(src.shape[0], 1), dtype=np.int64)
+    total = lib.oracle_khop_rows(n, _p(row), _p(col), int(k), src.shape[0], _p(src),
+                                 _p(counts), None, 0)
+    out = np.zeros(max(total, 1), dtype=np.int32)
+    got = lib.oracle_khop_rows(n, _p(row), _p(col), int(k), src.shape[0], _p(src),
+                               _p(counts), _p(out), total)
+    if got != total:
+        raise RuntimeError("oracle_khop_rows: size mismatch")
+    return counts[: src.shape[0]], out[:total]
+
+
+def forces(n, row_ptr, col_idx, krow, kcol, pos, d=1.0, p=2, q=1, sel=None):
+    """Resultant force F(u) (Section 3.1 over N_u(k)) for all u, or for the
+    vertices in sel: float64[len, 2]."""
+    lib = _load()
+    row, col = _csr(n, row_ptr, col_idx)
+    kr, kc = _csr(n, krow, kcol)
+    P = _pos(pos, n)
+    if sel is None:
+        F = np.zeros((n, 2), dtype=np.float64)
+        lib.oracle_forces(n, _p(row), _p(col), _p(kr), _p(kc), _p(P), float(d), int(p), int(q),
+                          0, None, _p(F))
+    else:
+        s = np.ascontiguousarray(sel, dtype=np.int64)
+        F = np.zeros((s.shape[0], 2), dtype=np.float64)
+        lib.oracle_forces(n, _p(row), _p(col), _p(kr), _p(kc), _p(P), float(d), int(p), int(q),
+                          s.shape[0], _p(s), _p(F))
+    return F
+
+
+def step(n, row_ptr, col_idx, krow, kcol, pos, t, d=1.0, p=2, q=1):
+    """One synchronous capped iteration: (new positions, displacements)."""
+    lib = _load()
+    row, col = _csr(n, row_ptr, col_idx)
+    kr, kc = _csr(n, krow, kcol)
+    P = _pos(pos, n)
+    out = np.zeros((n, 2), dtype=np.float64)
+    disp = np.zeros((n, 2), dtype=np.float64)
+    lib.oracle_step(n, _p(row), _p(col), _p(kr), _p(kc), _p(P), float(d), int(p), int(q),
+                    float(t), _p(out), _p(disp))
+    return out, disp
+
+
+def temperature(schedule, t0, i, iters) -> float:
+    return _load().oracle_temperature(int(schedule), float(t0), int(i), int(iters))
+
+
+def default_t0(schedule, n, d, pos) -> float:
+    P = _pos(pos, n)
+    return _load().oracle_default_t0(int(schedule), n, float(d), _p(P))
+
+
+def run(n, row_ptr, col_idx, krow, kcol, pos0, iters, d=1.0, p=2, q=1,
+        schedule=SCHED_LINEAR, t0=0.0):
+    """`iters` iterations from pos0; returns the final float64[n, 2]."""
+    lib = _load()
+    row, col = _csr(n, row_ptr, col_idx)
+    kr, kc = _csr(n, krow, kcol)
+    P = _pos(pos0, n)
+    out = np.zeros((n, 2), dtype=np.float64)
+    rc = lib.oracle_run(n, _p(row), _p(col), _p(kr), _p(kc), _p(P), float(d), int(p), int(q),
+                        int(schedule), float(t0), int(iters), _p(out))
+    if rc != 0:
+        raise MemoryError("oracle_run")
+    return out
+
+
+def metrics(n, row_ptr, col_idx, krow, kcol, pos, d=1.0, p=2, q=1) -> dict:
+    """Edge-length mean/std/CV and the repulsive/attractive totals and ratio."""
+    lib = _load()
+    row, col = _csr(n, row_ptr, col_idx)
+    kr, kc = _csr(n, krow, kcol)
+    P = _pos(pos, n)
+    out = np.zeros(6, dtype=np.float64)
+    lib.oracle_metrics(n, _p(row), _p(col), _p(kr), _p(kc), _p(P), float(d), int(p), int(q),
+                       _p(out))
+    return {"edge_mean": out[0], "edge_std": out[1], "edge_cv": out[2],
+            "rep_total": out[3], "att_total": out[4], "rep_att_ratio": out[5]}
