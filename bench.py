@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the GiLA k-hop Fruchterman-Reingold layout on GB300.
+
+One step = one whole layout of the workload graph with its placement
+resident in HBM: rebuild the k-hop lists N_v(k) (the lists are dropped
+before every step), run every FR iteration, then take the FP64 quality
+reductions of the result. `value` is pair interactions per second over the
+timed steps, P = nnz(N(k)) + nnz(A) directed pairs per iteration (each
+k-hop pair gives a repulsion, each edge also an attraction).
+
+Default workload: Barabasi-Albert graph, n = 100,000, m = 3 (299,994 edges),
+k = 3, 500 iterations, linear cooling from 0.1 sqrt(n), d = 1, FP32,
+placement uniform in [0, sqrt n]^2 (seed 2). The k-hop lists (about 0.96 GB)
+are larger than L2, so no explicit flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gila|reference]
+Under torchrun each rank lays out its own copy of the workload (replicas).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "ba100k_k3": dict(graph="ba100k", k=3, iters=500, precision="fp32",
+                      desc="Barabasi-Albert n=100000 m=3 (299,994 edges), k=3, 500 iterations, "
+                           "linear cooling from 0.1*sqrt(n), d=1, FP32"),
+    "ba100k_k2": dict(graph="ba100k", k=2, iters=500, precision="fp32",
+                      desc="Barabasi-Albert n=100000 m=3 (299,994 edges), k=2, 500 iterations, "
+                           "linear cooling from 0.1*sqrt(n), d=1, FP32"),
+    "grid32": dict(graph="grid32", k=2, iters=100, precision="fp64",
+                   desc="32x32 grid, k=2, 100 iterations, linear cooling from 3.2, d=1, FP64"),
+    "mesh1000_k3": dict(graph="mesh1000", k=3, iters=300, precision="fp32c",
+                        desc="1000x1000 triangulated mesh, k=3, 300 iterations, FP32 compensated"),
+}
+PREC = {"fp32": 0, "fp64": 1, "fp32c": 2}
+DTYPE_NAME = {"fp32": "f32", "fp64": "f64", "fp32c": "f32"}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        try:
+            os.unlink(self.file.name)
+        except OSError:
+            pass
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reference_arm(args, wl, ws, rank):
+    """The oracle, as it stands, on the host cores: each step is one FP64 FR
+    iteration over the whole workload graph plus 1/iters of the oracle's
+    k-hop build (timed once), i.e. the per-iteration share of one layout."""
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_1606_02162_gb300 import inputs as I
+    g, pos = I.workload(wl["graph"])
+    k, iters = wl["k"], wl["iters"]
+    t = time.perf_counter()
+    krow, kcol = O.khop(g.n, g.row_ptr, g.col_idx, k)
+    t_build = time.perf_counter() - t
+    P = int(krow[-1]) + g.nnz
+    t0 = 0.1 * math.sqrt(g.n)
+    cur = pos
+    for i in range(args.warmup):
+        cur, _ = O.step(g.n, g.row_ptr, g.col_idx, krow, kcol, cur, O.temperature(0, t0, i, iters))
+    times = []
+    for i in range(args.steps):
+        t = time.perf_counter()
+        cur, _ = O.step(g.n, g.row_ptr, g.col_idx, krow, kcol, cur,
+                        O.temperature(0, t0, args.warmup + i, iters))
+        times.append(time.perf_counter() - t)
+    t_step = sum(times) / len(times) + t_build / iters
+    value = P / t_step
+    cores = O.threads()
+    line = {
+        "impl": "reference", "metric": "pair-interactions/s", "value": value, "unit": "pairs/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "n": g.n, "edges": g.num_edges, "k": k,
+                   "pairs_per_iter": P},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                         "sample": f"FP64 C oracle, one FR iteration over the whole graph per "
+                                   f"step plus 1/{iters} of its k-hop build ({t_build:.2f} s)"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(wl, g, pos, budget_s=20.0):
+    """The FP64 oracle on the host cores on a bounded sample of the workload:
+    its own k-hop build plus as many whole-graph iterations as fit in about
+    budget_s seconds, scaled to one whole layout (build + all iterations)."""
+    import oracle as O
+    k, iters = wl["k"], wl["iters"]
+    t = time.perf_counter()
+    krow, kcol = O.khop(g.n, g.row_ptr, g.col_idx, k)
+    t_build = time.perf_counter() - t
+    P = int(krow[-1]) + g.nnz
+    t0 = 0.1 * math.sqrt(g.n)
+    cur = pos
+    done, t_it = 0, 0.0
+    while done < iters and (done < 2 or t_build + t_it < budget_s):
+        t = time.perf_counter()
+        cur, _ = O.step(g.n, g.row_ptr, g.col_idx, krow, kcol, cur,
+                        O.temperature(0, t0, done, iters))
+        t_it += time.perf_counter() - t
+        done += 1
+    t_layout = t_build + t_it / done * iters
+    return {"value": P * iters / t_layout, "unit": "pairs/s", "cores": O.threads(),
+            "kind": "oracle",
+            "sample": f"FP64 C oracle: k-hop build ({t_build:.2f} s) + {done} of {iters} "
+                      f"iterations ({t_it:.2f} s), scaled to one whole layout"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gila", choices=["gila", "reference"])
+    ap.add_argument("--workload", default="ba100k_k3", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        return reference_arm(args, wl, ws, rank)
+
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1606_02162_gb300 import gila as G
+    from paper_1606_02162_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    g, pos0 = I.workload(wl["graph"])
+    prec = PREC[wl["precision"]]
+    k, iters = wl["k"], wl["iters"]
+    prm = G.params(k=k, iters=iters, precision=prec)
+    dt = torch.float64 if prec == G.GILA_FP64 else torch.float32
+    stream = torch.cuda.current_stream()
+
+    # ------------------------------------------------ device-resident steps
+    h = G.Graph.from_inputs(g)
+    pos_init = torch.tensor(pos0, dtype=dt, device="cuda")
+    pos = torch.empty_like(pos_init)
+
+    def step():
+        G.gila_khop_reset(h.handle)
+        G.gila_build_khop(h.handle, k)
+        pos.copy_(pos_init)
+        G.gila_layout_run_device(h.handle, prm, pos)
+        return G.gila_layout_metrics(h.handle, prm, pos)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    nnzk = G.gila_graph_info(h.handle)["nnz_khop"]
+    P = nnzk + g.nnz
+    G.gila_profile_read(h.handle)  # clear
+    G.gila_profile_enable(h.handle, True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = G.gila_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    last = None
+    for _ in range(args.steps):
+        last = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = G.gila_kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = G.gila_profile_read(h.handle)
+    G.gila_profile_enable(h.handle, False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = P * iters * args.steps * ws / (ms / 1e3)
+    iter_ms = prof["iter_ms"] / max(prof["iter_launches"], 1)
+    build_ms = prof["build_ms"] / max(prof["builds"], 1)
+    h.close()
+
+    # roofline of the iteration kernel: 12 B per directed pair (4 B id +
+    # 8 B float2 position) plus 8 B row offset, 8 B own position read and
+    # 8 B position write per vertex
+    elem = 16 if prec == G.GILA_FP64 else 8
+    alg_bytes = (4 + elem) * P + 8 * (g.n + 1) + 2 * elem * g.n
+    hbm, peak_kind = peaks()
+    achieved = alg_bytes / (iter_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None,
+                "kernel": "iteration_kernel", "peak_source": peak_kind,
+                "alg_bytes_per_launch": alg_bytes}
+
+    # ------------------------------------------------ end to end (host buffers)
+    e2e = None
+    if not args.no_e2e:
+        row = torch.from_numpy(g.row_ptr).pin_memory().numpy()
+        col = torch.from_numpy(g.col_idx).pin_memory().numpy()
+        pin_in = torch.from_numpy(np.ascontiguousarray(pos0)).pin_memory().numpy()
+        pin_out = torch.empty(pin_in.shape, dtype=torch.float64).pin_memory().numpy()
+
+        def e2e_step():
+            hh = G.Graph(g.n, row, col)
+            try:
+                G.gila_layout_run(hh.handle, prm, pin_in, pin_out)
+            finally:
+                hh.close()
+
+        e2e_step()
+        barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = time.perf_counter() - t
+        if dist is not None:
+            tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": P * iters * args.steps * ws / e2e_s, "unit": "pairs/s",
+               "h2d_bytes_per_step": int(row.nbytes + col.nbytes + pin_in.nbytes),
+               "d2h_bytes_per_step": int(pin_out.nbytes),
+               "ms_per_step": e2e_s / args.steps * 1e3}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, g, pos0)
+
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "pair-interactions/s", "value": value, "unit": "pairs/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE_NAME[wl["precision"]], "data": "synthetic",
+        "config": {"workload": wl["desc"], "n": g.n, "edges": g.num_edges, "k": k,
+                   "iters": iters, "nnz_khop": nnzk, "pairs_per_iter": P,
+                   "ms_per_iter": iter_ms, "khop_build_ms": build_ms,
+                   "layouts_per_s": ws * args.steps / (ms / 1e3),
+                   "l2": "inputs larger than L2 (k-hop lists %.2f GB)" % (4 * nnzk / 1e9),
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "quality_last": {"edge_cv": last["edge_cv"],
+                                    "rep_att_ratio": last["rep_att_ratio"]} if last else None},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

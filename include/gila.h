@@ -1,0 +1,197 @@
+/*
+ * gila.h -- C ABI of the GiLA k-hop Fruchterman-Reingold layout library
+ * (single GB300 GPU, sm_103a).
+ *
+ * The method (Arleo, Didimo, Liotta, Montecchiani, "A Distributed
+ * Force-Directed Algorithm on Giraph", arXiv 1606.02162):
+ *   - Section 3.1: each vertex u feels F(u) = sum over edges (u,v) of an
+ *     attraction of length delta^p / d toward v, plus a repulsion of length
+ *     d^2 / delta^q away from every repelling vertex v (delta = |x_u - x_v|,
+ *     d = ideal edge length, p = 2 and q = 1 in Fruchterman-Reingold). The
+ *     move of u is F(u) cut to the temperature t, which falls per iteration.
+ *   - Section 4.5: the repelling set of v is its k-neighbourhood N_v(k),
+ *     the vertices at graph distance 1..k; all vertices move together once
+ *     every force is known.
+ *   - Section 5.1: the geometric cooling t_h = sqrt(n d / a) 0.93^h.
+ *
+ * Conventions for every call:
+ *   - Every call returns a gila_status; nothing throws across the ABI. On
+ *     failure gila_last_error() returns a message (thread-local, valid until
+ *     the next failing call on the same thread).
+ *   - Host arrays belong to the caller; the library copies what it keeps.
+ *     Device buffers created by the library belong to the graph and are
+ *     freed by gila_graph_destroy. Pointers named *_dev are device
+ *     pointers owned by the caller (e.g. a torch tensor's data_ptr()).
+ *   - A graph is bound to the CUDA device current at creation and issues
+ *     its work on the stream set by gila_graph_set_stream (default: the
+ *     legacy default stream). Calls on one graph must not run concurrently.
+ *   - Placements are arrays of n (x, y) pairs, row-major: element 2u is x_u,
+ *     2u+1 is y_u. Host placements are always double. Device placements are
+ *     float2 in GILA_FP32 / GILA_FP32_COMPENSATED and double2 in GILA_FP64.
+ */
+#ifndef GILA_H
+#define GILA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gila_status {
+    GILA_OK = 0,
+    GILA_EINVAL = 1,    /* bad argument or malformed graph */
+    GILA_ENOMEM = 2,    /* device or host allocation failed */
+    GILA_EBUDGET = 3,   /* admission refused: over the memory budget */
+    GILA_ETIMEDOUT = 4, /* a bounded wait ran out */
+    GILA_ECUDA = 5,     /* CUDA runtime or launch error */
+    GILA_EBUSY = 6,     /* object still in use */
+    GILA_ESTATE = 7     /* call out of order */
+} gila_status;
+
+/* Arithmetic of the force step. */
+enum {
+    GILA_FP32 = 0,             /* float positions and force sums */
+    GILA_FP64 = 1,             /* double everywhere (validation mode) */
+    GILA_FP32_COMPENSATED = 2  /* float, with compensated (two-sum) force sums */
+};
+
+/* Cooling schedules: temperature of iteration i of `iters` (0-based). */
+enum {
+    GILA_COOL_LINEAR = 0,   /* t_i = t0 (iters - i) / iters; default t0 = 0.1 sqrt(n) */
+    GILA_COOL_GEOMETRIC = 1 /* t_i = t0 0.93^i; default t0 = sqrt(n d / a), Section 5.1,
+                               a = height / width of the initial bounding box */
+};
+
+/* gila_graph_create flags. */
+enum {
+    GILA_GRAPH_VALIDATE = 1, /* check the CSR is simple and symmetric (else GILA_EINVAL) */
+    GILA_GRAPH_SIMPLIFY = 2  /* symmetrise, drop self-loops and repeats before upload */
+};
+
+typedef struct gila_params {
+    int32_t k;         /* radius of the repelling set N_v(k), 1 <= k <= 64 (Section 4.5) */
+    int32_t iters;     /* iterations run by gila_layout_run*, >= 0 */
+    double d;          /* ideal edge length, > 0 (Section 3.1) */
+    double t0;         /* initial temperature; <= 0 selects the schedule's default */
+    int32_t schedule;  /* GILA_COOL_* */
+    int32_t p;         /* attraction exponent, 0..8 (2 = Fruchterman-Reingold) */
+    int32_t q;         /* repulsion exponent, 0..8 (1 = Fruchterman-Reingold) */
+    int32_t precision; /* GILA_FP32 | GILA_FP64 | GILA_FP32_COMPENSATED */
+} gila_params;
+
+/* Layout quality figures of a placement, all accumulated in FP64. */
+typedef struct gila_metrics {
+    double edge_mean;     /* mean edge length over the undirected edges */
+    double edge_std;      /* population standard deviation of edge lengths */
+    double edge_cv;       /* edge_std / edge_mean */
+    double rep_total;     /* sum over unordered k-hop pairs of d^2 / delta^q */
+    double att_total;     /* sum over undirected edges of delta^p / d */
+    double rep_att_ratio; /* rep_total / att_total */
+} gila_metrics;
+
+typedef struct gila_graph gila_graph;
+
+/* Fills *p with k = 2, iters = 300, d = 1, t0 = 0 (default), linear
+ * cooling, p = 2, q = 1, GILA_FP32. */
+void gila_params_default(gila_params* p);
+
+/* Host-only check that (row_ptr, col_idx) is a simple undirected graph in
+ * symmetric CSR form (Table 1 of the paper: no self-loops, no parallel
+ * edges): row_ptr[0] = 0, non-decreasing, ids in [0, n), no self-loop, no
+ * repeat within a row, and u in row v whenever v in row u. Returns GILA_OK
+ * or GILA_EINVAL with the first violation in gila_last_error(). Touches no
+ * GPU. */
+gila_status gila_csr_validate(int64_t n, const int64_t* row_ptr, const int32_t* col_idx);
+
+/* Upload a graph. n vertices (0 <= n < 2^31); row_ptr int64[n+1] and
+ * col_idx int32[row_ptr[n]] are host arrays in symmetric CSR form (each
+ * undirected edge stored in both rows). flags: GILA_GRAPH_VALIDATE rejects a
+ * malformed CSR with GILA_EINVAL; GILA_GRAPH_SIMPLIFY repairs it instead.
+ * Without either flag the CSR is trusted. On success *out owns device
+ * copies of the arrays. */
+gila_status gila_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                              int32_t flags, gila_graph** out);
+
+/* Free the graph and every device buffer it owns. NULL is ignored. */
+void gila_graph_destroy(gila_graph* g);
+
+/* Issue all later work of g on this cudaStream_t (NULL = legacy default
+ * stream). The stream stays owned by the caller. */
+gila_status gila_graph_set_stream(gila_graph* g, void* cuda_stream);
+
+/* Sizes: vertices, stored adjacency entries (2E), the k of the built
+ * k-hop lists (0 if none) and their total length. Any pointer may be NULL. */
+gila_status gila_graph_info(const gila_graph* g, int64_t* n, int64_t* nnz_adj,
+                            int32_t* k_built, int64_t* nnz_khop);
+
+/* Build the k-hop lists N_v(k) of every vertex (Section 4.5) on the GPU:
+ * breadth-first expansion to depth k, deduplicated, each list sorted by
+ * ascending id, v itself excluded. Idempotent for the same k (a second call
+ * returns at once); a different k rebuilds. *nnz_out (may be NULL) receives
+ * the total list length. Synchronises the graph's stream. */
+gila_status gila_build_khop(gila_graph* g, int32_t k, int64_t* nnz_out);
+
+/* Drop the cached k-hop lists so the next build recomputes them (buffers
+ * are kept for reuse). */
+gila_status gila_khop_reset(gila_graph* g);
+
+/* Copy the built lists to host arrays: krow int64[n+1] (offsets) and kcol
+ * int32[nnz_khop] (ids, ascending per row). GILA_ESTATE if none are built. */
+gila_status gila_khop_export(const gila_graph* g, int64_t* krow_host, int32_t* kcol_host);
+
+/* One synchronous iteration at temperature t (Sections 3.1, 4.5): every
+ * F(u) is formed from pos_in_dev, then pos_out_dev[u] = pos_in_dev[u] +
+ * F(u) min(1, t / |F(u)|). Builds the k-hop lists for prm->k first when
+ * needed. pos_in_dev and pos_out_dev are caller device arrays of n
+ * float2 (FP32 modes) or double2 (GILA_FP64) and must not overlap.
+ * disp_out_dev (may be NULL) receives the moves, same type. Asynchronous
+ * on the graph's stream. */
+gila_status gila_layout_step(gila_graph* g, const gila_params* prm, double t,
+                             const void* pos_in_dev, void* pos_out_dev, void* disp_out_dev);
+
+/* prm->iters iterations on a device-resident placement (float2 or double2
+ * per prm->precision), under prm->schedule. Builds the k-hop lists first
+ * when needed. The result is left in pos_dev_inout. Asynchronous on the
+ * graph's stream apart from the k-hop build. */
+gila_status gila_layout_run_device(gila_graph* g, const gila_params* prm, void* pos_dev_inout);
+
+/* Whole layout from and to host memory: uploads pos_in_host (double[2n];
+ * FP32 modes round once on the device), builds the k-hop lists when needed,
+ * runs prm->iters iterations and writes the final placement to
+ * pos_out_host (double[2n]; may equal pos_in_host). Returns after the
+ * result is on the host. */
+gila_status gila_layout_run(gila_graph* g, const gila_params* prm,
+                            const double* pos_in_host, double* pos_out_host);
+
+/* Quality figures of a device placement (float2 or double2 per
+ * prm->precision) with the k-hop lists of prm->k, in FP64 with a fixed
+ * reduction order. Synchronises the graph's stream. */
+gila_status gila_layout_metrics(gila_graph* g, const gila_params* prm, const void* pos_dev,
+                                gila_metrics* out);
+
+/* Temperature of iteration i under prm (t0 = resolved initial temperature). */
+double gila_temperature(const gila_params* prm, double t0, int32_t i);
+
+/* Per-graph timing by CUDA events recorded on the graph's stream while
+ * enabled (on = 1): k-hop builds (count, ms) and iteration kernels
+ * (launches, ms of the launch sequence). gila_profile_read returns the
+ * totals since the previous read, then clears them; it waits for the last
+ * recorded event. */
+gila_status gila_profile_enable(gila_graph* g, int32_t on);
+gila_status gila_profile_read(gila_graph* g, int64_t* builds, double* build_ms,
+                              int64_t* iter_launches, double* iter_ms);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* gila_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * graphs, all threads), for accounting of device work. */
+int64_t gila_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GILA_H */

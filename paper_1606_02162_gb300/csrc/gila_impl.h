@@ -1,0 +1,145 @@
+// Internal declarations shared by the translation units of libgila.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gila.h"
+
+namespace gila {
+
+// ---------------------------------------------------------------- errors
+
+void set_error(const std::string& msg);
+gila_status fail(gila_status s, const std::string& msg);
+gila_status cuda_fail(cudaError_t e, const char* what);
+
+#define GILA_CUDA(call)                                          \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return ::gila::cuda_fail(e_, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------- k-hop flag
+
+// The top bit of a stored k-hop entry marks an edge of G (distance 1):
+// A is contained in N_v(k) for every k >= 1, so the attraction terms ride
+// in the same stream as the repulsion terms.
+constexpr uint32_t kEdgeFlag = 0x80000000u;
+constexpr uint32_t kIdMask = 0x7fffffffu;
+
+// ---------------------------------------------------------------- binning
+
+// Row-length classes of the iteration kernel.
+//   class 0: len <= kSmallMax, kGroupSmall lanes per vertex
+//   class 1: len <= kWarpMax, one warp per vertex
+//   class 2: len <= kBlockMax, one block per vertex
+//   class 3: longer, split into chunks of kChunk entries, one block each,
+//            summed in chunk order by the last block to finish
+struct BinConfig {
+    int small_max = 32;
+    int group_small = 8;
+    int warp_max = 8192;
+    int block_max = 65536;
+    int chunk = 32768;
+};
+
+struct Chunk {
+    int64_t begin;   // first entry (absolute index into kcol)
+    int64_t end;     // one past the last entry
+    int32_t vertex;  // owner
+    int32_t giant;   // index of the owner in the giant list
+    int32_t first;   // index of the owner's first chunk
+    int32_t count;   // number of chunks of the owner
+};
+
+// Scratch that a single k-hop build needs (reused across builds).
+struct KhopScratch {
+    int64_t* counts = nullptr;  // n
+    int32_t* queue = nullptr;   // n: sources whose ball overflowed tier 1
+    int* qn = nullptr;          // 1
+    uint32_t* bitmaps = nullptr;
+    int32_t* lists = nullptr;
+    int64_t bitmap_words = 0;   // per block
+    int t2_blocks = 0;
+    size_t cap_n = 0;
+};
+
+struct Bins {
+    int32_t* lists = nullptr;   // all classes back to back: class 0, 1, 2
+    int32_t n0 = 0, n1 = 0, n2 = 0;
+    Chunk* chunks = nullptr;
+    int32_t nchunks = 0;
+    int32_t ngiant = 0;
+    int32_t* giant_counter = nullptr;  // ngiant, zero between launches
+    void* partials = nullptr;          // nchunks x 4 doubles
+    size_t cap_lists = 0, cap_chunks = 0, cap_giant = 0;
+    BinConfig cfg;
+};
+
+struct ProfileRec {
+    cudaEvent_t a, b;
+    int kind;  // 0 build, 1 iterations
+    int64_t launches;
+};
+
+}  // namespace gila
+
+struct gila_graph {
+    int64_t n = 0;
+    int64_t nnz_adj = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t* row = nullptr;
+    int32_t* col = nullptr;
+    // k-hop lists
+    int32_t k_built = 0;
+    int64_t nnz_khop = 0;
+    int64_t* krow = nullptr;
+    uint32_t* kcol = nullptr;
+    size_t cap_kcol = 0;
+    gila::KhopScratch ks;
+    gila::Bins bins;
+    // placement buffers for the run calls
+    void* pos[2] = {nullptr, nullptr};
+    size_t pos_cap[2] = {0, 0};
+    double* stage = nullptr;  // double[2n] upload/download staging
+    size_t stage_cap = 0;
+    // FP64 reduction scratch
+    double* red = nullptr;
+    size_t red_cap = 0;
+    // profiling
+    bool prof_on = false;
+    std::vector<gila::ProfileRec> prof;
+    int64_t prof_builds = 0, prof_launches = 0;
+    double prof_build_ms = 0.0, prof_iter_ms = 0.0;
+};
+
+namespace gila {
+
+// k-hop build (khop.cu)
+gila_status build_khop(gila_graph* g, int k);
+void free_khop(gila_graph* g);
+
+// iteration + metrics (layout.cu)
+gila_status launch_iteration(gila_graph* g, const gila_params* prm, double t,
+                             const void* pos_in, void* pos_out, void* disp_out);
+gila_status compute_metrics(gila_graph* g, const gila_params* prm, const void* pos,
+                            gila_metrics* out);
+gila_status bbox_aspect(gila_graph* g, int precision, const void* pos, double* aspect);
+gila_status convert_positions(gila_graph* g, int precision, const double* src, void* dst,
+                              bool to_device_type);
+void free_layout(gila_graph* g);
+
+// memory helper: grow a device buffer to at least `bytes`
+gila_status ensure(void** p, size_t* cap, size_t bytes);
+
+int sm_count(int device);
+
+// Count one kernel launch issued by the library (all launch sites call it).
+void count_launch();
+
+}  // namespace gila

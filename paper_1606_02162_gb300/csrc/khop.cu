@@ -1,0 +1,679 @@
+// k-hop list build (Section 4.5 of the paper: the repelling set of v is
+// N_v(k), the vertices at graph distance 1..k from v).
+//
+// The paper rebuilds these sets every iteration by TTL-limited flooding of
+// messages through Giraph supersteps. The topology never changes during a
+// layout, so here they are built once, on the GPU, as a CSR of sorted ids:
+//
+//   tier 1  one warp per source: breadth-first expansion level by level,
+//           with a shared-memory open-addressing set for de-duplication
+//           and warp-aggregated appends; balls of up to kT1Cap vertices.
+//   tier 2  one block per remaining source: the same expansion with a
+//           global-memory bitmap per block; the sorted row comes out of a
+//           scan over the bitmap.
+//   Both tiers run twice (count, then fill) around an exclusive scan of
+//   the counts, so the output needs no atomics and is the same every run.
+//   Afterwards the entries that are edges of G get the top-bit flag used by
+//   the force kernel, and rows are classed by length for scheduling.
+#include <algorithm>
+#include <climits>
+#include <vector>
+
+#include "device_util.cuh"
+#include "gila_impl.h"
+
+namespace gila {
+
+namespace {
+
+constexpr int kT1Cap = 512;          // ball size limit of tier 1 (source included)
+constexpr int kT1HashBits = 10;
+constexpr int kT1Hash = 1 << kT1HashBits;  // open-addressing slots
+constexpr int kT1Warps = 8;          // warps per block
+constexpr int kT2Threads = 256;
+
+struct T1Smem {
+    int32_t table[kT1Hash];
+    int32_t list[kT1Cap];
+};
+
+__device__ __forceinline__ unsigned t1_hash(unsigned x)
+{
+    return (x * 2654435761u) >> (32 - kT1HashBits);
+}
+
+// Insert x; true if it was not present. The table holds at most
+// kT1Cap + 31 < kT1Hash keys, so a free slot always exists.
+__device__ __forceinline__ bool t1_insert(int32_t* table, int32_t x)
+{
+    unsigned h = t1_hash((unsigned)x);
+    for (int probe = 0; probe < kT1Hash; ++probe) {
+        int old = atomicCAS(&table[h], -1, x);
+        if (old == -1) return true;
+        if (old == x) return false;
+        h = (h + 1) & (kT1Hash - 1);
+    }
+    return false;
+}
+
+// Ball of radius k around src in warp-private shared memory. Returns its
+// size (src included), or -1 once it exceeds kT1Cap. Warp-uniform result.
+__device__ int t1_ball(const int64_t* __restrict__ row, const int32_t* __restrict__ col, int k,
+                       int32_t src, T1Smem& S, int lane)
+{
+    for (int i = lane; i < kT1Hash; i += 32) S.table[i] = -1;
+    __syncwarp();
+    if (lane == 0) {
+        S.table[t1_hash((unsigned)src)] = src;
+        S.list[0] = src;
+    }
+    __syncwarp();
+    int cnt = 1, lb = 0, le = 1;
+    const unsigned lt = lanemask_lt();
+    for (int depth = 1; depth <= k && lb < le; ++depth) {
+        for (int fb = lb; fb < le; fb += 32) {
+            const int f = fb + lane;
+            int64_t start = 0;
+            int deg = 0;
+            if (f < le) {
+                const int32_t w = S.list[f];
+                start = row[w];
+                deg = (int)(row[w + 1] - start);
+            }
+            const int incl = warp_inclusive_scan(deg, lane);
+            const int total = __shfl_sync(kFull, incl, 31);
+            const int excl = incl - deg;
+            for (int base = 0; base < total; base += 32) {
+                const int e = base + lane;
+                // owner lane: the number of lanes whose inclusive prefix is <= e
+                int j = 0;
+#pragma unroll
+                for (int s = 16; s >= 1; s >>= 1) {
+                    int v = __shfl_sync(kFull, incl, j + s - 1);
+                    if (v <= e) j += s;
+                }
+                const int64_t st = __shfl_sync(kFull, start, j);
+                const int ex = __shfl_sync(kFull, excl, j);
+                bool ins = false;
+                int32_t x = 0;
+                if (e < total) {
+                    x = col[st + (e - ex)];
+                    ins = t1_insert(S.table, x);
+                }
+                const unsigned m = __ballot_sync(kFull, ins);
+                const int p = cnt + __popc(m & lt);
+                if (ins && p < kT1Cap) S.list[p] = x;
+                cnt += __popc(m);
+                if (cnt > kT1Cap) return -1;
+            }
+            __syncwarp();
+        }
+        lb = le;
+        le = cnt;
+    }
+    return cnt;
+}
+
+__device__ void warp_bitonic_sort(int32_t* a, int P, int lane)
+{
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < (P >> 1); i += 32) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const int32_t x = a[lo], y = a[hi];
+                if ((x > y) == up) {
+                    a[lo] = y;
+                    a[hi] = x;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kT1Warps * 32)
+t1_count_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __restrict__ col, int k,
+                int64_t* __restrict__ counts, int32_t* __restrict__ queue, int* __restrict__ qn)
+{
+    __shared__ T1Smem sm[kT1Warps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t v = (int64_t)blockIdx.x * kT1Warps + warp; v < n;
+         v += (int64_t)gridDim.x * kT1Warps) {
+        const int c = t1_ball(row, col, k, (int32_t)v, sm[warp], lane);
+        if (lane == 0) {
+            if (c < 0) {
+                counts[v] = -1;
+                queue[atomicAdd(qn, 1)] = (int32_t)v;
+            } else {
+                counts[v] = c - 1;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(kT1Warps * 32)
+t1_fill_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __restrict__ col, int k,
+               const int64_t* __restrict__ counts, const int64_t* __restrict__ krow,
+               uint32_t* __restrict__ kcol)
+{
+    __shared__ T1Smem sm[kT1Warps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t v = (int64_t)blockIdx.x * kT1Warps + warp; v < n;
+         v += (int64_t)gridDim.x * kT1Warps) {
+        if (counts[v] + 1 > kT1Cap) continue;  // warp-uniform: tier 2 owns this source
+        T1Smem& S = sm[warp];
+        const int c = t1_ball(row, col, k, (int32_t)v, S, lane);
+        const int m = c - 1;
+        int P = 1;
+        while (P < m) P <<= 1;
+        // the table is no longer needed: sort the ball (source excluded) in it
+        for (int i = lane; i < P; i += 32) S.table[i] = (i < m) ? S.list[1 + i] : INT_MAX;
+        __syncwarp();
+        warp_bitonic_sort(S.table, P, lane);
+        uint32_t* out = kcol + krow[v];
+        for (int i = lane; i < m; i += 32) out[i] = (uint32_t)S.table[i];
+        __syncwarp();
+    }
+}
+
+// Tier 2: one block per source with a global bitmap and visit list.
+// fill == false: counts[src] = |N_src(k)|; fill == true: sorted row at krow[src].
+__global__ void __launch_bounds__(kT2Threads)
+t2_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __restrict__ col, int k,
+          const int32_t* __restrict__ queue, int nq, uint32_t* __restrict__ bitmaps,
+          int32_t* __restrict__ lists, int64_t nwords, int64_t* __restrict__ counts,
+          const int64_t* __restrict__ krow, uint32_t* __restrict__ kcol, int fill)
+{
+    __shared__ int64_t s_incl[kT2Threads];
+    __shared__ int64_t s_start[kT2Threads];
+    __shared__ int64_t s_deg[kT2Threads];
+    __shared__ int64_t s_wt[kT2Threads / 32 + 1];
+    __shared__ int s_cnt;
+    const int tid = threadIdx.x;
+    uint32_t* B = bitmaps + (int64_t)blockIdx.x * nwords;
+    int32_t* V = lists + (int64_t)blockIdx.x * n;
+    for (int qi = blockIdx.x; qi < nq; qi += gridDim.x) {
+        const int32_t src = queue[qi];
+        if (tid == 0) {
+            B[src >> 5] |= 1u << (src & 31);
+            V[0] = src;
+            s_cnt = 1;
+        }
+        __syncthreads();
+        int64_t lb = 0, le = 1;
+        for (int depth = 1; depth <= k && lb < le; ++depth) {
+            for (int64_t fb = lb; fb < le; fb += kT2Threads) {
+                const int64_t f = fb + tid;
+                int64_t start = 0, deg = 0;
+                if (f < le) {
+                    const int32_t w = V[f];
+                    start = row[w];
+                    deg = row[w + 1] - start;
+                }
+                int64_t total;
+                const int64_t incl = block_inclusive_scan<int64_t, kT2Threads>(deg, s_wt, &total);
+                s_incl[tid] = incl;
+                s_start[tid] = start;
+                s_deg[tid] = deg;
+                __syncthreads();
+                for (int64_t base = 0; base < total; base += kT2Threads) {
+                    const int64_t e = base + tid;
+                    if (e < total) {
+                        int lo = 0, hi = kT2Threads - 1;  // first j with incl[j] > e
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (s_incl[mid] > e) hi = mid; else lo = mid + 1;
+                        }
+                        const int64_t off = e - (s_incl[lo] - s_deg[lo]);
+                        const int32_t x = col[s_start[lo] + off];
+                        const uint32_t bit = 1u << (x & 31);
+                        const uint32_t old = atomicOr(&B[x >> 5], bit);
+                        if (!(old & bit)) V[atomicAdd(&s_cnt, 1)] = x;
+                    }
+                }
+                __syncthreads();
+            }
+            lb = le;
+            le = s_cnt;
+            __syncthreads();
+        }
+        const int cnt = s_cnt;
+        if (!fill) {
+            if (tid == 0) counts[src] = cnt - 1;
+        } else {
+            uint32_t* out = kcol + krow[src];
+            int64_t base = 0;
+            for (int64_t w0 = 0; w0 < nwords; w0 += kT2Threads) {
+                const int64_t wi = w0 + tid;
+                uint32_t w = (wi < nwords) ? B[wi] : 0u;
+                if (wi == (src >> 5)) w &= ~(1u << (src & 31));
+                int64_t total;
+                const int64_t incl =
+                    block_inclusive_scan<int64_t, kT2Threads>((int64_t)__popc(w), s_wt, &total);
+                int64_t o = base + incl - __popc(w);
+                while (w) {
+                    const int b = __ffs(w) - 1;
+                    out[o++] = (uint32_t)(wi * 32 + b);
+                    w &= w - 1;
+                }
+                base += total;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < cnt; i += kT2Threads) B[V[i] >> 5] = 0u;
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------------- scan
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// out[i + 1] = in[0] + ... + in[i] within each tile; tile totals to bsum.
+__global__ void __launch_bounds__(kScanThreads)
+scan_tiles_kernel(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ out,
+                  int64_t* __restrict__ bsum)
+{
+    __shared__ int64_t wt[kScanThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0;
+        s += v[i];
+    }
+    int64_t total;
+    const int64_t incl = block_inclusive_scan<int64_t, kScanThreads>(s, wt, &total);
+    int64_t run = incl - s;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        run += v[i];
+        if (base + i < n) out[base + i + 1] = run;
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// Exclusive scan of the tile totals, in place, by one block.
+__global__ void __launch_bounds__(kScanThreads)
+scan_bsum_kernel(int64_t* __restrict__ bsum, int64_t nb)
+{
+    __shared__ int64_t wt[kScanThreads / 32 + 1];
+    int64_t carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
+        const int64_t i = b0 + threadIdx.x;
+        const int64_t v = (i < nb) ? bsum[i] : 0;
+        int64_t total;
+        const int64_t incl = block_inclusive_scan<int64_t, kScanThreads>(v, wt, &total);
+        if (i < nb) bsum[i] = carry + incl - v;
+        carry += total;
+    }
+}
+
+__global__ void scan_add_kernel(int64_t* __restrict__ out, int64_t n,
+                                const int64_t* __restrict__ bsum)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) out[0] = 0;
+    if (i < n) out[i + 1] += bsum[i / kScanTile];
+}
+
+// --------------------------------------------------------------- edge flags
+
+// Set the edge flag on every entry of row v that is a neighbour of v in G.
+// Searches compare ids without the flag, so concurrent flagging in the same
+// row does not disturb them.
+__global__ void mark_edges_kernel(int64_t n, const int64_t* __restrict__ row,
+                                  const int32_t* __restrict__ col,
+                                  const int64_t* __restrict__ krow, uint32_t* __restrict__ kcol)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        const int64_t ks = krow[v], ke = krow[v + 1];
+        for (int64_t e = row[v] + lane; e < row[v + 1]; e += 32) {
+            const uint32_t w = (uint32_t)col[e];
+            int64_t lo = ks, hi = ke;  // first entry with id >= w
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if ((kcol[mid] & kIdMask) < w) lo = mid + 1; else hi = mid;
+            }
+            if (lo < ke && (kcol[lo] & kIdMask) == w) kcol[lo] = w | kEdgeFlag;
+        }
+    }
+}
+
+// --------------------------------------------------------------- binning
+
+constexpr int kBinThreads = 1024;
+
+__device__ __forceinline__ int row_class(int64_t len, BinConfig c)
+{
+    if (len <= c.small_max) return 0;
+    if (len <= c.warp_max) return 1;
+    if (len <= c.block_max) return 2;
+    return 3;
+}
+
+// Per-block class counts (block b covers vertices [b*1024, (b+1)*1024)).
+__global__ void __launch_bounds__(kBinThreads)
+bin_count_kernel(int64_t n, const int64_t* __restrict__ krow, BinConfig cfg,
+                 int* __restrict__ bcount)
+{
+    __shared__ int cnt[4];
+    if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t v = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
+    if (v < n) atomicAdd(&cnt[row_class(krow[v + 1] - krow[v], cfg)], 1);
+    __syncthreads();
+    if (threadIdx.x < 4) bcount[blockIdx.x * 4 + threadIdx.x] = cnt[threadIdx.x];
+}
+
+// Scatter vertex ids to their class lists in ascending id order.
+__global__ void __launch_bounds__(kBinThreads)
+bin_scatter_kernel(int64_t n, const int64_t* __restrict__ krow, BinConfig cfg,
+                   const int* __restrict__ boff, int32_t* __restrict__ lists,
+                   int32_t* __restrict__ giants)
+{
+    __shared__ int wcnt[kBinThreads / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t v = (int64_t)blockIdx.x * kBinThreads + threadIdx.x;
+    const int c = (v < n) ? row_class(krow[v + 1] - krow[v], cfg) : -1;
+    int rank = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const unsigned m = __ballot_sync(kFull, c == q);
+        if (c == q) rank = __popc(m & lanemask_lt());
+        if (lane == 0) wcnt[warp][q] = __popc(m);
+    }
+    __syncthreads();
+    if (c >= 0) {
+        int pre = 0;
+        for (int w = 0; w < warp; ++w) pre += wcnt[w][c];
+        const int pos = boff[blockIdx.x * 4 + c] + pre + rank;
+        if (c < 3) lists[pos] = (int32_t)v; else giants[pos] = (int32_t)v;
+    }
+}
+
+template <class T>
+gila_status dev_alloc(T** p, size_t count)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GILA_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    *p = (T*)q;
+    return GILA_OK;
+}
+
+gila_status exclusive_scan(const int64_t* in, int64_t n, int64_t* out, cudaStream_t st)
+{
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    int64_t* bsum = nullptr;
+    gila_status s = dev_alloc(&bsum, (size_t)std::max<int64_t>(nb, 1));
+    if (s != GILA_OK) return s;
+    if (n > 0) {
+        scan_tiles_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, out, bsum);
+        count_launch();
+        scan_bsum_kernel<<<1, kScanThreads, 0, st>>>(bsum, nb);
+        count_launch();
+        scan_add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n, bsum);
+        count_launch();
+    } else {
+        cudaMemsetAsync(out, 0, sizeof(int64_t), st);
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(bsum);
+    if (e != cudaSuccess) return cuda_fail(e, "exclusive_scan");
+    return GILA_OK;
+}
+
+gila_status build_bins(gila_graph* g)
+{
+    Bins& B = g->bins;
+    const int64_t n = g->n;
+    cudaStream_t st = g->stream;
+    const int64_t nb = (n + kBinThreads - 1) / kBinThreads;
+    std::vector<int> bc((size_t)nb * 4), boff((size_t)nb * 4);
+    int* d_bc = nullptr;
+    gila_status s = dev_alloc(&d_bc, (size_t)std::max<int64_t>(nb * 4, 4));
+    if (s != GILA_OK) return s;
+    if (nb > 0) {
+        bin_count_kernel<<<(unsigned)nb, kBinThreads, 0, st>>>(n, g->krow, B.cfg, d_bc);
+        count_launch();
+        cudaMemcpyAsync(bc.data(), d_bc, sizeof(int) * nb * 4, cudaMemcpyDeviceToHost, st);
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { cudaFree(d_bc); return cuda_fail(e, "bin_count"); }
+    int64_t tot[4] = {0, 0, 0, 0};
+    for (int64_t b = 0; b < nb; ++b)
+        for (int c = 0; c < 4; ++c) tot[c] += bc[b * 4 + c];
+    int64_t base[4] = {0, tot[0], tot[0] + tot[1], 0};
+    for (int c = 0; c < 4; ++c) {
+        int64_t run = base[c];
+        for (int64_t b = 0; b < nb; ++b) {
+            boff[b * 4 + c] = (int)run;
+            run += bc[b * 4 + c];
+        }
+    }
+    B.n0 = (int32_t)tot[0];
+    B.n1 = (int32_t)tot[1];
+    B.n2 = (int32_t)tot[2];
+    B.ngiant = (int32_t)tot[3];
+    const size_t nlist = (size_t)(tot[0] + tot[1] + tot[2]);
+    if (nlist > B.cap_lists || !B.lists) {
+        if (B.lists) cudaFree(B.lists);
+        B.lists = nullptr;
+        s = dev_alloc(&B.lists, std::max<size_t>(nlist, 1));
+        if (s != GILA_OK) { cudaFree(d_bc); return s; }
+        B.cap_lists = std::max<size_t>(nlist, 1);
+    }
+    int32_t* d_giants = nullptr;
+    s = dev_alloc(&d_giants, (size_t)std::max<int64_t>(tot[3], 1));
+    if (s != GILA_OK) { cudaFree(d_bc); return s; }
+    if (nb > 0) {
+        cudaMemcpyAsync(d_bc, boff.data(), sizeof(int) * nb * 4, cudaMemcpyHostToDevice, st);
+        bin_scatter_kernel<<<(unsigned)nb, kBinThreads, 0, st>>>(n, g->krow, B.cfg, d_bc, B.lists,
+                                                                 d_giants);
+        count_launch();
+    }
+    // chunk table of the giant rows, built on the host
+    std::vector<int32_t> giants((size_t)tot[3]);
+    std::vector<int64_t> gk((size_t)tot[3] * 2);
+    if (tot[3] > 0)
+        cudaMemcpyAsync(giants.data(), d_giants, sizeof(int32_t) * tot[3], cudaMemcpyDeviceToHost,
+                        st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { cudaFree(d_bc); cudaFree(d_giants); return cuda_fail(e, "bin_scatter"); }
+    for (int64_t i = 0; i < tot[3]; ++i) {
+        e = cudaMemcpyAsync(&gk[2 * i], g->krow + giants[i], 2 * sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_bc);
+    cudaFree(d_giants);
+    if (e != cudaSuccess) return cuda_fail(e, "giant rows");
+    std::vector<Chunk> chunks;
+    for (int64_t i = 0; i < tot[3]; ++i) {
+        const int64_t b = gk[2 * i], en = gk[2 * i + 1];
+        const int32_t first = (int32_t)chunks.size();
+        const int32_t count = (int32_t)((en - b + B.cfg.chunk - 1) / B.cfg.chunk);
+        for (int32_t c = 0; c < count; ++c) {
+            Chunk ch;
+            ch.begin = b + (int64_t)c * B.cfg.chunk;
+            ch.end = std::min<int64_t>(en, ch.begin + B.cfg.chunk);
+            ch.vertex = giants[i];
+            ch.giant = (int32_t)i;
+            ch.first = first;
+            ch.count = count;
+            chunks.push_back(ch);
+        }
+    }
+    B.nchunks = (int32_t)chunks.size();
+    if (chunks.size() > B.cap_chunks || !B.chunks) {
+        if (B.chunks) cudaFree(B.chunks);
+        if (B.partials) cudaFree(B.partials);
+        B.chunks = nullptr;
+        B.partials = nullptr;
+        size_t cap = std::max<size_t>(chunks.size(), 1);
+        s = dev_alloc(&B.chunks, cap);
+        if (s != GILA_OK) return s;
+        double* part = nullptr;
+        s = dev_alloc(&part, cap * 4);
+        if (s != GILA_OK) return s;
+        B.partials = part;
+        B.cap_chunks = cap;
+    }
+    if ((size_t)tot[3] > B.cap_giant || !B.giant_counter) {
+        if (B.giant_counter) cudaFree(B.giant_counter);
+        B.giant_counter = nullptr;
+        size_t cap = std::max<size_t>((size_t)tot[3], 1);
+        s = dev_alloc(&B.giant_counter, cap);
+        if (s != GILA_OK) return s;
+        B.cap_giant = cap;
+    }
+    if (!chunks.empty())
+        GILA_CUDA(cudaMemcpyAsync(B.chunks, chunks.data(), sizeof(Chunk) * chunks.size(),
+                                  cudaMemcpyHostToDevice, st));
+    GILA_CUDA(cudaMemsetAsync(B.giant_counter, 0, sizeof(int32_t) * B.cap_giant, st));
+    GILA_CUDA(cudaStreamSynchronize(st));
+    return GILA_OK;
+}
+
+}  // namespace
+
+int sm_count(int device)
+{
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0)
+        v = 1;
+    return v;
+}
+
+void free_khop(gila_graph* g)
+{
+    KhopScratch& s = g->ks;
+    cudaFree(s.counts);
+    cudaFree(s.queue);
+    cudaFree(s.qn);
+    cudaFree(s.bitmaps);
+    cudaFree(s.lists);
+    s = KhopScratch();
+    cudaFree(g->krow);
+    cudaFree(g->kcol);
+    g->krow = nullptr;
+    g->kcol = nullptr;
+    g->cap_kcol = 0;
+    Bins& B = g->bins;
+    cudaFree(B.lists);
+    cudaFree(B.chunks);
+    cudaFree(B.giant_counter);
+    cudaFree(B.partials);
+    BinConfig cfg = B.cfg;
+    B = Bins();
+    B.cfg = cfg;
+    g->k_built = 0;
+    g->nnz_khop = 0;
+}
+
+gila_status build_khop(gila_graph* g, int k)
+{
+    const int64_t n = g->n;
+    cudaStream_t st = g->stream;
+    KhopScratch& S = g->ks;
+    gila_status s;
+    if (!g->krow) {
+        s = dev_alloc(&g->krow, (size_t)n + 1);
+        if (s != GILA_OK) return s;
+    }
+    if (S.cap_n < (size_t)n || !S.counts) {
+        cudaFree(S.counts);
+        cudaFree(S.queue);
+        cudaFree(S.qn);
+        S.counts = nullptr; S.queue = nullptr; S.qn = nullptr;
+        if ((s = dev_alloc(&S.counts, (size_t)std::max<int64_t>(n, 1))) != GILA_OK) return s;
+        if ((s = dev_alloc(&S.queue, (size_t)std::max<int64_t>(n, 1))) != GILA_OK) return s;
+        if ((s = dev_alloc(&S.qn, 1)) != GILA_OK) return s;
+        S.cap_n = (size_t)n;
+    }
+    GILA_CUDA(cudaMemsetAsync(S.qn, 0, sizeof(int), st));
+    const int sms = sm_count(g->device);
+    const int64_t t1_blocks = std::max<int64_t>(
+        1, std::min<int64_t>((n + kT1Warps - 1) / kT1Warps, (int64_t)sms * 8));
+    if (n > 0) {
+        t1_count_kernel<<<(unsigned)t1_blocks, kT1Warps * 32, 0, st>>>(n, g->row, g->col, k,
+                                                                       S.counts, S.queue, S.qn);
+        count_launch();
+    }
+    int nq = 0;
+    GILA_CUDA(cudaMemcpyAsync(&nq, S.qn, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GILA_CUDA(cudaStreamSynchronize(st));
+    // tier 2 scratch: one bitmap and one visit list per block
+    const int64_t nwords = ((n + 31) / 32 + 3) & ~int64_t(3);
+    int t2_blocks = 0;
+    if (nq > 0) {
+        const size_t per_block = (size_t)nwords * 4 + (size_t)n * 4;
+        const size_t budget = (size_t)2 << 30;  // at most 2 GiB of tier-2 scratch
+        int64_t want = std::min<int64_t>(nq, (int64_t)sms * 4);
+        want = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)(budget / per_block)));
+        t2_blocks = (int)want;
+        if (S.t2_blocks < t2_blocks || S.bitmap_words != nwords || !S.bitmaps) {
+            cudaFree(S.bitmaps);
+            cudaFree(S.lists);
+            S.bitmaps = nullptr; S.lists = nullptr;
+            if ((s = dev_alloc(&S.bitmaps, (size_t)nwords * t2_blocks)) != GILA_OK) return s;
+            if ((s = dev_alloc(&S.lists, (size_t)n * t2_blocks)) != GILA_OK) return s;
+            GILA_CUDA(cudaMemsetAsync(S.bitmaps, 0, sizeof(uint32_t) * nwords * t2_blocks, st));
+            S.t2_blocks = t2_blocks;
+            S.bitmap_words = nwords;
+        }
+        t2_kernel<<<t2_blocks, kT2Threads, 0, st>>>(n, g->row, g->col, k, S.queue, nq, S.bitmaps,
+                                                    S.lists, nwords, S.counts, nullptr, nullptr, 0);
+        count_launch();
+    }
+    s = exclusive_scan(S.counts, n, g->krow, st);
+    if (s != GILA_OK) return s;
+    int64_t nnz = 0;
+    GILA_CUDA(cudaMemcpyAsync(&nnz, g->krow + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GILA_CUDA(cudaStreamSynchronize(st));
+    if ((size_t)nnz > g->cap_kcol || !g->kcol) {
+        cudaFree(g->kcol);
+        g->kcol = nullptr;
+        g->cap_kcol = 0;
+        if ((s = dev_alloc(&g->kcol, (size_t)nnz)) != GILA_OK) return s;
+        g->cap_kcol = (size_t)nnz;
+    }
+    if (n > 0) {
+        t1_fill_kernel<<<(unsigned)t1_blocks, kT1Warps * 32, 0, st>>>(n, g->row, g->col, k,
+                                                                      S.counts, g->krow, g->kcol);
+        count_launch();
+    }
+    if (nq > 0) {
+        t2_kernel<<<t2_blocks, kT2Threads, 0, st>>>(n, g->row, g->col, k, S.queue, nq, S.bitmaps,
+                                                    S.lists, nwords, S.counts, g->krow, g->kcol, 1);
+        count_launch();
+    }
+    if (n > 0) {
+        const int64_t warps = std::min<int64_t>(n, (int64_t)sms * 64);
+        mark_edges_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(n, g->row, g->col,
+                                                                              g->krow, g->kcol);
+        count_launch();
+    }
+    GILA_CUDA(cudaGetLastError());
+    GILA_CUDA(cudaStreamSynchronize(st));
+    s = build_bins(g);
+    if (s != GILA_OK) return s;
+    g->nnz_khop = nnz;
+    g->k_built = k;
+    return GILA_OK;
+}
+
+}  // namespace gila

@@ -1,0 +1,639 @@
+// One layout iteration as a single kernel launch, plus FP64 quality
+// reductions and placement conversions.
+//
+// Iteration (Sections 3.1 and 4.5 of the paper): for every vertex u
+//   F(u) = sum over v in N_u(k) of d^2/delta^q along (x_u - x_v)/delta
+//        + sum over edges (u,v)  of delta^p/d along (x_v - x_u)/delta
+//   x_u <- x_u + F(u) min(1, t/|F(u)|), all vertices at once.
+// Per entry of a k-hop row the kernel computes Delta = x_u - x_v and adds
+// c Delta with c = d^2/delta^(q+1) - [edge] delta^(p-1)/d; for p = 2, q = 1
+// this is d^2/r^2 - [edge] sqrt(r^2)/d with r^2 = |Delta|^2, one divide and,
+// on edges only, one square root. The edge flag rides in the top bit of the
+// stored id, so attraction and repulsion share one pass over the list.
+//
+// Work is split by row length into four classes, each a range of blocks
+// of the same launch (heaviest first): rows split into chunks summed by the
+// last chunk to finish, one block per row, one warp per row, and groups of
+// 8 lanes per row. Every row's reduction order depends on its own length
+// only, so a vertex gets the same result whatever else is in the graph.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "device_util.cuh"
+#include "gila_impl.h"
+
+namespace gila {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarpsPerBlock = kThreads / 32;
+
+template <class T> struct V2;
+template <> struct V2<float> { using type = float2; };
+template <> struct V2<double> { using type = double2; };
+
+enum Model { kFR = 0, kGeneric = 1 };
+
+struct IterArgs {
+    const int64_t* krow;
+    const uint32_t* kcol;
+    const int32_t* list0;
+    const int32_t* list1;
+    const int32_t* list2;
+    const Chunk* chunks;
+    int32_t* giant_counter;
+    double* partials;
+    int32_t n0, n1, n2, nchunks;
+    int32_t b3, b2, b1, b0;  // blocks per class, launched in the order 3, 2, 1, 0
+    double d, t;
+    int p, q;
+    const void* pos_in;
+    void* pos_out;
+    void* disp_out;
+};
+
+// Streaming load of four ids: read once per iteration, kept out of L1 so
+// that L1 serves the position gathers.
+__device__ __forceinline__ uint4 ld_ids4(const uint4* p)
+{
+    uint4 r;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t ld_id(const uint32_t* p)
+{
+    uint32_t r;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(r) : "l"(p));
+    return r;
+}
+
+template <class T>
+__device__ __forceinline__ T ipow_(T x, int e)
+{
+    T r = T(1);
+    for (int i = 0; i < e; ++i) r *= x;
+    return r;
+}
+
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float fsqrt(float r2) { return r2 * rsqrtf(r2); }
+__device__ __forceinline__ double fsqrt(double r2) { return sqrt(r2); }
+
+// Force accumulator; COMP adds a running compensation term per component
+// (two-sum), which removes the rounding error of long float sums.
+template <class T, bool COMP>
+struct Acc {
+    T sx = T(0), sy = T(0), cx = T(0), cy = T(0);
+
+    __device__ __forceinline__ static void two_sum(T& s, T& c, T x)
+    {
+        const T t = s + x;
+        const T bp = t - s;
+        c += (s - (t - bp)) + (x - bp);
+        s = t;
+    }
+    __device__ __forceinline__ void add(T x, T y)
+    {
+        if (COMP) {
+            two_sum(sx, cx, x);
+            two_sum(sy, cy, y);
+        } else {
+            sx += x;
+            sy += y;
+        }
+    }
+    __device__ __forceinline__ void merge(T ox, T oy, T ocx, T ocy)
+    {
+        if (COMP) {
+            two_sum(sx, cx, ox);
+            two_sum(sy, cy, oy);
+            cx += ocx;
+            cy += ocy;
+        } else {
+            sx += ox;
+            sy += oy;
+        }
+    }
+    __device__ __forceinline__ void group_reduce(int width)
+    {
+        for (int o = width >> 1; o > 0; o >>= 1) {
+            const T ox = __shfl_xor_sync(kFull, sx, o, width);
+            const T oy = __shfl_xor_sync(kFull, sy, o, width);
+            const T ocx = COMP ? __shfl_xor_sync(kFull, cx, o, width) : T(0);
+            const T ocy = COMP ? __shfl_xor_sync(kFull, cy, o, width) : T(0);
+            merge(ox, oy, ocx, ocy);
+        }
+    }
+    __device__ __forceinline__ T fx() const { return COMP ? sx + cx : sx; }
+    __device__ __forceinline__ T fy() const { return COMP ? sy + cy : sy; }
+};
+
+template <class T, int MODEL, bool COMP>
+struct Pair {
+    using P2 = typename V2<T>::type;
+    const P2* __restrict__ pos;
+    T xu, yu, d2, inv_d;
+    int p, q;
+
+    __device__ __forceinline__ void operator()(uint32_t e, Acc<T, COMP>& a) const
+    {
+        const P2 pv = __ldg(pos + (e & kIdMask));
+        const T dx = xu - pv.x, dy = yu - pv.y;
+        const T r2 = dx * dx + dy * dy;
+        if (r2 > T(0)) {
+            T c;
+            if (MODEL == kFR) {
+                c = fdiv(d2, r2);
+                if (e & kEdgeFlag) c -= fsqrt(r2) * inv_d;
+            } else {
+                const T dl = sqrt(r2);
+                c = d2 / (ipow_(dl, q) * dl);
+                if (e & kEdgeFlag) c -= ipow_(dl, p) / dl * inv_d;
+            }
+            a.add(c * dx, c * dy);
+        }
+    }
+};
+
+// Entries [s, e) of kcol, lanes gl = 0..G-1 of a group (G >= 4): an
+// unaligned head of at most 3 entries, 16-byte vector loads of 4 ids,
+// then a tail of at most 3 entries.
+template <class T, int MODEL, bool COMP>
+__device__ __forceinline__ void row_sum(const uint32_t* __restrict__ kcol, int64_t s, int64_t e,
+                                        int gl, int G, const Pair<T, MODEL, COMP>& f,
+                                        Acc<T, COMP>& a)
+{
+    int64_t s4 = (s + 3) & ~int64_t(3);
+    if (s4 > e) s4 = e;
+    int64_t e4 = e & ~int64_t(3);
+    if (e4 < s4) e4 = s4;
+    if (s + gl < s4) f(ld_id(kcol + s + gl), a);
+    const uint4* k4 = reinterpret_cast<const uint4*>(kcol);
+#pragma unroll 2
+    for (int64_t c = (s4 >> 2) + gl; c < (e4 >> 2); c += G) {
+        const uint4 w = ld_ids4(k4 + c);
+        f(w.x, a);
+        f(w.y, a);
+        f(w.z, a);
+        f(w.w, a);
+    }
+    if (e4 + gl < e) f(ld_id(kcol + e4 + gl), a);
+}
+
+template <class T>
+__device__ __forceinline__ void apply_move(const IterArgs& A, int64_t u, T xu, T yu, T fx, T fy)
+{
+    using P2 = typename V2<T>::type;
+    const T t = (T)A.t;
+    const T fn = sqrt(fx * fx + fy * fy);
+    T mx = fx, my = fy;
+    if (fn > t) {
+        const T sc = t / fn;
+        mx = fx * sc;
+        my = fy * sc;
+    }
+    P2 o;
+    o.x = xu + mx;
+    o.y = yu + my;
+    reinterpret_cast<P2*>(A.pos_out)[u] = o;
+    if (A.disp_out) {
+        P2 m;
+        m.x = mx;
+        m.y = my;
+        reinterpret_cast<P2*>(A.disp_out)[u] = m;
+    }
+}
+
+// Block-wide sum of an accumulator in a fixed order (warps, then warp 0).
+template <class T, bool COMP>
+__device__ __forceinline__ void block_reduce(Acc<T, COMP>& a, T* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    a.group_reduce(32);
+    if (lane == 0) {
+        sh[warp * 4 + 0] = a.sx;
+        sh[warp * 4 + 1] = a.sy;
+        sh[warp * 4 + 2] = a.cx;
+        sh[warp * 4 + 3] = a.cy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Acc<T, COMP> r;
+        r.sx = sh[0];
+        r.sy = sh[1];
+        r.cx = sh[2];
+        r.cy = sh[3];
+        for (int w = 1; w < kWarpsPerBlock; ++w)
+            r.merge(sh[w * 4 + 0], sh[w * 4 + 1], sh[w * 4 + 2], sh[w * 4 + 3]);
+        a = r;
+    }
+}
+
+template <class T, int MODEL, bool COMP>
+__global__ void __launch_bounds__(kThreads)
+iteration_kernel(const IterArgs A)
+{
+    using P2 = typename V2<T>::type;
+    __shared__ T sh[kWarpsPerBlock * 4];
+    __shared__ int s_last;
+    const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos_in);
+    Pair<T, MODEL, COMP> f;
+    f.pos = pos;
+    f.d2 = (T)(A.d * A.d);
+    f.inv_d = (T)(1.0 / A.d);
+    f.p = A.p;
+    f.q = A.q;
+    int b = blockIdx.x;
+    if (b < A.b3) {
+        // a chunk of a giant row: block sum, then the last chunk finishes u
+        const Chunk ch = A.chunks[b];
+        const int64_t u = ch.vertex;
+        const P2 pu = pos[u];
+        f.xu = pu.x;
+        f.yu = pu.y;
+        Acc<T, COMP> a;
+        row_sum<T, MODEL, COMP>(A.kcol, ch.begin, ch.end, threadIdx.x, kThreads, f, a);
+        block_reduce<T, COMP>(a, sh);
+        if (threadIdx.x == 0) {
+            double* part = A.partials + (int64_t)b * 4;
+            part[0] = (double)a.sx;
+            part[1] = (double)a.sy;
+            part[2] = (double)a.cx;
+            part[3] = (double)a.cy;
+            __threadfence();
+            const int prev = atomicAdd(&A.giant_counter[ch.giant], 1);
+            s_last = (prev == ch.count - 1);
+        }
+        __syncthreads();
+        if (s_last && threadIdx.x == 0) {
+            __threadfence();
+            double fx = 0.0, fy = 0.0;
+            for (int i = 0; i < ch.count; ++i) {
+                const double* q = A.partials + (int64_t)(ch.first + i) * 4;
+                fx += __ldcg(q + 0) + __ldcg(q + 2);
+                fy += __ldcg(q + 1) + __ldcg(q + 3);
+            }
+            A.giant_counter[ch.giant] = 0;
+            apply_move<T>(A, u, pu.x, pu.y, (T)fx, (T)fy);
+        }
+        return;
+    }
+    b -= A.b3;
+    if (b < A.b2) {
+        const int64_t u = A.list2[b];
+        const P2 pu = pos[u];
+        f.xu = pu.x;
+        f.yu = pu.y;
+        Acc<T, COMP> a;
+        row_sum<T, MODEL, COMP>(A.kcol, A.krow[u], A.krow[u + 1], threadIdx.x, kThreads, f, a);
+        block_reduce<T, COMP>(a, sh);
+        if (threadIdx.x == 0) apply_move<T>(A, u, pu.x, pu.y, a.fx(), a.fy());
+        return;
+    }
+    b -= A.b2;
+    if (b < A.b1) {
+        const int i = b * kWarpsPerBlock + (threadIdx.x >> 5);
+        if (i >= A.n1) return;  // whole warp leaves together
+        const int lane = threadIdx.x & 31;
+        const int64_t u = A.list1[i];
+        const P2 pu = pos[u];
+        f.xu = pu.x;
+        f.yu = pu.y;
+        Acc<T, COMP> a;
+        row_sum<T, MODEL, COMP>(A.kcol, A.krow[u], A.krow[u + 1], lane, 32, f, a);
+        a.group_reduce(32);
+        if (lane == 0) apply_move<T>(A, u, pu.x, pu.y, a.fx(), a.fy());
+        return;
+    }
+    b -= A.b1;
+    {
+        constexpr int G = 8;
+        const int gl = threadIdx.x & (G - 1);
+        const int i = b * (kThreads / G) + (threadIdx.x / G);
+        const bool live = i < A.n0;
+        // lanes of a group stay together through the shuffles below
+        const int64_t u = live ? A.list0[i] : 0;
+        Acc<T, COMP> a;
+        T xu = T(0), yu = T(0);
+        if (live) {
+            const P2 pu = pos[u];
+            xu = pu.x;
+            yu = pu.y;
+            f.xu = xu;
+            f.yu = yu;
+            row_sum<T, MODEL, COMP>(A.kcol, A.krow[u], A.krow[u + 1], gl, G, f, a);
+        }
+        a.group_reduce(G);
+        if (live && gl == 0) apply_move<T>(A, u, xu, yu, a.fx(), a.fy());
+    }
+}
+
+template <class T, int MODEL, bool COMP>
+cudaError_t launch_typed(const IterArgs& A, unsigned grid, cudaStream_t st)
+{
+    iteration_kernel<T, MODEL, COMP><<<grid, kThreads, 0, st>>>(A);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- metrics
+
+constexpr int kRedBlocks = 512;
+constexpr int kRedThreads = 256;
+
+template <class T>
+__device__ __forceinline__ double2 load_pos(const void* pos, int64_t u)
+{
+    using P2 = typename V2<T>::type;
+    const P2 p = reinterpret_cast<const P2*>(pos)[u];
+    return make_double2((double)p.x, (double)p.y);
+}
+
+__device__ __forceinline__ double dipow(double x, int e)
+{
+    double r = 1.0;
+    for (int i = 0; i < e; ++i) r *= x;
+    return r;
+}
+
+// pass 0: [sum delta, count, sum delta^p/d, sum over k-hop pairs d^2/delta^q]
+// pass 1: [sum (delta - mean)^2, 0, 0, 0]
+// Each warp owns a fixed set of vertices; partial sums are combined in a
+// fixed order, so the result does not depend on timing.
+template <class T>
+__global__ void __launch_bounds__(kRedThreads)
+metrics_kernel(int pass, int64_t n, const int64_t* __restrict__ row,
+               const int32_t* __restrict__ col, const int64_t* __restrict__ krow,
+               const uint32_t* __restrict__ kcol, const void* pos, double d, int p, int q,
+               double mean, double* __restrict__ partials)
+{
+    __shared__ double sh[kRedThreads / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * (kRedThreads / 32);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int64_t u = (int64_t)blockIdx.x * (kRedThreads / 32) + warp; u < n; u += nw) {
+        const double2 pu = load_pos<T>(pos, u);
+        for (int64_t e = row[u] + lane; e < row[u + 1]; e += 32) {
+            const int64_t v = col[e];
+            if (v <= u) continue;
+            const double2 pv = load_pos<T>(pos, v);
+            const double dx = pu.x - pv.x, dy = pu.y - pv.y;
+            const double dl = sqrt(dx * dx + dy * dy);
+            if (pass == 0) {
+                a0 += dl;
+                a1 += 1.0;
+                if (dl > 0.0) a2 += dipow(dl, p) / d;
+            } else {
+                a0 += (dl - mean) * (dl - mean);
+            }
+        }
+        if (pass == 0) {
+            for (int64_t e = krow[u] + lane; e < krow[u + 1]; e += 32) {
+                const int64_t v = kcol[e] & kIdMask;
+                if (v <= u) continue;
+                const double2 pv = load_pos<T>(pos, v);
+                const double dx = pu.x - pv.x, dy = pu.y - pv.y;
+                const double dl = sqrt(dx * dx + dy * dy);
+                if (dl > 0.0) a3 += d * d / dipow(dl, q);
+            }
+        }
+    }
+    a0 = group_sum(a0, 32);
+    a1 = group_sum(a1, 32);
+    a2 = group_sum(a2, 32);
+    a3 = group_sum(a3, 32);
+    if (lane == 0) {
+        sh[warp][0] = a0;
+        sh[warp][1] = a1;
+        sh[warp][2] = a2;
+        sh[warp][3] = a3;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) s += sh[w][threadIdx.x];
+        partials[blockIdx.x * 4 + threadIdx.x] = s;
+    }
+}
+
+// Sum the per-block partials in block order (one thread per component).
+__global__ void reduce_partials_kernel(const double* __restrict__ partials, int nblocks,
+                                       double* __restrict__ out)
+{
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += partials[b * 4 + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+template <class T>
+__global__ void bbox_kernel(int64_t n, const void* pos, double* __restrict__ partials)
+{
+    __shared__ double sh[kRedThreads][4];
+    double x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const double2 p = load_pos<T>(pos, u);
+        x0 = fmin(x0, p.x);
+        x1 = fmax(x1, p.x);
+        y0 = fmin(y0, p.y);
+        y1 = fmax(y1, p.y);
+    }
+    sh[threadIdx.x][0] = x0;
+    sh[threadIdx.x][1] = x1;
+    sh[threadIdx.x][2] = y0;
+    sh[threadIdx.x][3] = y1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < blockDim.x; ++i) {
+            x0 = fmin(x0, sh[i][0]);
+            x1 = fmax(x1, sh[i][1]);
+            y0 = fmin(y0, sh[i][2]);
+            y1 = fmax(y1, sh[i][3]);
+        }
+        partials[blockIdx.x * 4 + 0] = x0;
+        partials[blockIdx.x * 4 + 1] = x1;
+        partials[blockIdx.x * 4 + 2] = y0;
+        partials[blockIdx.x * 4 + 3] = y1;
+    }
+}
+
+__global__ void to_float2_kernel(int64_t n, const double* __restrict__ src, float2* __restrict__ dst)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = make_float2((float)src[2 * i], (float)src[2 * i + 1]);
+}
+
+__global__ void from_float2_kernel(int64_t n, const float2* __restrict__ src, double* __restrict__ dst)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const float2 p = src[i];
+        dst[2 * i] = (double)p.x;
+        dst[2 * i + 1] = (double)p.y;
+    }
+}
+
+gila_status ensure_red(gila_graph* g, size_t doubles)
+{
+    return ensure((void**)&g->red, &g->red_cap, doubles * sizeof(double));
+}
+
+}  // namespace
+
+gila_status launch_iteration(gila_graph* g, const gila_params* prm, double t, const void* pos_in,
+                             void* pos_out, void* disp_out)
+{
+    const Bins& B = g->bins;
+    IterArgs A;
+    A.krow = g->krow;
+    A.kcol = g->kcol;
+    A.list0 = B.lists;
+    A.list1 = B.lists + B.n0;
+    A.list2 = B.lists + B.n0 + B.n1;
+    A.chunks = B.chunks;
+    A.giant_counter = B.giant_counter;
+    A.partials = (double*)B.partials;
+    A.n0 = B.n0;
+    A.n1 = B.n1;
+    A.n2 = B.n2;
+    A.nchunks = B.nchunks;
+    A.b3 = B.nchunks;
+    A.b2 = B.n2;
+    A.b1 = (B.n1 + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    A.b0 = (B.n0 + (kThreads / 8) - 1) / (kThreads / 8);
+    A.d = prm->d;
+    A.t = t;
+    A.p = prm->p;
+    A.q = prm->q;
+    A.pos_in = pos_in;
+    A.pos_out = pos_out;
+    A.disp_out = disp_out;
+    const int64_t grid = (int64_t)A.b3 + A.b2 + A.b1 + A.b0;
+    if (grid == 0) return GILA_OK;
+    const bool fr = (prm->p == 2 && prm->q == 1);
+    cudaError_t e;
+    switch (prm->precision) {
+    case GILA_FP64:
+        e = fr ? launch_typed<double, kFR, false>(A, (unsigned)grid, g->stream)
+               : launch_typed<double, kGeneric, false>(A, (unsigned)grid, g->stream);
+        break;
+    case GILA_FP32_COMPENSATED:
+        e = fr ? launch_typed<float, kFR, true>(A, (unsigned)grid, g->stream)
+               : launch_typed<float, kGeneric, true>(A, (unsigned)grid, g->stream);
+        break;
+    default:
+        e = fr ? launch_typed<float, kFR, false>(A, (unsigned)grid, g->stream)
+               : launch_typed<float, kGeneric, false>(A, (unsigned)grid, g->stream);
+        break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "iteration_kernel");
+    return GILA_OK;
+}
+
+gila_status compute_metrics(gila_graph* g, const gila_params* prm, const void* pos,
+                            gila_metrics* out)
+{
+    gila_status s = ensure_red(g, (size_t)kRedBlocks * 4 + 8);
+    if (s != GILA_OK) return s;
+    double* part = g->red;
+    double* res = g->red + (size_t)kRedBlocks * 4;
+    double h[4];
+    const bool f64 = prm->precision == GILA_FP64;
+    auto run = [&](int pass, double mean) -> cudaError_t {
+        if (f64)
+            metrics_kernel<double><<<kRedBlocks, kRedThreads, 0, g->stream>>>(
+                pass, g->n, g->row, g->col, g->krow, g->kcol, pos, prm->d, prm->p, prm->q, mean,
+                part);
+        else
+            metrics_kernel<float><<<kRedBlocks, kRedThreads, 0, g->stream>>>(
+                pass, g->n, g->row, g->col, g->krow, g->kcol, pos, prm->d, prm->p, prm->q, mean,
+                part);
+        count_launch();
+        reduce_partials_kernel<<<1, 32, 0, g->stream>>>(part, kRedBlocks, res);
+        count_launch();
+        cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, g->stream);
+        return cudaStreamSynchronize(g->stream);
+    };
+    cudaError_t e = run(0, 0.0);
+    if (e != cudaSuccess) return cuda_fail(e, "metrics pass 0");
+    const double m = h[1];
+    const double mean = m > 0 ? h[0] / m : 0.0;
+    const double att = h[2], rep = h[3];
+    e = run(1, mean);
+    if (e != cudaSuccess) return cuda_fail(e, "metrics pass 1");
+    const double var = m > 0 ? h[0] / m : 0.0;
+    out->edge_mean = mean;
+    out->edge_std = sqrt(var);
+    out->edge_cv = mean > 0 ? out->edge_std / mean : 0.0;
+    out->rep_total = rep;
+    out->att_total = att;
+    out->rep_att_ratio = att > 0 ? rep / att : 0.0;
+    return GILA_OK;
+}
+
+gila_status bbox_aspect(gila_graph* g, int precision, const void* pos, double* aspect)
+{
+    gila_status s = ensure_red(g, (size_t)kRedBlocks * 4 + 8);
+    if (s != GILA_OK) return s;
+    const int blocks = 64;
+    if (precision == GILA_FP64)
+        bbox_kernel<double><<<blocks, kRedThreads, 0, g->stream>>>(g->n, pos, g->red);
+    else
+        bbox_kernel<float><<<blocks, kRedThreads, 0, g->stream>>>(g->n, pos, g->red);
+    count_launch();
+    std::vector<double> h(blocks * 4);
+    GILA_CUDA(cudaMemcpyAsync(h.data(), g->red, sizeof(double) * blocks * 4,
+                              cudaMemcpyDeviceToHost, g->stream));
+    GILA_CUDA(cudaStreamSynchronize(g->stream));
+    double x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+    for (int b = 0; b < blocks; ++b) {
+        x0 = std::min(x0, h[b * 4 + 0]);
+        x1 = std::max(x1, h[b * 4 + 1]);
+        y0 = std::min(y0, h[b * 4 + 2]);
+        y1 = std::max(y1, h[b * 4 + 3]);
+    }
+    const double w = x1 - x0, hh = y1 - y0;
+    *aspect = (w > 0 && hh > 0) ? hh / w : 1.0;
+    return GILA_OK;
+}
+
+gila_status convert_positions(gila_graph* g, int precision, const double* src, void* dst,
+                              bool to_device_type)
+{
+    // FP64 placements need no conversion; callers copy them directly.
+    if (precision == GILA_FP64) return GILA_OK;
+    const int64_t n = g->n;
+    if (n == 0) return GILA_OK;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (to_device_type)
+        to_float2_kernel<<<grid, 256, 0, g->stream>>>(n, src, (float2*)dst);
+    else
+        from_float2_kernel<<<grid, 256, 0, g->stream>>>(n, (const float2*)dst, (double*)src);
+    count_launch();
+    GILA_CUDA(cudaGetLastError());
+    return GILA_OK;
+}
+
+void free_layout(gila_graph* g)
+{
+    cudaFree(g->pos[0]);
+    cudaFree(g->pos[1]);
+    cudaFree(g->stage);
+    cudaFree(g->red);
+    g->pos[0] = g->pos[1] = nullptr;
+    g->stage = nullptr;
+    g->red = nullptr;
+    g->pos_cap[0] = g->pos_cap[1] = 0;
+    g->stage_cap = 0;
+    g->red_cap = 0;
+}
+
+}  // namespace gila

@@ -1,0 +1,277 @@
+"""Python binding of libgila (ctypes): argument marshalling only.
+
+Every function here has the name of the C entry point it calls (see
+include/gila.h) and does no arithmetic of the method: all compute runs in
+the CUDA kernels of the library. Device placements are torch CUDA tensors
+(float32 [n, 2] in the FP32 modes, float64 [n, 2] in FP64); work is issued
+on torch's current CUDA stream. There is no CPU fallback: if libgila.so is
+missing the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgila.so")
+
+GILA_OK = 0
+GILA_EINVAL = 1
+GILA_ENOMEM = 2
+GILA_EBUDGET = 3
+GILA_ETIMEDOUT = 4
+GILA_ECUDA = 5
+GILA_EBUSY = 6
+GILA_ESTATE = 7
+
+GILA_FP32 = 0
+GILA_FP64 = 1
+GILA_FP32_COMPENSATED = 2
+
+GILA_COOL_LINEAR = 0
+GILA_COOL_GEOMETRIC = 1
+
+GILA_GRAPH_VALIDATE = 1
+GILA_GRAPH_SIMPLIFY = 2
+
+_STATUS = {0: "GILA_OK", 1: "GILA_EINVAL", 2: "GILA_ENOMEM", 3: "GILA_EBUDGET",
+           4: "GILA_ETIMEDOUT", 5: "GILA_ECUDA", 6: "GILA_EBUSY", 7: "GILA_ESTATE"}
+
+
+class gila_params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("iters", ctypes.c_int32), ("d", ctypes.c_double),
+                ("t0", ctypes.c_double), ("schedule", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("q", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class gila_metrics(ctypes.Structure):
+    _fields_ = [("edge_mean", ctypes.c_double), ("edge_std", ctypes.c_double),
+                ("edge_cv", ctypes.c_double), ("rep_total", ctypes.c_double),
+                ("att_total", ctypes.c_double), ("rep_att_ratio", ctypes.c_double)]
+
+
+class GilaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+D = ctypes.c_double
+PP = ctypes.POINTER(gila_params)
+SIGNATURES = [
+    ("gila_params_default", None, [PP]),
+    ("gila_csr_validate", ctypes.c_int, [I64, P, P]),
+    ("gila_graph_create", ctypes.c_int, [I64, P, P, I32, ctypes.POINTER(P)]),
+    ("gila_graph_destroy", None, [P]),
+    ("gila_graph_set_stream", ctypes.c_int, [P, P]),
+    ("gila_graph_info", ctypes.c_int, [P, P, P, P, P]),
+    ("gila_build_khop", ctypes.c_int, [P, I32, ctypes.POINTER(I64)]),
+    ("gila_khop_reset", ctypes.c_int, [P]),
+    ("gila_khop_export", ctypes.c_int, [P, P, P]),
+    ("gila_layout_step", ctypes.c_int, [P, PP, D, P, P, P]),
+    ("gila_layout_run_device", ctypes.c_int, [P, PP, P]),
+    ("gila_layout_run", ctypes.c_int, [P, PP, P, P]),
+    ("gila_layout_metrics", ctypes.c_int, [P, PP, P, ctypes.POINTER(gila_metrics)]),
+    ("gila_temperature", D, [PP, D, I32]),
+    ("gila_profile_enable", ctypes.c_int, [P, I32]),
+    ("gila_profile_read", ctypes.c_int, [P, P, P, P, P]),
+    ("gila_last_error", ctypes.c_char_p, []),
+    ("gila_kernel_launches", ctypes.c_int64, []),
+]
+
+
+def load(path: str | None = None):
+    """Load libgila.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"libgila.so not found at {p}: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(p)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int):
+    if status != GILA_OK:
+        raise GilaError(status, load().gila_last_error().decode(errors="replace"))
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_ptr(t) -> int:
+    """Device address of a torch tensor or an int address."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _torch_stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def params(k=2, iters=300, d=1.0, t0=0.0, schedule=GILA_COOL_LINEAR, p=2, q=1,
+           precision=GILA_FP32) -> gila_params:
+    return gila_params(int(k), int(iters), float(d), float(t0), int(schedule), int(p), int(q),
+                       int(precision))
+
+
+def gila_params_default() -> gila_params:
+    prm = gila_params()
+    load().gila_params_default(ctypes.byref(prm))
+    return prm
+
+
+def gila_csr_validate(n, row_ptr, col_idx) -> int:
+    """Host-only CSR check; returns the status (0 = valid)."""
+    row = _np(row_ptr, np.int64)
+    col = _np(col_idx, np.int32)
+    return load().gila_csr_validate(int(n), _ptr(row), _ptr(col))
+
+
+def gila_kernel_launches() -> int:
+    return load().gila_kernel_launches()
+
+
+def gila_last_error() -> str:
+    return load().gila_last_error().decode(errors="replace")
+
+
+def gila_graph_create(n, row_ptr, col_idx, flags=0) -> int:
+    row = _np(row_ptr, np.int64)
+    col = _np(col_idx, np.int32)
+    h = ctypes.c_void_p()
+    _check(load().gila_graph_create(int(n), _ptr(row), _ptr(col), int(flags), ctypes.byref(h)))
+    return h.value
+
+
+def gila_graph_destroy(g) -> None:
+    if g:
+        load().gila_graph_destroy(g)
+
+
+def gila_graph_set_stream(g, stream=None) -> None:
+    """stream: a cudaStream_t address (int); None = torch's current stream."""
+    s = _torch_stream() if stream is None else stream
+    _check(load().gila_graph_set_stream(g, s))
+
+
+def gila_graph_info(g) -> dict:
+    n, nnz, kb, nk = I64(), I64(), I32(), I64()
+    _check(load().gila_graph_info(g, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(kb),
+                                  ctypes.byref(nk)))
+    return {"n": n.value, "nnz_adj": nnz.value, "k_built": kb.value, "nnz_khop": nk.value}
+
+
+def gila_build_khop(g, k) -> int:
+    nnz = I64()
+    _check(load().gila_build_khop(g, int(k), ctypes.byref(nnz)))
+    return nnz.value
+
+
+def gila_khop_reset(g) -> None:
+    _check(load().gila_khop_reset(g))
+
+
+def gila_khop_export(g):
+    info = gila_graph_info(g)
+    krow = np.zeros(info["n"] + 1, dtype=np.int64)
+    kcol = np.zeros(max(info["nnz_khop"], 1), dtype=np.int32)
+    _check(load().gila_khop_export(g, _ptr(krow), _ptr(kcol)))
+    return krow, kcol[: info["nnz_khop"]]
+
+
+def gila_layout_step(g, prm, t, pos_in, pos_out, disp_out=None) -> None:
+    _check(load().gila_layout_step(g, ctypes.byref(prm), float(t), _dev_ptr(pos_in),
+                                   _dev_ptr(pos_out), _dev_ptr(disp_out)))
+
+
+def gila_layout_run_device(g, prm, pos) -> None:
+    _check(load().gila_layout_run_device(g, ctypes.byref(prm), _dev_ptr(pos)))
+
+
+def gila_layout_run(g, prm, pos_in, pos_out=None) -> np.ndarray:
+    """Host placement in (float64 [n, 2]), host placement out."""
+    src = _np(pos_in, np.float64)
+    out = np.empty_like(src) if pos_out is None else pos_out
+    _check(load().gila_layout_run(g, ctypes.byref(prm), _ptr(src), _ptr(out)))
+    return out
+
+
+def gila_layout_metrics(g, prm, pos) -> dict:
+    m = gila_metrics()
+    _check(load().gila_layout_metrics(g, ctypes.byref(prm), _dev_ptr(pos), ctypes.byref(m)))
+    return {f: getattr(m, f) for f, _ in gila_metrics._fields_}
+
+
+def gila_temperature(prm, t0, i) -> float:
+    return load().gila_temperature(ctypes.byref(prm), float(t0), int(i))
+
+
+def gila_profile_enable(g, on=True) -> None:
+    _check(load().gila_profile_enable(g, 1 if on else 0))
+
+
+def gila_profile_read(g) -> dict:
+    b, bms, it, ims = I64(), D(), I64(), D()
+    _check(load().gila_profile_read(g, ctypes.byref(b), ctypes.byref(bms), ctypes.byref(it),
+                                    ctypes.byref(ims)))
+    return {"builds": b.value, "build_ms": bms.value, "iter_launches": it.value,
+            "iter_ms": ims.value}
+
+
+class Graph:
+    """Owning wrapper of a gila_graph handle bound to torch's current stream."""
+
+    def __init__(self, n, row_ptr, col_idx, flags=0):
+        self.n = int(n)
+        self.handle = gila_graph_create(n, row_ptr, col_idx, flags)
+        gila_graph_set_stream(self.handle)
+
+    @classmethod
+    def from_inputs(cls, g, flags=0):
+        return cls(g.n, g.row_ptr, g.col_idx, flags)
+
+    def close(self):
+        if self.handle:
+            gila_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

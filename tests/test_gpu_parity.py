@@ -1,0 +1,340 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (element by element on the same seeded inputs):
+  k-hop lists        bit-exact (sorted rows, same offsets)
+  one step, FP32     max |disp_gpu - disp_oracle| <= 1e-4 max |disp_oracle|
+  one step, FP64     max |disp_gpu - disp_oracle| <= 1e-12 max |disp_oracle|
+  whole runs         edge-length CV and repulsive/attractive ratio within 2%
+The FP32 step is compared from the FP32-rounded placement, so both sides
+start from identical coordinates.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+import oracle as O
+from paper_1606_02162_gb300 import gila as G
+from paper_1606_02162_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {G.GILA_FP32: 1e-4, G.GILA_FP32_COMPENSATED: 1e-4, G.GILA_FP64: 1e-12}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+    import torch
+    torch.cuda.set_device(0)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dt(prec):
+    t = _torch()
+    return t.float64 if prec == G.GILA_FP64 else t.float32
+
+
+def gpu_khop(g, k):
+    with G.Graph.from_inputs(g) as h:
+        nnz = G.gila_build_khop(h.handle, k)
+        krow, kcol = G.gila_khop_export(h.handle)
+    assert nnz == krow[-1]
+    return krow, kcol
+
+
+def gpu_step(g, k, pos, t, prec, d=1.0, p=2, q=1):
+    torch = _torch()
+    with G.Graph.from_inputs(g) as h:
+        p_in = torch.tensor(pos, dtype=_dt(prec), device="cuda")
+        p_out = torch.empty_like(p_in)
+        disp = torch.empty_like(p_in)
+        G.gila_layout_step(h.handle, G.params(k=k, d=d, p=p, q=q, precision=prec), t, p_in, p_out,
+                           disp)
+        torch.cuda.synchronize()
+        return (p_in.double().cpu().numpy(), p_out.double().cpu().numpy(),
+                disp.double().cpu().numpy())
+
+
+KHOP_CASES = [
+    ("grid32", lambda: I.grid(32, 32), 2),
+    ("mesh60", lambda: I.tri_mesh(60, 60), 3),
+    ("ba5k_k2", lambda: I.barabasi_albert(5000, 3, 1), 2),
+    ("ba5k_k3", lambda: I.barabasi_albert(5000, 3, 1), 3),
+    ("er3k_k4", lambda: I.erdos_renyi(3000, 4.0, 2), 4),
+    ("tree2k_k5", lambda: I.random_tree(2000, 3), 5),
+    ("cl5k_k2", lambda: I.chung_lu(5000, 2.3, 8.0, 20000, 4), 2),
+    ("star2k_k1", lambda: I.star(2000), 1),
+    ("star2k_k2", lambda: I.star(2000), 2),
+    ("k700_k1", lambda: I.complete(700), 1),
+    ("path1k_k7", lambda: I.path(1000), 7),
+    ("isolated", lambda: I.csr_from_edges(50, [0, 3, 7], [1, 4, 8]), 3),
+    ("noedges", lambda: I.csr_from_edges(10, [], []), 2),
+]
+
+
+@pytest.mark.parametrize("name,maker,k", KHOP_CASES, ids=[c[0] for c in KHOP_CASES])
+def test_khop_bit_exact(name, maker, k):
+    g = maker()
+    krow, kcol = gpu_khop(g, k)
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, k)
+    assert np.array_equal(krow, okrow)
+    assert np.array_equal(kcol, okcol)
+
+
+def test_golden_grid_count():
+    krow, _ = gpu_khop(I.grid(32, 32), 2)
+    assert krow[-1] == 11652
+
+
+def test_khop_cache_and_rebuild():
+    g = I.barabasi_albert(3000, 3, 5)
+    with G.Graph.from_inputs(g) as h:
+        n2 = G.gila_build_khop(h.handle, 2)
+        a = G.gila_khop_export(h.handle)
+        assert G.gila_build_khop(h.handle, 2) == n2
+        n3 = G.gila_build_khop(h.handle, 3)
+        assert n3 > n2
+        assert G.gila_build_khop(h.handle, 2) == n2
+        b = G.gila_khop_export(h.handle)
+        G.gila_khop_reset(h.handle)
+        assert G.gila_graph_info(h.handle)["k_built"] == 0
+        assert G.gila_build_khop(h.handle, 2) == n2
+        c = G.gila_khop_export(h.handle)
+    for x, y in ((a, b), (a, c)):
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+
+
+STEP_CASES = [
+    ("grid32_k2", lambda: I.grid(32, 32), 2),
+    ("ba20k_k2", lambda: I.barabasi_albert(20000, 3, 7), 2),
+    ("ba5k_k3", lambda: I.barabasi_albert(5000, 3, 1), 3),
+    ("cl20k_k2", lambda: I.chung_lu(20000, 2.3, 8.0, 80000, 3), 2),
+    ("mesh100_k3", lambda: I.tri_mesh(100, 100), 3),
+    ("star70k_k1", lambda: I.star(70000), 1),
+    ("k700_k1", lambda: I.complete(700), 1),
+]
+
+
+@pytest.mark.parametrize("prec", [G.GILA_FP32, G.GILA_FP32_COMPENSATED, G.GILA_FP64],
+                         ids=["fp32", "fp32c", "fp64"])
+@pytest.mark.parametrize("name,maker,k", STEP_CASES, ids=[c[0] for c in STEP_CASES])
+def test_step_parity(name, maker, k, prec):
+    g = maker()
+    pos = I.uniform_positions(g.n, 11)
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, k)
+    for t in (0.1 * math.sqrt(g.n), 1e30):
+        base, new, disp = gpu_step(g, k, pos, t, prec)
+        _, odisp = O.step(g.n, g.row_ptr, g.col_idx, okrow, okcol, base, t)
+        scale = np.abs(odisp).max()
+        err = np.abs(disp - odisp).max()
+        assert err <= TOL[prec] * scale, (t, err, scale)
+        assert np.array_equal(new, (base.astype(_np_dt(prec)) + disp.astype(_np_dt(prec))).astype(np.float64))
+
+
+def _np_dt(prec):
+    return np.float64 if prec == G.GILA_FP64 else np.float32
+
+
+@pytest.mark.parametrize("p,q", [(3, 2), (0, 1), (1, 3)])
+@pytest.mark.parametrize("prec", [G.GILA_FP32, G.GILA_FP64], ids=["fp32", "fp64"])
+def test_step_parity_generic_exponents(p, q, prec):
+    g = I.barabasi_albert(4000, 3, 9)
+    k, d = 2, 1.7
+    pos = I.uniform_positions(g.n, 3)
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, k)
+    t = 1e30
+    base, _, disp = gpu_step(g, k, pos, t, prec, d=d, p=p, q=q)
+    _, odisp = O.step(g.n, g.row_ptr, g.col_idx, okrow, okcol, base, t, d=d, p=p, q=q)
+    assert np.abs(disp - odisp).max() <= TOL[prec] * np.abs(odisp).max()
+
+
+@pytest.mark.parametrize("name,maker,k", [
+    ("grid32_k2", lambda: I.grid(32, 32), 2),
+    ("ba20k_k3", lambda: I.barabasi_albert(20000, 3, 4), 3),
+])
+def test_fp64_first_ten_iterations(name, maker, k):
+    """FP64 mode over the first 10 iterations of a linear-cooling run: at each
+    iteration both sides step from the oracle's placement (identical
+    positions) and the moves agree within 1e-12 of the largest move. The
+    free-running trajectories are also followed: rounding-order differences
+    of one ulp grow with the dynamics (about 3x per iteration on the grid),
+    so they are held to a looser bound that states that growth."""
+    torch = _torch()
+    g = maker()
+    pos = I.uniform_positions(g.n, 1)
+    iters = 100
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, k)
+    prm = G.params(k=k, iters=iters, precision=G.GILA_FP64)
+    t0 = 0.1 * math.sqrt(g.n)
+    with G.Graph.from_inputs(g) as h:
+        a = torch.tensor(pos, dtype=torch.float64, device="cuda")
+        b = torch.empty_like(a)
+        free_a = a.clone()
+        free_b = torch.empty_like(a)
+        disp = torch.empty_like(a)
+        ref = pos.copy()
+        for i in range(10):
+            t = G.gila_temperature(prm, t0, i)
+            assert t == O.temperature(O.SCHED_LINEAR, t0, i, iters)
+            a.copy_(torch.from_numpy(ref))
+            G.gila_layout_step(h.handle, prm, t, a, b, disp)
+            G.gila_layout_step(h.handle, prm, t, free_a, free_b)
+            ref, odisp = O.step(g.n, g.row_ptr, g.col_idx, okrow, okcol, ref, t)
+            scale = np.abs(odisp).max()
+            assert np.abs(disp.cpu().numpy() - odisp).max() <= 1e-12 * scale, i
+            free_a, free_b = free_b, free_a
+            drift = np.abs(free_a.cpu().numpy() - ref).max()
+            assert drift <= 1e-15 * np.abs(ref).max() * 8.0 ** (i + 1), (i, drift)
+
+
+def test_run_device_equals_step_loop():
+    torch = _torch()
+    g = I.barabasi_albert(3000, 3, 2)
+    pos = I.uniform_positions(g.n, 4)
+    for prec in (G.GILA_FP32, G.GILA_FP64):
+        prm = G.params(k=2, iters=7, precision=prec)
+        with G.Graph.from_inputs(g) as h:
+            x = torch.tensor(pos, dtype=_dt(prec), device="cuda")
+            G.gila_layout_run_device(h.handle, prm, x)
+            a = torch.tensor(pos, dtype=_dt(prec), device="cuda")
+            b = torch.empty_like(a)
+            t0 = 0.1 * math.sqrt(g.n)
+            for i in range(7):
+                G.gila_layout_step(h.handle, prm, G.gila_temperature(prm, t0, i), a, b)
+                a, b = b, a
+            torch.cuda.synchronize()
+            assert torch.equal(x, a)
+            host = G.gila_layout_run(h.handle, prm, pos)
+            want = a.double().cpu().numpy()
+            assert np.array_equal(host, want)
+
+
+def test_determinism():
+    g = I.chung_lu(30000, 2.3, 8.0, 120000, 8)
+    pos = I.uniform_positions(g.n, 2)
+    for prec in (G.GILA_FP32, G.GILA_FP32_COMPENSATED, G.GILA_FP64):
+        prm = G.params(k=2, iters=20, precision=prec)
+        outs = []
+        for _ in range(2):
+            with G.Graph.from_inputs(g) as h:
+                outs.append(G.gila_layout_run(h.handle, prm, pos))
+        assert np.array_equal(outs[0], outs[1])
+
+
+def test_whole_run_grid_fp64():
+    """32x32 grid, k=2, d=1, 100 iterations, linear cooling from 0.1 sqrt(n), FP64."""
+    torch = _torch()
+    g = I.grid(32, 32)
+    pos = I.uniform_positions(g.n, 1)
+    prm = G.params(k=2, iters=100, precision=G.GILA_FP64)
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, 2)
+    ref = O.run(g.n, g.row_ptr, g.col_idx, okrow, okcol, pos, 100)
+    mo = O.metrics(g.n, g.row_ptr, g.col_idx, okrow, okcol, ref)
+    with G.Graph.from_inputs(g) as h:
+        out = G.gila_layout_run(h.handle, prm, pos)
+        m = G.gila_layout_metrics(h.handle, prm, torch.tensor(out, device="cuda"))
+    mg = O.metrics(g.n, g.row_ptr, g.col_idx, okrow, okcol, out)
+    for key in ("edge_cv", "rep_att_ratio"):
+        assert abs(mg[key] - mo[key]) <= 0.02 * abs(mo[key]), key
+        assert m[key] == pytest.approx(mg[key], rel=1e-12), key
+
+
+@pytest.mark.parametrize("prec", [G.GILA_FP32, G.GILA_FP32_COMPENSATED], ids=["fp32", "fp32c"])
+def test_whole_run_ba_fp32_quality(prec):
+    g = I.barabasi_albert(20000, 3, 2)
+    pos = I.uniform_positions(g.n, 2)
+    k, iters = 2, 100
+    prm = G.params(k=k, iters=iters, precision=prec)
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, k)
+    ref = O.run(g.n, g.row_ptr, g.col_idx, okrow, okcol, pos.astype(np.float32).astype(np.float64),
+                iters)
+    mo = O.metrics(g.n, g.row_ptr, g.col_idx, okrow, okcol, ref)
+    with G.Graph.from_inputs(g) as h:
+        out = G.gila_layout_run(h.handle, prm, pos)
+    mg = O.metrics(g.n, g.row_ptr, g.col_idx, okrow, okcol, out)
+    for key in ("edge_cv", "rep_att_ratio"):
+        assert abs(mg[key] - mo[key]) <= 0.02 * abs(mo[key]), (key, mg[key], mo[key])
+
+
+def test_metrics_kernel_matches_oracle():
+    torch = _torch()
+    g = I.barabasi_albert(8000, 3, 6)
+    pos = I.uniform_positions(g.n, 9)
+    for p, q in ((2, 1), (3, 2)):
+        prm = G.params(k=2, d=1.3, p=p, q=q, precision=G.GILA_FP64)
+        okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, 2)
+        mo = O.metrics(g.n, g.row_ptr, g.col_idx, okrow, okcol, pos, d=1.3, p=p, q=q)
+        with G.Graph.from_inputs(g) as h:
+            m = G.gila_layout_metrics(h.handle, prm, torch.tensor(pos, device="cuda"))
+        for key in mo:
+            assert m[key] == pytest.approx(mo[key], rel=1e-11), key
+
+
+def test_geometric_schedule_run():
+    g = I.grid(20, 12)
+    pos = I.uniform_positions(g.n, 5) * np.array([1.0, 0.5])
+    prm = G.params(k=2, iters=15, schedule=G.GILA_COOL_GEOMETRIC, precision=G.GILA_FP64, d=1.2)
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, 2)
+    ref = O.run(g.n, g.row_ptr, g.col_idx, okrow, okcol, pos, 15, d=1.2, schedule=O.SCHED_GEOM)
+    with G.Graph.from_inputs(g) as h:
+        out = G.gila_layout_run(h.handle, prm, pos)
+    assert np.abs(out - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_edge_cases():
+    torch = _torch()
+    # no vertices
+    with G.Graph(0, np.zeros(1, np.int64), np.zeros(0, np.int32)) as h:
+        assert G.gila_build_khop(h.handle, 2) == 0
+        out = G.gila_layout_run(h.handle, G.params(iters=3), np.zeros((0, 2)))
+        assert out.shape == (0, 2)
+    # one vertex, no edges: nothing moves
+    g = I.csr_from_edges(1, [], [])
+    with G.Graph.from_inputs(g) as h:
+        out = G.gila_layout_run(h.handle, G.params(iters=3), np.array([[0.5, 0.25]]))
+        assert np.array_equal(out, [[0.5, 0.25]])
+    # all vertices on one point: every pair is at distance 0 and contributes nothing
+    g = I.complete(5)
+    with G.Graph.from_inputs(g) as h:
+        pos = np.ones((5, 2))
+        for prec in (G.GILA_FP32, G.GILA_FP64):
+            out = G.gila_layout_run(h.handle, G.params(k=1, iters=4, precision=prec), pos)
+            assert np.array_equal(out, pos)
+    # zero temperature: nothing moves
+    g = I.barabasi_albert(500, 2, 1)
+    pos = I.uniform_positions(g.n, 1)
+    base, new, disp = gpu_step(g, 2, pos, 0.0, G.GILA_FP64)
+    assert np.array_equal(new, base) and not disp.any()
+    # bad arguments come back as GILA_EINVAL, not a crash
+    with G.Graph.from_inputs(g) as h:
+        x = torch.tensor(pos, device="cuda")
+        for bad in (dict(k=0), dict(d=0.0), dict(p=9), dict(precision=7), dict(iters=-1)):
+            with pytest.raises(G.GilaError) as e:
+                G.gila_layout_run_device(h.handle, G.params(**bad), x)
+            assert e.value.status == G.GILA_EINVAL
+        with pytest.raises(G.GilaError):
+            G.gila_layout_step(h.handle, G.params(), 1.0, x, x)
+
+
+def test_graph_create_flags():
+    # a CSR with a self-loop, a repeat and a missing reverse entry
+    row = np.array([0, 3, 4, 5], dtype=np.int64)
+    col = np.array([0, 1, 1, 2, 1], dtype=np.int32)
+    with pytest.raises(G.GilaError) as e:
+        G.gila_graph_create(3, row, col, G.GILA_GRAPH_VALIDATE)
+    assert e.value.status == G.GILA_EINVAL
+    h = G.gila_graph_create(3, row, col, G.GILA_GRAPH_SIMPLIFY)
+    try:
+        info = G.gila_graph_info(h)
+        assert info["nnz_adj"] == 4  # edges 0-1 and 1-2, both directions
+        G.gila_build_khop(h, 1)
+        krow, kcol = G.gila_khop_export(h)
+        assert krow.tolist() == [0, 1, 3, 4] and kcol.tolist() == [1, 0, 2, 1]
+    finally:
+        G.gila_graph_destroy(h)
