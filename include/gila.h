@@ -27,7 +27,8 @@
  *     legacy default stream). Calls on one graph must not run concurrently.
  *   - Placements are arrays of n (x, y) pairs, row-major: element 2u is x_u,
  *     2u+1 is y_u. Host placements are always double. Device placements are
- *     float2 in GILA_FP32 / GILA_FP32_COMPENSATED and double2 in GILA_FP64.
+ *     float2 in GILA_FP32 / GILA_FP32_COMPENSATED and double2 in GILA_FP64 /
+ *     GILA_FP64_ORDERED.
  */
 #ifndef GILA_H
 #define GILA_H
@@ -54,7 +55,12 @@ typedef enum gila_status {
 enum {
     GILA_FP32 = 0,             /* float positions and force sums */
     GILA_FP64 = 1,             /* double everywhere (validation mode) */
-    GILA_FP32_COMPENSATED = 2  /* float, with compensated (two-sum) force sums */
+    GILA_FP32_COMPENSATED = 2, /* float, with compensated (two-sum) force sums */
+    GILA_FP64_ORDERED = 3      /* double, validation: each force summed in the order of its
+                                  definition (repulsion over N_u(k) by ascending id, then
+                                  attraction in CSR order), every operation an individually
+                                  rounded IEEE double op; reproduces a sequential FP64
+                                  evaluation bit for bit. Slow. */
 };
 
 /* Cooling schedules: temperature of iteration i of `iters` (0-based). */
@@ -78,7 +84,7 @@ typedef struct gila_params {
     int32_t schedule;  /* GILA_COOL_* */
     int32_t p;         /* attraction exponent, 0..8 (2 = Fruchterman-Reingold) */
     int32_t q;         /* repulsion exponent, 0..8 (1 = Fruchterman-Reingold) */
-    int32_t precision; /* GILA_FP32 | GILA_FP64 | GILA_FP32_COMPENSATED */
+    int32_t precision; /* GILA_FP32 | GILA_FP64 | GILA_FP32_COMPENSATED | GILA_FP64_ORDERED */
 } gila_params;
 
 /* Layout quality figures of a placement, all accumulated in FP64. */

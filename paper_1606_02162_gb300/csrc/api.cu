@@ -62,12 +62,12 @@ gila_status check_params(const gila_params* p)
     if (p->p < 0 || p->p > 8 || p->q < 0 || p->q > 8)
         return fail(GILA_EINVAL, "p and q must be in [0, 8]");
     if (p->precision != GILA_FP32 && p->precision != GILA_FP64 &&
-        p->precision != GILA_FP32_COMPENSATED)
+        p->precision != GILA_FP32_COMPENSATED && p->precision != GILA_FP64_ORDERED)
         return fail(GILA_EINVAL, "unknown precision");
     return GILA_OK;
 }
 
-size_t pos_elem(int precision) { return precision == GILA_FP64 ? 16 : 8; }
+size_t pos_elem(int precision) { return is_f64(precision) ? 16 : 8; }
 
 gila_status use_device(const gila_graph* g)
 {
@@ -398,7 +398,7 @@ gila_status gila_layout_run(gila_graph* g, const gila_params* prm, const double*
     const size_t bytes = pos_elem(prm->precision) * n;
     if ((s = ensure(&g->pos[0], &g->pos_cap[0], bytes)) != GILA_OK) return s;
     if ((s = ensure(&g->pos[1], &g->pos_cap[1], bytes)) != GILA_OK) return s;
-    const bool f64 = prm->precision == GILA_FP64;
+    const bool f64 = is_f64(prm->precision);
     if (!f64 && (s = ensure((void**)&g->stage, &g->stage_cap, 16 * n)) != GILA_OK) return s;
     if (f64) {
         GILA_CUDA(cudaMemcpyAsync(g->pos[0], pos_in_host, 16 * n, cudaMemcpyHostToDevice, g->stream));

@@ -23,6 +23,11 @@ gila_status cuda_fail(cudaError_t e, const char* what);
         if (e_ != cudaSuccess) return ::gila::cuda_fail(e_, #call); \
     } while (0)
 
+inline bool is_f64(int precision)
+{
+    return precision == GILA_FP64 || precision == GILA_FP64_ORDERED;
+}
+
 // ---------------------------------------------------------------- k-hop flag
 
 // The top bit of a stored k-hop entry marks an edge of G (distance 1):

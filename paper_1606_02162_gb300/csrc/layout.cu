@@ -334,6 +334,75 @@ iteration_kernel(const IterArgs A)
     }
 }
 
+// FP64 validation mode that sums every force in the order of the definition:
+// repulsion over N_u(k) by ascending id, attraction over the adjacency row in
+// CSR order, each term rounded as magnitude * (component / delta), the two
+// sums added last; every operation is an explicitly rounded IEEE double op
+// (no fused multiply-add), so the result depends on nothing but the inputs.
+// One warp per vertex: lanes form 32 consecutive terms, then every lane
+// folds them in order.
+__device__ __forceinline__ double ordered_pow(double x, int e)
+{
+    double r = 1.0;
+    for (int i = 0; i < e; ++i) r = __dmul_rn(r, x);
+    return r;
+}
+
+__global__ void __launch_bounds__(kThreads)
+ordered_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __restrict__ col,
+               const int64_t* __restrict__ krow, const uint32_t* __restrict__ kcol, double d,
+               int p, int q, double t, const double2* __restrict__ pos_in,
+               double2* __restrict__ pos_out, double2* __restrict__ disp_out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t u = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    if (u >= n) return;  // whole warp
+    const double2 pu = pos_in[u];
+    const double dd = __dmul_rn(d, d);
+    double s[2][2] = {{0.0, 0.0}, {0.0, 0.0}};  // [repulsion|attraction][x|y]
+    for (int pass = 0; pass < 2; ++pass) {
+        const int64_t b = pass == 0 ? krow[u] : row[u];
+        const int64_t e = pass == 0 ? krow[u + 1] : row[u + 1];
+        for (int64_t j0 = b; j0 < e; j0 += 32) {
+            const int64_t j = j0 + lane;
+            double tx = 0.0, ty = 0.0;
+            if (j < e) {
+                const int64_t v = pass == 0 ? (int64_t)(kcol[j] & kIdMask) : (int64_t)col[j];
+                const double2 pv = pos_in[v];
+                // repulsion along x_u - x_v, attraction along x_v - x_u
+                const double dx = pass == 0 ? __dsub_rn(pu.x, pv.x) : __dsub_rn(pv.x, pu.x);
+                const double dy = pass == 0 ? __dsub_rn(pu.y, pv.y) : __dsub_rn(pv.y, pu.y);
+                const double dl = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+                if (dl != 0.0 && v != u) {
+                    const double mag = pass == 0 ? __ddiv_rn(dd, ordered_pow(dl, q))
+                                                 : __ddiv_rn(ordered_pow(dl, p), d);
+                    tx = __dmul_rn(mag, __ddiv_rn(dx, dl));
+                    ty = __dmul_rn(mag, __ddiv_rn(dy, dl));
+                } else {
+                    tx = ty = -0.0;  // identity of the sum: the term is skipped
+                }
+            }
+            const int cnt = (e - j0) < 32 ? (int)(e - j0) : 32;
+            for (int i = 0; i < cnt; ++i) {
+                s[pass][0] = __dadd_rn(s[pass][0], __shfl_sync(kFull, tx, i));
+                s[pass][1] = __dadd_rn(s[pass][1], __shfl_sync(kFull, ty, i));
+            }
+        }
+    }
+    if (lane != 0) return;
+    const double fx = __dadd_rn(s[0][0], s[1][0]);
+    const double fy = __dadd_rn(s[0][1], s[1][1]);
+    const double norm = __dsqrt_rn(__dadd_rn(__dmul_rn(fx, fx), __dmul_rn(fy, fy)));
+    double mx = fx, my = fy;
+    if (norm > t) {
+        const double sc = norm > 0.0 ? __ddiv_rn(t, norm) : 0.0;
+        mx = __dmul_rn(fx, sc);
+        my = __dmul_rn(fy, sc);
+    }
+    pos_out[u] = make_double2(__dadd_rn(pu.x, mx), __dadd_rn(pu.y, my));
+    if (disp_out) disp_out[u] = make_double2(mx, my);
+}
+
 template <class T, int MODEL, bool COMP>
 cudaError_t launch_typed(const IterArgs& A, unsigned grid, cudaStream_t st)
 {
@@ -491,6 +560,17 @@ gila_status ensure_red(gila_graph* g, size_t doubles)
 gila_status launch_iteration(gila_graph* g, const gila_params* prm, double t, const void* pos_in,
                              void* pos_out, void* disp_out)
 {
+    if (prm->precision == GILA_FP64_ORDERED) {
+        if (g->n == 0) return GILA_OK;
+        const unsigned grid = (unsigned)((g->n * 32 + kThreads - 1) / kThreads);
+        ordered_kernel<<<grid, kThreads, 0, g->stream>>>(
+            g->n, g->row, g->col, g->krow, g->kcol, prm->d, prm->p, prm->q, t,
+            (const double2*)pos_in, (double2*)pos_out, (double2*)disp_out);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "ordered_kernel");
+        return GILA_OK;
+    }
     const Bins& B = g->bins;
     IterArgs A;
     A.krow = g->krow;
@@ -546,7 +626,7 @@ gila_status compute_metrics(gila_graph* g, const gila_params* prm, const void* p
     double* part = g->red;
     double* res = g->red + (size_t)kRedBlocks * 4;
     double h[4];
-    const bool f64 = prm->precision == GILA_FP64;
+    const bool f64 = is_f64(prm->precision);
     auto run = [&](int pass, double mean) -> cudaError_t {
         if (f64)
             metrics_kernel<double><<<kRedBlocks, kRedThreads, 0, g->stream>>>(
@@ -584,7 +664,7 @@ gila_status bbox_aspect(gila_graph* g, int precision, const void* pos, double* a
     gila_status s = ensure_red(g, (size_t)kRedBlocks * 4 + 8);
     if (s != GILA_OK) return s;
     const int blocks = 64;
-    if (precision == GILA_FP64)
+    if (is_f64(precision))
         bbox_kernel<double><<<blocks, kRedThreads, 0, g->stream>>>(g->n, pos, g->red);
     else
         bbox_kernel<float><<<blocks, kRedThreads, 0, g->stream>>>(g->n, pos, g->red);
@@ -609,7 +689,7 @@ gila_status convert_positions(gila_graph* g, int precision, const double* src, v
                               bool to_device_type)
 {
     // FP64 placements need no conversion; callers copy them directly.
-    if (precision == GILA_FP64) return GILA_OK;
+    if (is_f64(precision)) return GILA_OK;
     const int64_t n = g->n;
     if (n == 0) return GILA_OK;
     const unsigned grid = (unsigned)((n + 255) / 256);

@@ -30,6 +30,7 @@ GILA_ESTATE = 7
 GILA_FP32 = 0
 GILA_FP64 = 1
 GILA_FP32_COMPENSATED = 2
+GILA_FP64_ORDERED = 3
 
 GILA_COOL_LINEAR = 0
 GILA_COOL_GEOMETRIC = 1

@@ -37,7 +37,7 @@ def _torch():
 
 def _dt(prec):
     t = _torch()
-    return t.float64 if prec == G.GILA_FP64 else t.float32
+    return t.float64 if prec in (G.GILA_FP64, G.GILA_FP64_ORDERED) else t.float32
 
 
 def gpu_khop(g, k):
@@ -138,7 +138,7 @@ def test_step_parity(name, maker, k, prec):
 
 
 def _np_dt(prec):
-    return np.float64 if prec == G.GILA_FP64 else np.float32
+    return np.float64 if prec in (G.GILA_FP64, G.GILA_FP64_ORDERED) else np.float32
 
 
 @pytest.mark.parametrize("p,q", [(3, 2), (0, 1), (1, 3)])
@@ -227,22 +227,65 @@ def test_determinism():
         assert np.array_equal(outs[0], outs[1])
 
 
-def test_whole_run_grid_fp64():
-    """32x32 grid, k=2, d=1, 100 iterations, linear cooling from 0.1 sqrt(n), FP64."""
+def test_whole_run_grid_fp64_ordered_bit_exact():
+    """32x32 grid, k=2, d=1, 100 iterations, linear cooling from 0.1 sqrt(n),
+    FP64 in the ordered validation mode: the whole trajectory reproduces the
+    oracle's bit for bit, so the quality figures agree exactly."""
     torch = _torch()
     g = I.grid(32, 32)
     pos = I.uniform_positions(g.n, 1)
-    prm = G.params(k=2, iters=100, precision=G.GILA_FP64)
+    prm = G.params(k=2, iters=100, precision=G.GILA_FP64_ORDERED)
     okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, 2)
     ref = O.run(g.n, g.row_ptr, g.col_idx, okrow, okcol, pos, 100)
     mo = O.metrics(g.n, g.row_ptr, g.col_idx, okrow, okcol, ref)
     with G.Graph.from_inputs(g) as h:
         out = G.gila_layout_run(h.handle, prm, pos)
         m = G.gila_layout_metrics(h.handle, prm, torch.tensor(out, device="cuda"))
-    mg = O.metrics(g.n, g.row_ptr, g.col_idx, okrow, okcol, out)
+    assert np.array_equal(out, ref)
+    for key in mo:
+        assert m[key] == pytest.approx(mo[key], rel=1e-12), key
+
+
+@pytest.mark.parametrize("prec", [G.GILA_FP64, G.GILA_FP32], ids=["fp64", "fp32"])
+def test_whole_run_grid_ensemble(prec):
+    """The same grid run in the fast modes. A one-ulp change of a single
+    coordinate already moves the oracle's own 100-iteration layout by several
+    units and its edge-length CV by up to 7%, so single runs are compared
+    through the mean over 32 seeded placements (seed-to-seed spread of the
+    CV about 3%, of the ratio about 1%): both means within 2%."""
+    g = I.grid(32, 32)
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, 2)
+    prm = G.params(k=2, iters=100, precision=prec)
+    got, want = [], []
+    with G.Graph.from_inputs(g) as h:
+        for s in range(1, 33):
+            pos = I.uniform_positions(g.n, s)
+            out = G.gila_layout_run(h.handle, prm, pos)
+            ref = O.run(g.n, g.row_ptr, g.col_idx, okrow, okcol,
+                        pos.astype(np.float32).astype(np.float64) if prec == G.GILA_FP32 else pos,
+                        100)
+            got.append(O.metrics(g.n, g.row_ptr, g.col_idx, okrow, okcol, out))
+            want.append(O.metrics(g.n, g.row_ptr, g.col_idx, okrow, okcol, ref))
     for key in ("edge_cv", "rep_att_ratio"):
-        assert abs(mg[key] - mo[key]) <= 0.02 * abs(mo[key]), key
-        assert m[key] == pytest.approx(mg[key], rel=1e-12), key
+        a = np.mean([m[key] for m in got])
+        b = np.mean([m[key] for m in want])
+        assert abs(a - b) <= 0.02 * abs(b), (key, a, b)
+
+
+@pytest.mark.parametrize("name,maker,k", STEP_CASES, ids=[c[0] for c in STEP_CASES])
+def test_ordered_step_bit_exact(name, maker, k):
+    g = maker()
+    pos = I.uniform_positions(g.n, 11)
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, k)
+    for t in (0.1 * math.sqrt(g.n), 1e30):
+        base, new, disp = gpu_step(g, k, pos, t, G.GILA_FP64_ORDERED)
+        onew, odisp = O.step(g.n, g.row_ptr, g.col_idx, okrow, okcol, base, t)
+        assert np.array_equal(disp, odisp)
+        assert np.array_equal(new, onew)
+    # generic exponents and ideal length
+    base, new, disp = gpu_step(g, k, pos, 1e30, G.GILA_FP64_ORDERED, d=1.7, p=3, q=2)
+    _, odisp = O.step(g.n, g.row_ptr, g.col_idx, okrow, okcol, base, 1e30, d=1.7, p=3, q=2)
+    assert np.array_equal(disp, odisp)
 
 
 @pytest.mark.parametrize("prec", [G.GILA_FP32, G.GILA_FP32_COMPENSATED], ids=["fp32", "fp32c"])
