@@ -196,6 +196,35 @@ const char* gila_last_error(void);
  * graphs, all threads), for accounting of device work. */
 int64_t gila_kernel_launches(void);
 
+/* Sizes |N_v(k)| of every k-hop list, computed without allocating any
+ * memory. The paper has no counterpart: this is a service for callers that
+ * must not allocate device memory themselves or have it allocated for them,
+ * for example a serving process whose memory manager owns the whole device
+ * and decides admission by the bytes a graph's k-hop lists would need
+ * (it must learn that size before it may reserve anything), or a caller
+ * that cannot afford the device-wide synchronisation that cudaMalloc and
+ * cudaFree may imply while other streams are busy.
+ *
+ * Inputs are caller-owned device arrays: row_ptr_dev int64[n+1] and
+ * col_idx_dev int32[row_ptr[n]] in symmetric CSR form (as for
+ * gila_graph_create, unchecked). Output: counts_dev int64[n] (device, caller
+ * owned) receives |N_v(k)| for every v; *total_host (may be NULL) receives
+ * their sum. Work runs on cuda_stream (NULL = legacy default stream) and the
+ * call returns after it has finished.
+ *
+ * Scratch lives in one fixed device array inside the library (about 5.1 MiB,
+ * present on every device that loads the library until the process exits),
+ * which bounds n to at most 262,144 vertices: larger n returns GILA_EINVAL
+ * with a message. The call makes no cudaMalloc or cudaFree call and uses no
+ * allocating library routine. The first call on a device looks up the
+ * scratch address for that device (cudaGetSymbolAddress with the device
+ * current); make that first call before any stream capture. Every call
+ * reuses the same scratch: calls that overlap on the GPU (other threads,
+ * other streams) race and must be serialised by the caller. */
+gila_status gila_khop_count_noalloc(int64_t n, const int64_t* row_ptr_dev,
+                                    const int32_t* col_idx_dev, int32_t k, int64_t* counts_dev,
+                                    int64_t* total_host, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,6 +17,8 @@
 //   the force kernel, and rows are classed by length for scheduling.
 #include <algorithm>
 #include <climits>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "device_util.cuh"
@@ -676,4 +678,118 @@ gila_status build_khop(gila_graph* g, int k)
     return GILA_OK;
 }
 
+// ------------------------------------------------------------------------
+// k-hop list sizes without any allocation (gila_khop_count_noalloc).
+//
+// The same two counting kernels as above, with their scratch (overflow
+// queue, tier-2 bitmaps and visit lists, counters) in one file-scope device
+// array instead of cudaMalloc'd buffers. The array exists on every device
+// that loads the library, from load until exit.
+
+namespace {
+
+constexpr int64_t kNoAllocMaxN = int64_t(1) << 18;           // 262,144 vertices
+constexpr int kNoAllocT2Blocks = 4;                           // tier-2 blocks
+constexpr int64_t kNoAllocWords = kNoAllocMaxN / 32;          // bitmap words per block
+
+struct NoAllocScratch {
+    int32_t queue[kNoAllocMaxN];                        // 1 MiB
+    uint32_t bitmaps[kNoAllocT2Blocks * kNoAllocWords]; // 128 KiB, all zero between sources
+    int32_t lists[kNoAllocT2Blocks * kNoAllocMaxN];     // 4 MiB
+    int64_t total;
+    int qn;
+};
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+__global__ void __launch_bounds__(1024)
+sum_counts_kernel(const int64_t* __restrict__ counts, int64_t n, int64_t* __restrict__ out)
+{
+    __shared__ int64_t wt[1024 / 32 + 1];
+    int64_t s = 0;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) s += counts[i];
+    int64_t total;
+    block_inclusive_scan<int64_t, 1024>(s, wt, &total);
+    if (threadIdx.x == 0) *out = total;
+}
+
+// Device address of the scratch array, looked up once per device with that
+// device current (host code cannot use the array's name as an address).
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+NoAllocScratch* g_noalloc_ptr[kMaxDevices] = {};
+
+gila_status noalloc_scratch(int device, NoAllocScratch** out)
+{
+    if (device < 0 || device >= kMaxDevices) return fail(GILA_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[device] = (NoAllocScratch*)p;
+    }
+    *out = g_noalloc_ptr[device];
+    return GILA_OK;
+}
+
+}  // namespace
 }  // namespace gila
+
+extern "C" gila_status gila_khop_count_noalloc(int64_t n, const int64_t* row_ptr_dev,
+                                               const int32_t* col_idx_dev, int32_t k,
+                                               int64_t* counts_dev, int64_t* total_host,
+                                               void* cuda_stream)
+{
+    using namespace gila;
+    if (n < 0) return fail(GILA_EINVAL, "n must be >= 0");
+    if (n > kNoAllocMaxN)
+        return fail(GILA_EINVAL, "gila_khop_count_noalloc: n = " + std::to_string(n) +
+                                     " exceeds the fixed scratch limit of " +
+                                     std::to_string(kNoAllocMaxN) + " vertices");
+    if (k < 1 || k > 64) return fail(GILA_EINVAL, "k must be in [1, 64]");
+    if (n > 0 && (!row_ptr_dev || !col_idx_dev || !counts_dev))
+        return fail(GILA_EINVAL, "device array is NULL");
+    int device = 0;
+    GILA_CUDA(cudaGetDevice(&device));
+    NoAllocScratch* S = nullptr;
+    gila_status s = noalloc_scratch(device, &S);
+    if (s != GILA_OK) return s;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the queue counter and the bitmaps must start at zero; the rest is
+    // written before it is read
+    GILA_CUDA(cudaMemsetAsync(&S->qn, 0, sizeof(int), st));
+    GILA_CUDA(cudaMemsetAsync(S->bitmaps, 0, sizeof(S->bitmaps), st));
+    GILA_CUDA(cudaMemsetAsync(&S->total, 0, sizeof(int64_t), st));
+    int nq = 0;
+    if (n > 0) {
+        const int sms = sm_count(device);
+        const int64_t t1_blocks = std::max<int64_t>(
+            1, std::min<int64_t>((n + kT1Warps - 1) / kT1Warps, (int64_t)sms * 8));
+        t1_count_kernel<<<(unsigned)t1_blocks, kT1Warps * 32, 0, st>>>(
+            n, row_ptr_dev, col_idx_dev, k, counts_dev, S->queue, &S->qn);
+        count_launch();
+        GILA_CUDA(cudaGetLastError());
+        GILA_CUDA(cudaMemcpyAsync(&nq, &S->qn, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GILA_CUDA(cudaStreamSynchronize(st));
+    }
+    if (nq > 0) {
+        const int64_t nwords = ((n + 31) / 32 + 3) & ~int64_t(3);
+        const int blocks = std::min(nq, kNoAllocT2Blocks);
+        t2_kernel<<<blocks, kT2Threads, 0, st>>>(n, row_ptr_dev, col_idx_dev, k, S->queue, nq,
+                                                 S->bitmaps, S->lists, nwords, counts_dev, nullptr,
+                                                 nullptr, 0);
+        count_launch();
+        GILA_CUDA(cudaGetLastError());
+    }
+    if (n > 0) {
+        sum_counts_kernel<<<1, 1024, 0, st>>>(counts_dev, n, &S->total);
+        count_launch();
+        GILA_CUDA(cudaGetLastError());
+    }
+    int64_t total = 0;
+    GILA_CUDA(cudaMemcpyAsync(&total, &S->total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GILA_CUDA(cudaStreamSynchronize(st));
+    if (total_host) *total_host = total;
+    return GILA_OK;
+}

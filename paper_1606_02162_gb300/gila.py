@@ -88,6 +88,7 @@ SIGNATURES = [
     ("gila_profile_read", ctypes.c_int, [P, P, P, P, P]),
     ("gila_last_error", ctypes.c_char_p, []),
     ("gila_kernel_launches", ctypes.c_int64, []),
+    ("gila_khop_count_noalloc", ctypes.c_int, [I64, P, P, I32, P, ctypes.POINTER(I64), P]),
 ]
 
 
@@ -159,6 +160,18 @@ def gila_csr_validate(n, row_ptr, col_idx) -> int:
 
 def gila_kernel_launches() -> int:
     return load().gila_kernel_launches()
+
+
+def gila_khop_count_noalloc(n, row_ptr_dev, col_idx_dev, k, counts_dev, stream=None) -> int:
+    """|N_v(k)| of every vertex into counts_dev (int64 device tensor of n),
+    from caller-owned device CSR arrays, with no allocation inside the
+    library; returns the total. stream: cudaStream_t address, None = torch's
+    current stream."""
+    total = I64()
+    s = _torch_stream() if stream is None else stream
+    _check(load().gila_khop_count_noalloc(int(n), _dev_ptr(row_ptr_dev), _dev_ptr(col_idx_dev),
+                                          int(k), _dev_ptr(counts_dev), ctypes.byref(total), s))
+    return total.value
 
 
 def gila_last_error() -> str:
