@@ -249,8 +249,6 @@ def main():
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()
-    nnzk = G.gila_graph_info(h.handle)["nnz_khop"]
-    P = nnzk + g.nnz
     G.gila_profile_read(h.handle)  # clear
     G.gila_profile_enable(h.handle, True)
     clocks = ClockSampler(local)
@@ -260,13 +258,19 @@ def main():
     launches0 = G.gila_kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ev0.record(stream)
+    marks[0].record(stream)
     last = None
-    for _ in range(args.steps):
+    for i in range(args.steps):
         last = step()
+        marks[i + 1].record(stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
+    step_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps)]
+    nnzk = G.gila_graph_info(h.handle)["nnz_khop"]
+    P = nnzk + g.nnz
     launches = G.gila_kernel_launches() - launches0
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
@@ -342,6 +346,7 @@ def main():
         "config": {"workload": wl["desc"], "n": g.n, "edges": g.num_edges, "k": k,
                    "iters": iters, "nnz_khop": nnzk, "pairs_per_iter": P,
                    "ms_per_iter": iter_ms, "khop_build_ms": build_ms,
+                   "step_ms": [round(x, 3) for x in step_ms],
                    "layouts_per_s": ws * args.steps / (ms / 1e3),
                    "l2": "inputs larger than L2 (k-hop lists %.2f GB)" % (4 * nnzk / 1e9),
                    "parallelism": "replicas" if ws > 1 else "single GPU",

@@ -97,6 +97,20 @@ typedef struct gila_metrics {
     double rep_att_ratio; /* rep_total / att_total */
 } gila_metrics;
 
+/* Scheduling knobs of the iteration kernels. Each setting gives
+ * deterministic results; different settings may differ in the last bits of
+ * FP32 sums (different summation trees). Zero fields keep the defaults. */
+typedef struct gila_tuning {
+    int32_t tiled;         /* -1 automatic (default), 0 never, 1 always: stage positions in
+                              shared-memory tiles instead of gathering them through L2 */
+    int32_t tile_vertices; /* positions per tile; 0 = as many as fit in 200 KiB */
+    int32_t min_segment;   /* automatic mode tiles when nnz_khop / (n * tiles) >= this (48) */
+    int32_t small_max;     /* untiled kernel: rows of length <= this use 8-lane groups (32) */
+    int32_t warp_max;      /* ... rows <= this use one warp (8192) */
+    int32_t block_max;     /* ... rows <= this use one block (65536); longer rows are chunked */
+    int32_t chunk;         /* entries per chunk of a chunked row (32768) */
+} gila_tuning;
+
 typedef struct gila_graph gila_graph;
 
 /* Fills *p with k = 2, iters = 300, d = 1, t0 = 0 (default), linear
@@ -126,6 +140,12 @@ void gila_graph_destroy(gila_graph* g);
 /* Issue all later work of g on this cudaStream_t (NULL = legacy default
  * stream). The stream stays owned by the caller. */
 gila_status gila_graph_set_stream(gila_graph* g, void* cuda_stream);
+
+/* Set the scheduling knobs of g (see gila_tuning). Changing a row-class
+ * bound drops the cached k-hop lists (the next call rebuilds them).
+ * gila_graph_get_tuning returns the values in force, defaults filled in. */
+gila_status gila_graph_tune(gila_graph* g, const gila_tuning* t);
+gila_status gila_graph_get_tuning(const gila_graph* g, gila_tuning* out);
 
 /* Sizes: vertices, stored adjacency entries (2E), the k of the built
  * k-hop lists (0 if none) and their total length. Any pointer may be NULL. */
@@ -176,6 +196,65 @@ gila_status gila_layout_run(gila_graph* g, const gila_params* prm,
  * reduction order. Synchronises the graph's stream. */
 gila_status gila_layout_metrics(gila_graph* g, const gila_params* prm, const void* pos_dev,
                                 gila_metrics* out);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent graphs laid out together (SURVEY pattern
+ * "thousands of small uneven graphs"). The batch is the disjoint union of
+ * its graphs, so one k-hop build serves all of them; the layouts then run in
+ * one persistent kernel launch in which each CTA takes one graph at a time
+ * and carries it through all iterations with its placement staged in shared
+ * memory. The launch is captured in a CUDA graph and replayed while the
+ * arguments stay the same. Every graph follows its own temperature schedule
+ * (default t0 from its own n and initial bounding box). A graph's result
+ * depends only on the graph, its placement, the parameters and the batch
+ * tuning, not on the other graphs of the batch. Precisions: GILA_FP32,
+ * GILA_FP32_COMPENSATED, GILA_FP64. Placements are concatenated in graph
+ * order: graph i starts at vertex offset n[0] + ... + n[i-1].
+ * ------------------------------------------------------------------------ */
+typedef struct gila_batch gila_batch;
+
+typedef struct gila_batch_tuning {
+    int32_t threads;     /* threads per CTA: 256, 512 or 1024; 0 = 512 */
+    int32_t ctas_per_sm; /* CTAs per SM (1..8); 0 = 2 when two graphs fit in shared memory */
+    int32_t group4_max;  /* graphs whose mean k-hop row length is <= this use 4 lanes per
+                            vertex; 0 = 8 */
+    int32_t group8_max;  /* ... 8 lanes; 0 = 24 */
+    int32_t group16_max; /* ... 16 lanes; 0 = 64; longer rows use 32 lanes */
+} gila_batch_tuning;
+
+/* Pack `count` host CSR graphs (n[i], row_ptr[i], col_idx[i], each as for
+ * gila_graph_create) into one device batch (one upload). flags:
+ * GILA_GRAPH_VALIDATE checks every graph. */
+gila_status gila_batch_create(int32_t count, const int64_t* n, const int64_t* const* row_ptr,
+                              const int32_t* const* col_idx, int32_t flags, gila_batch** out);
+void gila_batch_destroy(gila_batch* b);
+gila_status gila_batch_set_stream(gila_batch* b, void* cuda_stream);
+gila_status gila_batch_info(const gila_batch* b, int32_t* count, int64_t* total_n,
+                            int64_t* nnz_khop);
+/* k-hop lists of every graph of the batch (one build over the union). */
+gila_status gila_batch_build_khop(gila_batch* b, int32_t k, int64_t* nnz_out);
+/* Set (or read back, defaults filled in for a precision) the launch shape
+ * and lanes-per-vertex thresholds of the batched kernel. */
+gila_status gila_batch_tune(gila_batch* b, const gila_batch_tuning* t);
+gila_status gila_batch_get_tuning(const gila_batch* b, int32_t precision, gila_batch_tuning* out);
+/* Time candidate tunings on this batch (probe_iters iterations each, from
+ * the placement pos_dev, which is not modified), keep the fastest and
+ * return it in *chosen. */
+gila_status gila_batch_autotune(gila_batch* b, const gila_params* prm, const void* pos_dev,
+                                int32_t probe_iters, gila_batch_tuning* chosen);
+/* prm->iters iterations of every graph on a device placement (float2 or
+ * double2 per precision, concatenated), in one persistent launch; builds the
+ * k-hop lists first when needed. Asynchronous on the batch's stream. */
+gila_status gila_layout_batch_device(gila_batch* b, const gila_params* prm, void* pos_dev_inout);
+/* The same from and to host memory (double[2 * total_n]); returns when the
+ * result is on the host. */
+gila_status gila_layout_batch_run(gila_batch* b, const gila_params* prm,
+                                  const double* pos_in_host, double* pos_out_host);
+/* Lay out `count` already-created graphs together: their device CSRs are
+ * packed into a temporary batch; pos_in[i] / pos_out[i] are host
+ * double[2 n_i] placements. Runs on the stream of gs[0]. */
+gila_status gila_layout_batch(gila_graph* const* gs, int32_t count, const gila_params* prm,
+                              const double* const* pos_in, double* const* pos_out);
 
 /* Temperature of iteration i under prm (t0 = resolved initial temperature). */
 double gila_temperature(const gila_params* prm, double t0, int32_t i);

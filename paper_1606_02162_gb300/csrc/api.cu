@@ -85,6 +85,7 @@ gila_status ensure_khop(gila_graph* g, int k)
         GILA_CUDA(cudaEventRecord(a, g->stream));
     }
     g->k_built = 0;
+    invalidate_tile_plans(g);
     gila_status s = build_khop(g, k);
     if (g->prof_on) {
         cudaEventRecord(b, g->stream);
@@ -293,6 +294,43 @@ gila_status gila_graph_set_stream(gila_graph* g, void* cuda_stream)
 {
     if (!g) return fail(GILA_EINVAL, "graph is NULL");
     g->stream = (cudaStream_t)cuda_stream;
+    return GILA_OK;
+}
+
+gila_status gila_graph_tune(gila_graph* g, const gila_tuning* t)
+{
+    if (!g || !t) return fail(GILA_EINVAL, "graph or tuning is NULL");
+    if (t->tiled < -1 || t->tiled > 1) return fail(GILA_EINVAL, "tiled must be -1, 0 or 1");
+    if (t->tile_vertices < 0 || t->min_segment < 0 || t->small_max < 0 || t->warp_max < 0 ||
+        t->block_max < 0 || t->chunk < 0)
+        return fail(GILA_EINVAL, "tuning values must be >= 0");
+    BinConfig c;  // defaults
+    if (t->small_max) c.small_max = t->small_max;
+    if (t->warp_max) c.warp_max = t->warp_max;
+    if (t->block_max) c.block_max = t->block_max;
+    if (t->chunk) c.chunk = t->chunk;
+    if (!(c.small_max <= c.warp_max && c.warp_max <= c.block_max))
+        return fail(GILA_EINVAL, "row-class bounds must satisfy small_max <= warp_max <= block_max");
+    BinConfig& old = g->bins.cfg;
+    if (old.small_max != c.small_max || old.warp_max != c.warp_max ||
+        old.block_max != c.block_max || old.chunk != c.chunk) {
+        old = c;
+        g->k_built = 0;  // classes are assigned at build time
+    }
+    g->tune = *t;
+    invalidate_tile_plans(g);
+    return GILA_OK;
+}
+
+gila_status gila_graph_get_tuning(const gila_graph* g, gila_tuning* out)
+{
+    if (!g || !out) return fail(GILA_EINVAL, "graph or out is NULL");
+    *out = g->tune;
+    out->min_segment = g->tune.min_segment > 0 ? g->tune.min_segment : 48;
+    out->small_max = g->bins.cfg.small_max;
+    out->warp_max = g->bins.cfg.warp_max;
+    out->block_max = g->bins.cfg.block_max;
+    out->chunk = g->bins.cfg.chunk;
     return GILA_OK;
 }
 

@@ -1,0 +1,181 @@
+// Device helpers shared by the iteration kernels (single graph, tiled and
+// batched): position vector types, streaming id loads, the per-pair force
+// term, compensated accumulators, row traversal and the capped move.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "device_util.cuh"
+#include "gila_impl.h"
+
+namespace gila {
+
+template <class T> struct V2;
+template <> struct V2<float> { using type = float2; };
+template <> struct V2<double> { using type = double2; };
+
+enum Model { kFR = 0, kGeneric = 1 };
+
+
+// Streaming load of four ids: read once per iteration, kept out of L1 so
+// that L1 serves the position gathers.
+__device__ __forceinline__ uint4 ld_ids4(const uint4* p)
+{
+    uint4 r;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t ld_id(const uint32_t* p)
+{
+    uint32_t r;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(r) : "l"(p));
+    return r;
+}
+
+template <class T>
+__device__ __forceinline__ T ipow_(T x, int e)
+{
+    T r = T(1);
+    for (int i = 0; i < e; ++i) r *= x;
+    return r;
+}
+
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float fsqrt(float r2) { return r2 * rsqrtf(r2); }
+__device__ __forceinline__ double fsqrt(double r2) { return sqrt(r2); }
+
+// Force accumulator; COMP adds a running compensation term per component
+// (two-sum), which removes the rounding error of long float sums.
+template <class T, bool COMP>
+struct Acc {
+    T sx = T(0), sy = T(0), cx = T(0), cy = T(0);
+
+    __device__ __forceinline__ static void two_sum(T& s, T& c, T x)
+    {
+        const T t = s + x;
+        const T bp = t - s;
+        c += (s - (t - bp)) + (x - bp);
+        s = t;
+    }
+    __device__ __forceinline__ void add(T x, T y)
+    {
+        if (COMP) {
+            two_sum(sx, cx, x);
+            two_sum(sy, cy, y);
+        } else {
+            sx += x;
+            sy += y;
+        }
+    }
+    __device__ __forceinline__ void merge(T ox, T oy, T ocx, T ocy)
+    {
+        if (COMP) {
+            two_sum(sx, cx, ox);
+            two_sum(sy, cy, oy);
+            cx += ocx;
+            cy += ocy;
+        } else {
+            sx += ox;
+            sy += oy;
+        }
+    }
+    __device__ __forceinline__ void group_reduce(int width)
+    {
+        for (int o = width >> 1; o > 0; o >>= 1) {
+            const T ox = __shfl_xor_sync(kFull, sx, o, width);
+            const T oy = __shfl_xor_sync(kFull, sy, o, width);
+            const T ocx = COMP ? __shfl_xor_sync(kFull, cx, o, width) : T(0);
+            const T ocy = COMP ? __shfl_xor_sync(kFull, cy, o, width) : T(0);
+            merge(ox, oy, ocx, ocy);
+        }
+    }
+    __device__ __forceinline__ T fx() const { return COMP ? sx + cx : sx; }
+    __device__ __forceinline__ T fy() const { return COMP ? sy + cy : sy; }
+};
+
+// One k-hop entry's contribution. Positions come through L1/L2 (SMEM =
+// false, `pos` is the whole placement) or from a shared-memory tile holding
+// ids [base, base + tile size) (SMEM = true).
+template <class T, int MODEL, bool COMP, bool SMEM = false>
+struct Pair {
+    using P2 = typename V2<T>::type;
+    const P2* __restrict__ pos;
+    uint32_t base = 0;
+    T xu, yu, d2, inv_d;
+    int p, q;
+
+    __device__ __forceinline__ void operator()(uint32_t e, Acc<T, COMP>& a) const
+    {
+        const P2 pv = SMEM ? pos[(e & kIdMask) - base] : __ldg(pos + (e & kIdMask));
+        const T dx = xu - pv.x, dy = yu - pv.y;
+        const T r2 = dx * dx + dy * dy;
+        if (r2 > T(0)) {
+            T c;
+            if (MODEL == kFR) {
+                c = fdiv(d2, r2);
+                if (e & kEdgeFlag) c -= fsqrt(r2) * inv_d;
+            } else {
+                const T dl = sqrt(r2);
+                c = d2 / (ipow_(dl, q) * dl);
+                if (e & kEdgeFlag) c -= ipow_(dl, p) / dl * inv_d;
+            }
+            a.add(c * dx, c * dy);
+        }
+    }
+};
+
+// Entries [s, e) of kcol, lanes gl = 0..G-1 of a group (G >= 4): an
+// unaligned head of at most 3 entries, 16-byte vector loads of 4 ids,
+// then a tail of at most 3 entries.
+template <class F, class A>
+__device__ __forceinline__ void row_sum(const uint32_t* __restrict__ kcol, int64_t s, int64_t e,
+                                        int gl, int G, const F& f, A& a)
+{
+    int64_t s4 = (s + 3) & ~int64_t(3);
+    if (s4 > e) s4 = e;
+    int64_t e4 = e & ~int64_t(3);
+    if (e4 < s4) e4 = s4;
+    if (s + gl < s4) f(ld_id(kcol + s + gl), a);
+    const uint4* k4 = reinterpret_cast<const uint4*>(kcol);
+#pragma unroll 2
+    for (int64_t c = (s4 >> 2) + gl; c < (e4 >> 2); c += G) {
+        const uint4 w = ld_ids4(k4 + c);
+        f(w.x, a);
+        f(w.y, a);
+        f(w.z, a);
+        f(w.w, a);
+    }
+    if (e4 + gl < e) f(ld_id(kcol + e4 + gl), a);
+}
+
+template <class T>
+__device__ __forceinline__ void apply_move(double t_, void* pos_out, void* disp_out, int64_t u,
+                                           T xu, T yu, T fx, T fy)
+{
+    using P2 = typename V2<T>::type;
+    const T t = (T)t_;
+    const T fn = sqrt(fx * fx + fy * fy);
+    T mx = fx, my = fy;
+    if (fn > t) {
+        const T sc = t / fn;
+        mx = fx * sc;
+        my = fy * sc;
+    }
+    P2 o;
+    o.x = xu + mx;
+    o.y = yu + my;
+    reinterpret_cast<P2*>(pos_out)[u] = o;
+    if (disp_out) {
+        P2 m;
+        m.x = mx;
+        m.y = my;
+        reinterpret_cast<P2*>(disp_out)[u] = m;
+    }
+}
+
+}  // namespace gila

@@ -85,6 +85,20 @@ struct Bins {
     BinConfig cfg;
 };
 
+// Shared-memory tiling plan of the iteration for one position width
+// (index 0: float2, 1: double2). Rebuilt after every k-hop build.
+struct TilePlan {
+    bool ready = false;  // decided for the current k-hop lists
+    bool use = false;    // the tiled kernel serves this graph
+    int32_t nt = 0, tv = 0, ncta = 0;
+    int32_t* seg = nullptr;
+    size_t seg_cap = 0;
+    int32_t* cta_rows = nullptr;
+    size_t cta_cap = 0;
+    void* acc = nullptr;
+    size_t acc_cap = 0;
+};
+
 struct ProfileRec {
     cudaEvent_t a, b;
     int kind;  // 0 build, 1 iterations
@@ -108,6 +122,8 @@ struct gila_graph {
     size_t cap_kcol = 0;
     gila::KhopScratch ks;
     gila::Bins bins;
+    gila::TilePlan tplan[2];
+    gila_tuning tune = {-1, 0, 0, 0, 0, 0, 0};
     // placement buffers for the run calls
     void* pos[2] = {nullptr, nullptr};
     size_t pos_cap[2] = {0, 0};
@@ -135,6 +151,7 @@ gila_status launch_iteration(gila_graph* g, const gila_params* prm, double t,
 gila_status compute_metrics(gila_graph* g, const gila_params* prm, const void* pos,
                             gila_metrics* out);
 gila_status bbox_aspect(gila_graph* g, int precision, const void* pos, double* aspect);
+void invalidate_tile_plans(gila_graph* g);
 gila_status convert_positions(gila_graph* g, int precision, const double* src, void* dst,
                               bool to_device_type);
 void free_layout(gila_graph* g);

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "device_util.cuh"
+#include "force.cuh"
 #include "gila_impl.h"
 
 namespace gila {
@@ -29,12 +30,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarpsPerBlock = kThreads / 32;
-
-template <class T> struct V2;
-template <> struct V2<float> { using type = float2; };
-template <> struct V2<double> { using type = double2; };
-
-enum Model { kFR = 0, kGeneric = 1 };
 
 struct IterArgs {
     const int64_t* krow;
@@ -54,160 +49,11 @@ struct IterArgs {
     void* disp_out;
 };
 
-// Streaming load of four ids: read once per iteration, kept out of L1 so
-// that L1 serves the position gathers.
-__device__ __forceinline__ uint4 ld_ids4(const uint4* p)
-{
-    uint4 r;
-    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-        : "l"(p));
-    return r;
-}
-
-__device__ __forceinline__ uint32_t ld_id(const uint32_t* p)
-{
-    uint32_t r;
-    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(r) : "l"(p));
-    return r;
-}
-
 template <class T>
-__device__ __forceinline__ T ipow_(T x, int e)
+__device__ __forceinline__ void apply_move_it(const IterArgs& A, int64_t u, T xu, T yu, T fx,
+                                              T fy)
 {
-    T r = T(1);
-    for (int i = 0; i < e; ++i) r *= x;
-    return r;
-}
-
-__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
-__device__ __forceinline__ float fsqrt(float r2) { return r2 * rsqrtf(r2); }
-__device__ __forceinline__ double fsqrt(double r2) { return sqrt(r2); }
-
-// Force accumulator; COMP adds a running compensation term per component
-// (two-sum), which removes the rounding error of long float sums.
-template <class T, bool COMP>
-struct Acc {
-    T sx = T(0), sy = T(0), cx = T(0), cy = T(0);
-
-    __device__ __forceinline__ static void two_sum(T& s, T& c, T x)
-    {
-        const T t = s + x;
-        const T bp = t - s;
-        c += (s - (t - bp)) + (x - bp);
-        s = t;
-    }
-    __device__ __forceinline__ void add(T x, T y)
-    {
-        if (COMP) {
-            two_sum(sx, cx, x);
-            two_sum(sy, cy, y);
-        } else {
-            sx += x;
-            sy += y;
-        }
-    }
-    __device__ __forceinline__ void merge(T ox, T oy, T ocx, T ocy)
-    {
-        if (COMP) {
-            two_sum(sx, cx, ox);
-            two_sum(sy, cy, oy);
-            cx += ocx;
-            cy += ocy;
-        } else {
-            sx += ox;
-            sy += oy;
-        }
-    }
-    __device__ __forceinline__ void group_reduce(int width)
-    {
-        for (int o = width >> 1; o > 0; o >>= 1) {
-            const T ox = __shfl_xor_sync(kFull, sx, o, width);
-            const T oy = __shfl_xor_sync(kFull, sy, o, width);
-            const T ocx = COMP ? __shfl_xor_sync(kFull, cx, o, width) : T(0);
-            const T ocy = COMP ? __shfl_xor_sync(kFull, cy, o, width) : T(0);
-            merge(ox, oy, ocx, ocy);
-        }
-    }
-    __device__ __forceinline__ T fx() const { return COMP ? sx + cx : sx; }
-    __device__ __forceinline__ T fy() const { return COMP ? sy + cy : sy; }
-};
-
-template <class T, int MODEL, bool COMP>
-struct Pair {
-    using P2 = typename V2<T>::type;
-    const P2* __restrict__ pos;
-    T xu, yu, d2, inv_d;
-    int p, q;
-
-    __device__ __forceinline__ void operator()(uint32_t e, Acc<T, COMP>& a) const
-    {
-        const P2 pv = __ldg(pos + (e & kIdMask));
-        const T dx = xu - pv.x, dy = yu - pv.y;
-        const T r2 = dx * dx + dy * dy;
-        if (r2 > T(0)) {
-            T c;
-            if (MODEL == kFR) {
-                c = fdiv(d2, r2);
-                if (e & kEdgeFlag) c -= fsqrt(r2) * inv_d;
-            } else {
-                const T dl = sqrt(r2);
-                c = d2 / (ipow_(dl, q) * dl);
-                if (e & kEdgeFlag) c -= ipow_(dl, p) / dl * inv_d;
-            }
-            a.add(c * dx, c * dy);
-        }
-    }
-};
-
-// Entries [s, e) of kcol, lanes gl = 0..G-1 of a group (G >= 4): an
-// unaligned head of at most 3 entries, 16-byte vector loads of 4 ids,
-// then a tail of at most 3 entries.
-template <class T, int MODEL, bool COMP>
-__device__ __forceinline__ void row_sum(const uint32_t* __restrict__ kcol, int64_t s, int64_t e,
-                                        int gl, int G, const Pair<T, MODEL, COMP>& f,
-                                        Acc<T, COMP>& a)
-{
-    int64_t s4 = (s + 3) & ~int64_t(3);
-    if (s4 > e) s4 = e;
-    int64_t e4 = e & ~int64_t(3);
-    if (e4 < s4) e4 = s4;
-    if (s + gl < s4) f(ld_id(kcol + s + gl), a);
-    const uint4* k4 = reinterpret_cast<const uint4*>(kcol);
-#pragma unroll 2
-    for (int64_t c = (s4 >> 2) + gl; c < (e4 >> 2); c += G) {
-        const uint4 w = ld_ids4(k4 + c);
-        f(w.x, a);
-        f(w.y, a);
-        f(w.z, a);
-        f(w.w, a);
-    }
-    if (e4 + gl < e) f(ld_id(kcol + e4 + gl), a);
-}
-
-template <class T>
-__device__ __forceinline__ void apply_move(const IterArgs& A, int64_t u, T xu, T yu, T fx, T fy)
-{
-    using P2 = typename V2<T>::type;
-    const T t = (T)A.t;
-    const T fn = sqrt(fx * fx + fy * fy);
-    T mx = fx, my = fy;
-    if (fn > t) {
-        const T sc = t / fn;
-        mx = fx * sc;
-        my = fy * sc;
-    }
-    P2 o;
-    o.x = xu + mx;
-    o.y = yu + my;
-    reinterpret_cast<P2*>(A.pos_out)[u] = o;
-    if (A.disp_out) {
-        P2 m;
-        m.x = mx;
-        m.y = my;
-        reinterpret_cast<P2*>(A.disp_out)[u] = m;
-    }
+    apply_move<T>(A.t, A.pos_out, A.disp_out, u, xu, yu, fx, fy);
 }
 
 // Block-wide sum of an accumulator in a fixed order (warps, then warp 0).
@@ -258,7 +104,7 @@ iteration_kernel(const IterArgs A)
         f.xu = pu.x;
         f.yu = pu.y;
         Acc<T, COMP> a;
-        row_sum<T, MODEL, COMP>(A.kcol, ch.begin, ch.end, threadIdx.x, kThreads, f, a);
+        row_sum(A.kcol, ch.begin, ch.end, threadIdx.x, kThreads, f, a);
         block_reduce<T, COMP>(a, sh);
         if (threadIdx.x == 0) {
             double* part = A.partials + (int64_t)b * 4;
@@ -280,7 +126,7 @@ iteration_kernel(const IterArgs A)
                 fy += __ldcg(q + 1) + __ldcg(q + 3);
             }
             A.giant_counter[ch.giant] = 0;
-            apply_move<T>(A, u, pu.x, pu.y, (T)fx, (T)fy);
+            apply_move_it<T>(A, u,pu.x, pu.y, (T)fx, (T)fy);
         }
         return;
     }
@@ -291,9 +137,9 @@ iteration_kernel(const IterArgs A)
         f.xu = pu.x;
         f.yu = pu.y;
         Acc<T, COMP> a;
-        row_sum<T, MODEL, COMP>(A.kcol, A.krow[u], A.krow[u + 1], threadIdx.x, kThreads, f, a);
+        row_sum(A.kcol, A.krow[u], A.krow[u + 1], threadIdx.x, kThreads, f, a);
         block_reduce<T, COMP>(a, sh);
-        if (threadIdx.x == 0) apply_move<T>(A, u, pu.x, pu.y, a.fx(), a.fy());
+        if (threadIdx.x == 0) apply_move_it<T>(A, u,pu.x, pu.y, a.fx(), a.fy());
         return;
     }
     b -= A.b2;
@@ -306,9 +152,9 @@ iteration_kernel(const IterArgs A)
         f.xu = pu.x;
         f.yu = pu.y;
         Acc<T, COMP> a;
-        row_sum<T, MODEL, COMP>(A.kcol, A.krow[u], A.krow[u + 1], lane, 32, f, a);
+        row_sum(A.kcol, A.krow[u], A.krow[u + 1], lane, 32, f, a);
         a.group_reduce(32);
-        if (lane == 0) apply_move<T>(A, u, pu.x, pu.y, a.fx(), a.fy());
+        if (lane == 0) apply_move_it<T>(A, u,pu.x, pu.y, a.fx(), a.fy());
         return;
     }
     b -= A.b1;
@@ -327,10 +173,10 @@ iteration_kernel(const IterArgs A)
             yu = pu.y;
             f.xu = xu;
             f.yu = yu;
-            row_sum<T, MODEL, COMP>(A.kcol, A.krow[u], A.krow[u + 1], gl, G, f, a);
+            row_sum(A.kcol, A.krow[u], A.krow[u + 1], gl, G, f, a);
         }
         a.group_reduce(G);
-        if (live && gl == 0) apply_move<T>(A, u, xu, yu, a.fx(), a.fy());
+        if (live && gl == 0) apply_move_it<T>(A, u,xu, yu, a.fx(), a.fy());
     }
 }
 
@@ -401,6 +247,164 @@ ordered_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __rest
     }
     pos_out[u] = make_double2(__dadd_rn(pu.x, mx), __dadd_rn(pu.y, my));
     if (disp_out) disp_out[u] = make_double2(mx, my);
+}
+
+// ------------------------------------------------------------- tiled path
+//
+// Positions are staged in shared memory one tile of `tv` consecutive ids at
+// a time, so the gathers of a row segment read shared memory instead of L2.
+// Every k-hop row is sorted, so its entries with ids in tile j form one
+// contiguous segment whose bounds are precomputed (seg). CTA c owns rows
+// [cta_rows[c], cta_rows[c+1]) (balanced by entries); for each tile in
+// order it loads the tile, then its warps take row segments from a shared
+// counter, sum them, and add the partial to the row's running sum (global
+// `acc`) -- or, at the last tile, finish the row and move the vertex. A
+// row's sum is combined in tile order by whichever warp holds it, so the
+// result does not depend on scheduling.
+constexpr int kTiledThreads = 1024;
+constexpr int kTileBytes = 200 * 1024;
+
+struct TiledArgs {
+    const int64_t* krow;
+    const uint32_t* kcol;
+    const int32_t* seg;       // n x (nt - 1) interior tile bounds, relative to krow[u]
+    const int32_t* cta_rows;  // gridDim.x + 1 row bounds
+    void* acc;                // n x 4 T running sums between tiles (nt > 1)
+    int64_t n;
+    int32_t nt, tv;
+    double d, t;
+    int p, q;
+    const void* pos_in;
+    void* pos_out;
+    void* disp_out;
+};
+
+template <class T, int MODEL, bool COMP>
+__global__ void __launch_bounds__(kTiledThreads, 1)
+tiled_kernel(const TiledArgs A)
+{
+    using P2 = typename V2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    P2* tile = reinterpret_cast<P2*>(smem_raw);
+    __shared__ int s_next;
+    const int lane = threadIdx.x & 31;
+    const int64_t r0 = A.cta_rows[blockIdx.x], r1 = A.cta_rows[blockIdx.x + 1];
+    if (r0 >= r1) return;  // whole block
+    const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos_in);
+    T* acc = reinterpret_cast<T*>(A.acc);
+    Pair<T, MODEL, COMP, true> f;
+    f.pos = tile;
+    f.d2 = (T)(A.d * A.d);
+    f.inv_d = (T)(1.0 / A.d);
+    f.p = A.p;
+    f.q = A.q;
+    for (int j = 0; j < A.nt; ++j) {
+        const int64_t tb = (int64_t)j * A.tv;
+        const int64_t tn = (A.n - tb < A.tv) ? A.n - tb : (int64_t)A.tv;
+        __syncthreads();  // every warp is done with the previous tile
+        {
+            // 16-byte copies (tv is even, so tile starts are 16-byte aligned)
+            const uint4* src = reinterpret_cast<const uint4*>(pos + tb);
+            uint4* dst = reinterpret_cast<uint4*>(tile);
+            const int64_t nv = (tn * (int64_t)sizeof(P2)) / 16;
+            for (int64_t i = threadIdx.x; i < nv; i += kTiledThreads) dst[i] = src[i];
+            if (sizeof(P2) == 8 && (tn & 1) && threadIdx.x == 0) tile[tn - 1] = pos[tb + tn - 1];
+        }
+        if (threadIdx.x == 0) s_next = 0;
+        __syncthreads();
+        f.base = (uint32_t)tb;
+        for (;;) {
+            int r = 0;
+            if (lane == 0) r = atomicAdd(&s_next, 1);
+            r = __shfl_sync(kFull, r, 0);
+            const int64_t u = r0 + r;
+            if (u >= r1) break;  // warp-uniform
+            const int64_t kb = A.krow[u];
+            const int64_t len = A.krow[u + 1] - kb;
+            const int64_t lo = (j == 0) ? 0 : A.seg[u * (A.nt - 1) + j - 1];
+            const int64_t hi = (j == A.nt - 1) ? len : A.seg[u * (A.nt - 1) + j];
+            const P2 pu = pos[u];
+            f.xu = pu.x;
+            f.yu = pu.y;
+            Acc<T, COMP> a;
+            row_sum(A.kcol, kb + lo, kb + hi, lane, 32, f, a);
+            a.group_reduce(32);
+            if (lane == 0) {
+                if (j > 0) {
+                    Acc<T, COMP> s;
+                    s.sx = acc[u * 4 + 0];
+                    s.sy = acc[u * 4 + 1];
+                    s.cx = acc[u * 4 + 2];
+                    s.cy = acc[u * 4 + 3];
+                    s.merge(a.sx, a.sy, a.cx, a.cy);
+                    a = s;
+                }
+                if (j < A.nt - 1) {
+                    acc[u * 4 + 0] = a.sx;
+                    acc[u * 4 + 1] = a.sy;
+                    acc[u * 4 + 2] = a.cx;
+                    acc[u * 4 + 3] = a.cy;
+                } else {
+                    apply_move<T>(A.t, A.pos_out, A.disp_out, u, pu.x, pu.y, a.fx(), a.fy());
+                }
+            }
+        }
+    }
+}
+
+// seg[u (nt-1) + j - 1] = index (relative to krow[u]) of the first entry of
+// row u with id >= j tv, for j = 1..nt-1.
+__global__ void tile_seg_kernel(int64_t n, const int64_t* __restrict__ krow,
+                                const uint32_t* __restrict__ kcol, int nt, int tv,
+                                int32_t* __restrict__ seg)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * (nt - 1)) return;
+    const int64_t u = i / (nt - 1);
+    const uint32_t key = (uint32_t)((i % (nt - 1)) + 1) * (uint32_t)tv;
+    int64_t lo = krow[u], hi = krow[u + 1];
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((kcol[mid] & kIdMask) < key) lo = mid + 1; else hi = mid;
+    }
+    seg[i] = (int32_t)(lo - krow[u]);
+}
+
+// cta_rows[c] = first row whose cost prefix krow[u] + w u reaches c/ncta of
+// the total cost (w = per-row overhead in entries).
+__global__ void tile_cta_kernel(int64_t n, const int64_t* __restrict__ krow, int ncta, int64_t w,
+                                int32_t* __restrict__ cta_rows)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > ncta) return;
+    if (c == ncta) {
+        cta_rows[c] = (int32_t)n;
+        return;
+    }
+    const int64_t total = krow[n] + w * n;
+    const int64_t target = total / ncta * c + (total % ncta) * c / ncta;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (krow[mid] + w * mid < target) lo = mid + 1; else hi = mid;
+    }
+    cta_rows[c] = (int32_t)lo;
+}
+
+template <class T, int MODEL, bool COMP>
+cudaError_t launch_tiled(const TiledArgs& A, int grid, size_t smem, cudaStream_t st)
+{
+    static bool configured = false;  // per instantiation; all devices take the same limit
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(tiled_kernel<T, MODEL, COMP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kTileBytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    tiled_kernel<T, MODEL, COMP><<<grid, kTiledThreads, smem, st>>>(A);
+    count_launch();
+    return cudaGetLastError();
 }
 
 template <class T, int MODEL, bool COMP>
@@ -557,9 +561,105 @@ gila_status ensure_red(gila_graph* g, size_t doubles)
 
 }  // namespace
 
+void invalidate_tile_plans(gila_graph* g)
+{
+    g->tplan[0].ready = false;
+    g->tplan[1].ready = false;
+}
+
+namespace {
+
+// Decide whether the tiled kernel serves g for positions of `esz` bytes and
+// prepare its segment bounds, CTA row ranges and running-sum buffer.
+gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
+{
+    P.ready = true;
+    P.use = false;
+    const int64_t n = g->n;
+    if (n == 0 || g->nnz_khop == 0 || g->tune.tiled == 0) return GILA_OK;
+    int64_t tv_max = kTileBytes / (int64_t)esz;
+    if (g->tune.tile_vertices > 0) tv_max = std::min<int64_t>(tv_max, g->tune.tile_vertices);
+    tv_max = std::max<int64_t>(2, tv_max & ~int64_t(1));
+    const int64_t nt = (n + tv_max - 1) / tv_max;
+    const int64_t tv = std::min<int64_t>(tv_max, (((n + nt - 1) / nt) + 1) & ~int64_t(1));
+    const int min_seg = g->tune.min_segment > 0 ? g->tune.min_segment : 48;
+    const double avg_seg = (double)g->nnz_khop / ((double)n * (double)nt);
+    if (g->tune.tiled < 0 && avg_seg < min_seg) return GILA_OK;
+    gila_status s;
+    if (nt > 1) {
+        s = ensure((void**)&P.seg, &P.seg_cap, sizeof(int32_t) * (size_t)(n * (nt - 1)));
+        if (s != GILA_OK) return s;
+        s = ensure(&P.acc, &P.acc_cap, 4 * (esz / 2) * (size_t)n);
+        if (s != GILA_OK) return s;
+        const int64_t cnt = n * (nt - 1);
+        tile_seg_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, g->stream>>>(
+            n, g->krow, g->kcol, (int)nt, (int)tv, P.seg);
+        count_launch();
+    }
+    const int ncta = sm_count(g->device);
+    s = ensure((void**)&P.cta_rows, &P.cta_cap, sizeof(int32_t) * (size_t)(ncta + 1));
+    if (s != GILA_OK) return s;
+    tile_cta_kernel<<<(ncta + 1 + 255) / 256, 256, 0, g->stream>>>(n, g->krow, ncta, 32 * nt,
+                                                                  P.cta_rows);
+    count_launch();
+    GILA_CUDA(cudaGetLastError());
+    P.nt = (int32_t)nt;
+    P.tv = (int32_t)tv;
+    P.ncta = ncta;
+    P.use = true;
+    return GILA_OK;
+}
+
+}  // namespace
+
 gila_status launch_iteration(gila_graph* g, const gila_params* prm, double t, const void* pos_in,
                              void* pos_out, void* disp_out)
 {
+    if (prm->precision != GILA_FP64_ORDERED && g->n > 0) {
+        const size_t esz = is_f64(prm->precision) ? 16 : 8;
+        TilePlan& P = g->tplan[esz == 16 ? 1 : 0];
+        if (!P.ready) {
+            gila_status s = plan_tiles(g, esz, P);
+            if (s != GILA_OK) return s;
+        }
+        if (P.use && ((uintptr_t)pos_in & 15) == 0) {
+            TiledArgs A;
+            A.krow = g->krow;
+            A.kcol = g->kcol;
+            A.seg = P.seg;
+            A.cta_rows = P.cta_rows;
+            A.acc = P.acc;
+            A.n = g->n;
+            A.nt = P.nt;
+            A.tv = P.tv;
+            A.d = prm->d;
+            A.t = t;
+            A.p = prm->p;
+            A.q = prm->q;
+            A.pos_in = pos_in;
+            A.pos_out = pos_out;
+            A.disp_out = disp_out;
+            const size_t smem = (size_t)P.tv * esz;
+            const bool fr = (prm->p == 2 && prm->q == 1);
+            cudaError_t e;
+            switch (prm->precision) {
+            case GILA_FP64:
+                e = fr ? launch_tiled<double, kFR, false>(A, P.ncta, smem, g->stream)
+                       : launch_tiled<double, kGeneric, false>(A, P.ncta, smem, g->stream);
+                break;
+            case GILA_FP32_COMPENSATED:
+                e = fr ? launch_tiled<float, kFR, true>(A, P.ncta, smem, g->stream)
+                       : launch_tiled<float, kGeneric, true>(A, P.ncta, smem, g->stream);
+                break;
+            default:
+                e = fr ? launch_tiled<float, kFR, false>(A, P.ncta, smem, g->stream)
+                       : launch_tiled<float, kGeneric, false>(A, P.ncta, smem, g->stream);
+                break;
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "tiled_kernel");
+            return GILA_OK;
+        }
+    }
     if (prm->precision == GILA_FP64_ORDERED) {
         if (g->n == 0) return GILA_OK;
         const unsigned grid = (unsigned)((g->n * 32 + kThreads - 1) / kThreads);
@@ -708,6 +808,12 @@ void free_layout(gila_graph* g)
     cudaFree(g->pos[1]);
     cudaFree(g->stage);
     cudaFree(g->red);
+    for (TilePlan& P : g->tplan) {
+        cudaFree(P.seg);
+        cudaFree(P.cta_rows);
+        cudaFree(P.acc);
+        P = TilePlan();
+    }
     g->pos[0] = g->pos[1] = nullptr;
     g->stage = nullptr;
     g->red = nullptr;

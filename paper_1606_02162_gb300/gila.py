@@ -54,6 +54,19 @@ class gila_metrics(ctypes.Structure):
                 ("att_total", ctypes.c_double), ("rep_att_ratio", ctypes.c_double)]
 
 
+class gila_tuning(ctypes.Structure):
+    _fields_ = [("tiled", ctypes.c_int32), ("tile_vertices", ctypes.c_int32),
+                ("min_segment", ctypes.c_int32), ("small_max", ctypes.c_int32),
+                ("warp_max", ctypes.c_int32), ("block_max", ctypes.c_int32),
+                ("chunk", ctypes.c_int32)]
+
+
+class gila_batch_tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("group4_max", ctypes.c_int32), ("group8_max", ctypes.c_int32),
+                ("group16_max", ctypes.c_int32)]
+
+
 class GilaError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
@@ -76,6 +89,8 @@ SIGNATURES = [
     ("gila_graph_destroy", None, [P]),
     ("gila_graph_set_stream", ctypes.c_int, [P, P]),
     ("gila_graph_info", ctypes.c_int, [P, P, P, P, P]),
+    ("gila_graph_tune", ctypes.c_int, [P, ctypes.POINTER(gila_tuning)]),
+    ("gila_graph_get_tuning", ctypes.c_int, [P, ctypes.POINTER(gila_tuning)]),
     ("gila_build_khop", ctypes.c_int, [P, I32, ctypes.POINTER(I64)]),
     ("gila_khop_reset", ctypes.c_int, [P]),
     ("gila_khop_export", ctypes.c_int, [P, P, P]),
@@ -89,6 +104,17 @@ SIGNATURES = [
     ("gila_last_error", ctypes.c_char_p, []),
     ("gila_kernel_launches", ctypes.c_int64, []),
     ("gila_khop_count_noalloc", ctypes.c_int, [I64, P, P, I32, P, ctypes.POINTER(I64), P]),
+    ("gila_batch_create", ctypes.c_int, [I32, P, P, P, I32, ctypes.POINTER(P)]),
+    ("gila_batch_destroy", None, [P]),
+    ("gila_batch_set_stream", ctypes.c_int, [P, P]),
+    ("gila_batch_info", ctypes.c_int, [P, P, P, P]),
+    ("gila_batch_build_khop", ctypes.c_int, [P, I32, ctypes.POINTER(I64)]),
+    ("gila_batch_tune", ctypes.c_int, [P, ctypes.POINTER(gila_batch_tuning)]),
+    ("gila_batch_get_tuning", ctypes.c_int, [P, I32, ctypes.POINTER(gila_batch_tuning)]),
+    ("gila_batch_autotune", ctypes.c_int, [P, PP, P, I32, ctypes.POINTER(gila_batch_tuning)]),
+    ("gila_layout_batch_device", ctypes.c_int, [P, PP, P]),
+    ("gila_layout_batch_run", ctypes.c_int, [P, PP, P, P]),
+    ("gila_layout_batch", ctypes.c_int, [P, I32, PP, P, P]),
 ]
 
 
@@ -204,6 +230,19 @@ def gila_graph_info(g) -> dict:
     return {"n": n.value, "nnz_adj": nnz.value, "k_built": kb.value, "nnz_khop": nk.value}
 
 
+def gila_graph_tune(g, tiled=-1, tile_vertices=0, min_segment=0, small_max=0, warp_max=0,
+                    block_max=0, chunk=0) -> None:
+    t = gila_tuning(int(tiled), int(tile_vertices), int(min_segment), int(small_max),
+                    int(warp_max), int(block_max), int(chunk))
+    _check(load().gila_graph_tune(g, ctypes.byref(t)))
+
+
+def gila_graph_get_tuning(g) -> dict:
+    t = gila_tuning()
+    _check(load().gila_graph_get_tuning(g, ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in gila_tuning._fields_}
+
+
 def gila_build_khop(g, k) -> int:
     nnz = I64()
     _check(load().gila_build_khop(g, int(k), ctypes.byref(nnz)))
@@ -276,6 +315,121 @@ class Graph:
     def close(self):
         if self.handle:
             gila_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# ------------------------------------------------------------------ batches
+
+def _ptr_array(arrs, ctype):
+    return (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs]) if arrs else None
+
+
+def gila_batch_create(graphs, flags=0) -> int:
+    """graphs: sequence of objects with n, row_ptr, col_idx (host arrays)."""
+    ns = np.array([g.n for g in graphs], dtype=np.int64)
+    rows = [_np(g.row_ptr, np.int64) for g in graphs]
+    cols = [_np(g.col_idx, np.int32) for g in graphs]
+    rp = _ptr_array(rows, ctypes.c_int64)
+    cp = _ptr_array(cols, ctypes.c_int32)
+    h = ctypes.c_void_p()
+    _check(load().gila_batch_create(len(graphs), _ptr(ns) if len(graphs) else None,
+                                    ctypes.cast(rp, P) if rp else None,
+                                    ctypes.cast(cp, P) if cp else None, int(flags),
+                                    ctypes.byref(h)))
+    return h.value
+
+
+def gila_batch_destroy(b) -> None:
+    if b:
+        load().gila_batch_destroy(b)
+
+
+def gila_batch_set_stream(b, stream=None) -> None:
+    s = _torch_stream() if stream is None else stream
+    _check(load().gila_batch_set_stream(b, s))
+
+
+def gila_batch_info(b) -> dict:
+    c, n, k = I32(), I64(), I64()
+    _check(load().gila_batch_info(b, ctypes.byref(c), ctypes.byref(n), ctypes.byref(k)))
+    return {"count": c.value, "total_n": n.value, "nnz_khop": k.value}
+
+
+def gila_batch_build_khop(b, k) -> int:
+    nnz = I64()
+    _check(load().gila_batch_build_khop(b, int(k), ctypes.byref(nnz)))
+    return nnz.value
+
+
+def gila_batch_tune(b, threads=0, ctas_per_sm=0, group4_max=0, group8_max=0,
+                    group16_max=0) -> None:
+    t = gila_batch_tuning(int(threads), int(ctas_per_sm), int(group4_max), int(group8_max),
+                          int(group16_max))
+    _check(load().gila_batch_tune(b, ctypes.byref(t)))
+
+
+def gila_batch_get_tuning(b, precision=GILA_FP32) -> dict:
+    t = gila_batch_tuning()
+    _check(load().gila_batch_get_tuning(b, int(precision), ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in gila_batch_tuning._fields_}
+
+
+def gila_batch_autotune(b, prm, pos, probe_iters=5) -> dict:
+    t = gila_batch_tuning()
+    _check(load().gila_batch_autotune(b, ctypes.byref(prm), _dev_ptr(pos), int(probe_iters),
+                                      ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in gila_batch_tuning._fields_}
+
+
+def gila_layout_batch_device(b, prm, pos) -> None:
+    _check(load().gila_layout_batch_device(b, ctypes.byref(prm), _dev_ptr(pos)))
+
+
+def gila_layout_batch_run(b, prm, pos_in, pos_out=None) -> np.ndarray:
+    src = _np(pos_in, np.float64)
+    out = np.empty_like(src) if pos_out is None else pos_out
+    _check(load().gila_layout_batch_run(b, ctypes.byref(prm), _ptr(src), _ptr(out)))
+    return out
+
+
+def gila_layout_batch(graph_handles, prm, pos_in_list):
+    """Lay out already-created graphs together; returns a list of host placements."""
+    ins = [_np(p, np.float64) for p in pos_in_list]
+    outs = [np.empty_like(p) for p in ins]
+    handles = list(graph_handles)
+    hs = (ctypes.c_void_p * len(handles))(*handles) if handles else None
+    ip = _ptr_array(ins, ctypes.c_double)
+    op = _ptr_array(outs, ctypes.c_double)
+    _check(load().gila_layout_batch(ctypes.cast(hs, P) if hs else None, len(ins),
+                                    ctypes.byref(prm), ctypes.cast(ip, P) if ip else None,
+                                    ctypes.cast(op, P) if op else None))
+    return outs
+
+
+class Batch:
+    """Owning wrapper of a gila_batch bound to torch's current stream."""
+
+    def __init__(self, graphs, flags=0):
+        self.graphs = list(graphs)
+        self.handle = gila_batch_create(self.graphs, flags)
+        gila_batch_set_stream(self.handle)
+        self.offsets = np.concatenate([[0], np.cumsum([g.n for g in self.graphs])]).astype(np.int64)
+
+    def close(self):
+        if self.handle:
+            gila_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -137,6 +137,43 @@ def test_step_parity(name, maker, k, prec):
         assert np.array_equal(new, (base.astype(_np_dt(prec)) + disp.astype(_np_dt(prec))).astype(np.float64))
 
 
+TUNINGS = [
+    ("untiled", dict(tiled=0)),
+    ("tiled", dict(tiled=1)),
+    ("tiled_small_tiles", dict(tiled=1, tile_vertices=1000)),
+    ("untiled_small_classes", dict(tiled=0, small_max=4, warp_max=64, block_max=512, chunk=300)),
+]
+
+
+@pytest.mark.parametrize("prec", [G.GILA_FP32, G.GILA_FP32_COMPENSATED, G.GILA_FP64],
+                         ids=["fp32", "fp32c", "fp64"])
+@pytest.mark.parametrize("tname,tune", TUNINGS, ids=[t[0] for t in TUNINGS])
+@pytest.mark.parametrize("name,maker,k", [
+    ("ba20k_k2", lambda: I.barabasi_albert(20000, 3, 7), 2),
+    ("cl9k_k3", lambda: I.chung_lu(9001, 2.3, 8.0, 36000, 5), 3),
+    ("mesh50_k3", lambda: I.tri_mesh(50, 51), 3),
+], ids=["ba20k_k2", "cl9k_k3", "mesh50_k3"])
+def test_step_parity_tunings(name, maker, k, tname, tune, prec):
+    """Every scheduling (tiled with one or many tiles, untiled with every row
+    class populated) matches the oracle within the precision's tolerance."""
+    torch = _torch()
+    g = maker()
+    pos = I.uniform_positions(g.n, 5)
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, k)
+    t = 0.1 * math.sqrt(g.n)
+    with G.Graph.from_inputs(g) as h:
+        G.gila_graph_tune(h.handle, **tune)
+        p_in = torch.tensor(pos, dtype=_dt(prec), device="cuda")
+        p_out = torch.empty_like(p_in)
+        disp = torch.empty_like(p_in)
+        G.gila_layout_step(h.handle, G.params(k=k, precision=prec), t, p_in, p_out, disp)
+        torch.cuda.synchronize()
+        base = p_in.double().cpu().numpy()
+        got = disp.double().cpu().numpy()
+    _, odisp = O.step(g.n, g.row_ptr, g.col_idx, okrow, okcol, base, t)
+    assert np.abs(got - odisp).max() <= TOL[prec] * np.abs(odisp).max()
+
+
 def _np_dt(prec):
     return np.float64 if prec in (G.GILA_FP64, G.GILA_FP64_ORDERED) else np.float32
 
