@@ -46,6 +46,15 @@ WORKLOADS = {
                    desc="32x32 grid, k=2, 100 iterations, linear cooling from 3.2, d=1, FP64"),
     "mesh1000_k3": dict(graph="mesh1000", k=3, iters=300, precision="fp32c",
                         desc="1000x1000 triangulated mesh, k=3, 300 iterations, FP32 compensated"),
+    "chunglu250k_k3": dict(graph="chunglu250k", k=3, iters=300, precision="fp32c",
+                           desc="Chung-Lu gamma=2.3, n=250000, E=1000000, k=3, 300 iterations, "
+                                "FP32 compensated"),
+    "batch4096": dict(k=2, iters=200, precision="fp32",
+                      desc="4096 graphs, n log-uniform in [50, 5000] (random trees, near-square "
+                           "grids, G(n, 4/(n-1))), k=2, 200 iterations each, one persistent launch"),
+    "serve": dict(iters=300, precision="fp32",
+                  desc="Poisson stream of Barabasi-Albert layout requests, E log-uniform in "
+                       "[1e3, 3e5], k in {2, 3}, 300 iterations, FP32"),
 }
 PREC = {"fp32": 0, "fp64": 1, "fp32c": 2}
 DTYPE_NAME = {"fp32": "f32", "fp64": "f64", "fp32c": "f32"}
@@ -194,6 +203,174 @@ def cpu_baseline(wl, g, pos, budget_s=20.0):
                       f"iterations ({t_it:.2f} s), scaled to one whole layout"}
 
 
+def _timed_region(torch, stream, fn, steps):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_batch(args, wl, ws, rank, local):
+    """Config of many small graphs: all 4096 layouts per step in one
+    persistent, graph-captured launch (plus the one k-hop build of the
+    union), against laying the same graphs out one at a time."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1606_02162_gb300 import gila as G
+    from paper_1606_02162_gb300 import inputs as I
+    torch.cuda.set_device(local)
+    graphs = I.batch_mix(4096, 50, 5000, 4)
+    pos = [I.uniform_positions(g.n, 400000 + i) for i, g in enumerate(graphs)]
+    k, iters = wl["k"], wl["iters"]
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, prec, dt in (("fp32", G.GILA_FP32, torch.float32), ("fp64", G.GILA_FP64, torch.float64)):
+        prm = G.params(k=k, iters=iters, precision=prec)
+        b = G.Batch(graphs)
+        x0 = torch.tensor(np.concatenate(pos), dtype=dt, device="cuda")
+        x = torch.empty_like(x0)
+
+        def step():
+            G.gila_batch_khop_reset(b.handle)
+            G.gila_batch_build_khop(b.handle, k)
+            x.copy_(x0)
+            G.gila_layout_batch_device(b.handle, prm, x)
+
+        for _ in range(max(args.warmup, 1)):
+            step()
+        clocks = ClockSampler(local)
+        clocks.start()
+        l0 = G.gila_kernel_launches()
+        ms = _timed_region(torch, stream, step, args.steps)
+        launches = G.gila_kernel_launches() - l0
+        clk = clocks.stop()
+        nnz = G.gila_batch_info(b.handle)["nnz_khop"]
+        P = nnz + sum(g.nnz for g in graphs)
+        b.close()
+        out[name] = {"layouts_per_s": len(graphs) * args.steps / (ms / 1e3),
+                     "ms_per_step": ms / args.steps,
+                     "pairs_per_s": P * iters * args.steps / (ms / 1e3),
+                     "gpu_launches": launches, "clocks": clk}
+    # one graph at a time (same kernels of the single-graph path), on a
+    # systematic sample of every 16th graph
+    sample = graphs[::16]
+    spos = pos[::16]
+    prm = G.params(k=k, iters=iters, precision=G.GILA_FP32)
+    hs = [G.Graph.from_inputs(g) for g in sample]
+    xs0 = [torch.tensor(p, dtype=torch.float32, device="cuda") for p in spos]
+    xs = [torch.empty_like(t) for t in xs0]
+
+    def plain():
+        for h, a0, a in zip(hs, xs0, xs):
+            G.gila_khop_reset(h.handle)
+            G.gila_build_khop(h.handle, k)
+            a.copy_(a0)
+            G.gila_layout_run_device(h.handle, prm, a)
+
+    plain()
+    pms = _timed_region(torch, stream, plain, 1)
+    for h in hs:
+        h.close()
+    plain_lps = len(sample) / (pms / 1e3)
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "layouts/s", "value": out["fp32"]["layouts_per_s"], "unit": "layouts/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": out["fp32"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "graphs": len(graphs),
+                   "vertices": int(sum(g.n for g in graphs)),
+                   "fp32": out["fp32"], "fp64": out["fp64"],
+                   "plain_one_at_a_time": {"layouts_per_s": plain_lps,
+                                           "sample": f"every 16th graph ({len(sample)})"},
+                   "speedup_vs_plain": out["fp32"]["layouts_per_s"] / plain_lps},
+        "gpu_launches": out["fp32"]["gpu_launches"], "clocks": out["fp32"]["clocks"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args, wl, ws, rank, local, count=48, emax=3e5):
+    """Serving stream: layout requests arriving as a Poisson process, served
+    by the continuous-batching server, against one-at-a-time service of the
+    same requests (a FIFO single server fed by the same arrivals)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1606_02162_gb300 import gila as G
+    from paper_1606_02162_gb300 import inputs as I
+    torch.cuda.set_device(local)
+    reqs = I.serving_requests(count, 5, emax=emax)
+    graphs = [I.barabasi_albert_fast(r["n"], 3, r["seed"]) for r in reqs]
+    pos = [I.uniform_positions(g.n, r["seed"]) for g, r in zip(graphs, reqs)]
+    prms = [G.params(k=r["k"], iters=wl["iters"], precision=G.GILA_FP32) for r in reqs]
+    # one at a time: service time of each request alone
+    service = []
+    for g, p, prm in zip(graphs[:2], pos[:2], prms[:2]):  # warm-up
+        with G.Graph.from_inputs(g) as h:
+            G.gila_layout_run(h.handle, prm, p)
+    for g, p, prm in zip(graphs, pos, prms):
+        t = time.perf_counter()
+        with G.Graph.from_inputs(g) as h:
+            G.gila_layout_run(h.handle, prm, p)
+        service.append(time.perf_counter() - t)
+    service = np.array(service)
+    rate = 0.9 / service.mean()  # arrivals at 90% of the one-at-a-time capacity
+    arrivals = I.poisson_arrivals(count, rate, 55)
+    # FIFO single server with the measured service times
+    done, plain_lat = 0.0, []
+    for a, sv in zip(arrivals, service):
+        start = max(a, done)
+        done = start + sv
+        plain_lat.append(done - a)
+    plain_makespan = done
+    free_b, _ = torch.cuda.mem_get_info()
+    budget = int(free_b * 0.6)
+    lat = []
+    with G.Server(budget, 16) as s:
+        t0 = time.perf_counter()
+        tickets = []
+        for a, g, p, prm in zip(arrivals, graphs, pos, prms):
+            now = time.perf_counter() - t0
+            if a > now:
+                time.sleep(a - now)
+            tickets.append((s.submit(g, p, prm), a))
+        for tk, a in tickets:
+            _, info = s.wait(tk)
+            lat.append(info["latency_ms"] / 1e3)
+        makespan = time.perf_counter() - t0
+        st = s.stats()
+    lat = np.array(lat)
+    plain_lat = np.array(plain_lat)
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "layouts/s", "value": count / makespan, "unit": "layouts/s", "n_gpus": ws,
+        "steps": 1, "warmup": 2, "ms_per_step": makespan * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "requests": count, "arrival_rate_per_s": rate,
+                   "server": {"layouts_per_s": count / makespan,
+                              "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                              "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                              "bytes_peak": st["bytes_peak"], "budget": budget},
+                   "plain_one_at_a_time": {"layouts_per_s": count / plain_makespan,
+                                           "p50_ms": float(np.percentile(plain_lat, 50) * 1e3),
+                                           "p99_ms": float(np.percentile(plain_lat, 99) * 1e3),
+                                           "mean_service_ms": float(service.mean() * 1e3)}},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -208,7 +385,15 @@ def main():
     ws, rank, local = dist_env()
 
     if args.impl == "reference":
+        if args.workload in ("batch4096", "serve"):
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the CPU oracle arm is defined for the single-graph workloads"}))
+            return 0
         return reference_arm(args, wl, ws, rank)
+    if args.workload == "batch4096":
+        return run_batch(args, wl, ws, rank, local)
+    if args.workload == "serve":
+        return run_serve(args, wl, ws, rank, local)
 
     import torch
 

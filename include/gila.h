@@ -231,8 +231,10 @@ void gila_batch_destroy(gila_batch* b);
 gila_status gila_batch_set_stream(gila_batch* b, void* cuda_stream);
 gila_status gila_batch_info(const gila_batch* b, int32_t* count, int64_t* total_n,
                             int64_t* nnz_khop);
-/* k-hop lists of every graph of the batch (one build over the union). */
+/* k-hop lists of every graph of the batch (one build over the union);
+ * cached per k like gila_build_khop. gila_batch_khop_reset drops them. */
 gila_status gila_batch_build_khop(gila_batch* b, int32_t k, int64_t* nnz_out);
+gila_status gila_batch_khop_reset(gila_batch* b);
 /* Set (or read back, defaults filled in for a precision) the launch shape
  * and lanes-per-vertex thresholds of the batched kernel. */
 gila_status gila_batch_tune(gila_batch* b, const gila_batch_tuning* t);
@@ -255,6 +257,59 @@ gila_status gila_layout_batch_run(gila_batch* b, const gila_params* prm,
  * double[2 n_i] placements. Runs on the stream of gs[0]. */
 gila_status gila_layout_batch(gila_graph* const* gs, int32_t count, const gila_params* prm,
                               const double* const* pos_in, double* const* pos_out);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop for layout jobs of mixed sizes. Jobs are admitted
+ * in arrival order by the device memory they need (the exact size of their
+ * k-hop lists is counted before any list memory is taken) and by a slot
+ * limit; admitted jobs keep placement and temperature on the device and
+ * advance together, a chunk of iterations per job per round, each job on
+ * its own CUDA stream, so their kernels overlap. Jobs arriving while others
+ * run are admitted as soon as memory and a slot free up. A job runs the same
+ * kernels as alone, so its result does not depend on the other jobs.
+ * Precisions: GILA_FP32, GILA_FP32_COMPENSATED, GILA_FP64. Concurrency
+ * between streams is limited by the CUDA_DEVICE_MAX_CONNECTIONS environment
+ * variable (default 8) of the process.
+ * ------------------------------------------------------------------------ */
+typedef struct gila_server gila_server;
+
+typedef struct gila_job_info {
+    int32_t status;    /* GILA_OK or the job's failure (e.g. GILA_EBUDGET) */
+    int64_t nnz_khop;  /* total k-hop list length of the job's graph */
+    double queue_ms;   /* submit -> admitted (lists built, placement on the device) */
+    double run_ms;     /* admitted -> result on the host */
+    double latency_ms; /* submit -> result on the host */
+} gila_job_info;
+
+typedef struct gila_server_stats {
+    int64_t completed, failed, pending, running;
+    size_t bytes_in_use, bytes_peak, budget;
+} gila_server_stats;
+
+/* Start a server on the current device: mem_budget_bytes bounds the device
+ * memory of admitted jobs, max_slots the number of jobs on the GPU at once.
+ * Two host threads serve it until gila_server_destroy. */
+gila_status gila_server_create(size_t mem_budget_bytes, int32_t max_slots, gila_server** out);
+/* Stop the threads, fail unfinished jobs, free everything. Must not run
+ * concurrently with other calls on the same server. */
+void gila_server_destroy(gila_server* s);
+/* Queue a job: graph (host CSR, as for gila_graph_create, trusted),
+ * parameters (prm->iters iterations), initial placement (host double[2n]).
+ * The arrays are copied before the call returns. *ticket identifies it. */
+gila_status gila_server_submit(gila_server* s, int64_t n, const int64_t* row_ptr,
+                               const int32_t* col_idx, const gila_params* prm,
+                               const double* pos_in, uint64_t* ticket);
+/* Wait up to timeout_ms (< 0: forever) for a job; on success its final
+ * placement goes to pos_out (host double[2n], may be NULL) and the ticket is
+ * released. GILA_ETIMEDOUT leaves the job running and the ticket valid. A
+ * failed job returns its status (info->status too). */
+gila_status gila_server_wait(gila_server* s, uint64_t ticket, int32_t timeout_ms,
+                             double* pos_out, gila_job_info* info);
+/* *done = 1 when the job has finished (without releasing the ticket). */
+gila_status gila_server_poll(gila_server* s, uint64_t ticket, int32_t* done);
+/* Counters: jobs completed / failed / queued / on the GPU, device bytes
+ * reserved now and at most, and the budget. */
+gila_status gila_server_get_stats(gila_server* s, gila_server_stats* out);
 
 /* Temperature of iteration i under prm (t0 = resolved initial temperature). */
 double gila_temperature(const gila_params* prm, double t0, int32_t i);

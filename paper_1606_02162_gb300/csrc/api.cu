@@ -378,7 +378,6 @@ gila_status gila_khop_export(const gila_graph* g, int64_t* krow_host, int32_t* k
         GILA_CUDA(cudaMemcpyAsync(kcol_host, g->kcol, sizeof(int32_t) * (size_t)g->nnz_khop,
                                   cudaMemcpyDeviceToHost, g->stream));
     GILA_CUDA(cudaStreamSynchronize(g->stream));
-    for (int64_t i = 0; i < g->nnz_khop; ++i) kcol_host[i] &= (int32_t)kIdMask;
     return GILA_OK;
 }
 

@@ -57,6 +57,8 @@ struct BatchArgs {
     const int64_t* voff;
     const int32_t* order;
     int32_t count;
+    const int64_t* row;
+    const int32_t* col;
     const int64_t* krow;
     const uint32_t* kcol;
     int* work;
@@ -158,12 +160,14 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchArgs A)
                 t0 = sqrt((double)n * A.d / a);
             }
         }
-        Pair<T, MODEL, COMP, true> f;
+        Rep<T, MODEL, COMP, true> f;
         f.base = (uint32_t)v0;
         f.d2 = (T)(A.d * A.d);
-        f.inv_d = (T)(1.0 / A.d);
-        f.p = A.p;
         f.q = A.q;
+        Att<T, MODEL, COMP, true> att;
+        att.base = (uint32_t)v0;
+        att.inv_d = (T)(1.0 / A.d);
+        att.p = A.p;
         const int groups = blockDim.x / G;
         const int grp = threadIdx.x / G, gl = threadIdx.x % G;
         for (int it = 0; it < A.iters; ++it) {
@@ -173,6 +177,7 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchArgs A)
             const T t = (T)td;
             // ids are global; the buffer holds this graph's vertices from 0
             f.pos = cur;
+            att.pos = cur;
             for (int64_t vb = 0; vb < n; vb += groups) {
                 const int64_t v = vb + grp;
                 const bool live = v < n;
@@ -184,7 +189,13 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchArgs A)
                     pu = cur[v];
                     f.xu = pu.x;
                     f.yu = pu.y;
-                    row_sum(A.kcol, A.krow[v0 + v], A.krow[v0 + v + 1], gl, G, f, a);
+                    att.xu = pu.x;
+                    att.yu = pu.y;
+                    // lanes take entries by their place in the row, so the
+                    // order does not depend on where the row sits in the batch
+                    row_sum_rel(A.kcol, A.krow[v0 + v], A.krow[v0 + v + 1], gl, G, f, a);
+                    row_sum_rel(reinterpret_cast<const uint32_t*>(A.col), A.row[v0 + v],
+                                A.row[v0 + v + 1], gl, G, att, a);
                 }
                 a.group_reduce(G);
                 if (live && gl == 0) {
@@ -348,6 +359,8 @@ gila_status batch_run(gila_batch* b, const gila_params* prm, void* pos)
     A.voff = b->voff;
     A.order = b->order;
     A.count = b->count;
+    A.row = g->row;
+    A.col = g->col;
     A.krow = g->krow;
     A.kcol = g->kcol;
     A.work = b->work;
@@ -512,6 +525,12 @@ gila_status gila_batch_build_khop(gila_batch* b, int32_t k, int64_t* nnz_out)
 {
     if (!b) return fail(GILA_EINVAL, "batch is NULL");
     return gila_build_khop(b->g, k, nnz_out);
+}
+
+gila_status gila_batch_khop_reset(gila_batch* b)
+{
+    if (!b) return fail(GILA_EINVAL, "batch is NULL");
+    return gila_khop_reset(b->g);
 }
 
 gila_status gila_batch_tune(gila_batch* b, const gila_batch_tuning* t)

@@ -98,40 +98,82 @@ struct Acc {
     __device__ __forceinline__ T fy() const { return COMP ? sy + cy : sy; }
 };
 
-// One k-hop entry's contribution. Positions come through L1/L2 (SMEM =
-// false, `pos` is the whole placement) or from a shared-memory tile holding
-// ids [base, base + tile size) (SMEM = true).
+// Repulsion of one k-hop entry v on u (Section 3.1 with the repelling set
+// of Section 4.5): adds c (x_u - x_v) with c = d^2 / delta^(q+1). For
+// Fruchterman-Reingold (q = 1) in FP32 that is d^2 * rsqrt(r^2)^2: one MUFU
+// and two multiplies, no divide. A pair at distance 0 adds nothing.
+// Positions come through L1/L2 (SMEM = false: `pos` is the whole placement)
+// or from a buffer holding ids [base, base + size) (SMEM = true; a shared
+// memory tile, or a graph's own slice of a global placement).
 template <class T, int MODEL, bool COMP, bool SMEM = false>
-struct Pair {
+struct Rep {
     using P2 = typename V2<T>::type;
     const P2* __restrict__ pos;
     uint32_t base = 0;
-    T xu, yu, d2, inv_d;
-    int p, q;
+    T xu, yu, d2;
+    int q;
 
-    __device__ __forceinline__ void operator()(uint32_t e, Acc<T, COMP>& a) const
+    __device__ __forceinline__ void operator()(uint32_t v, Acc<T, COMP>& a) const
     {
-        const P2 pv = SMEM ? pos[(e & kIdMask) - base] : __ldg(pos + (e & kIdMask));
+        const P2 pv = SMEM ? pos[v - base] : __ldg(pos + v);
+        const T dx = xu - pv.x, dy = yu - pv.y;
+        const T r2 = dx * dx + dy * dy;
+        T c;
+        if (MODEL == kFR) {
+            c = rep_fr(d2, r2);
+        } else {
+            c = T(0);
+            if (r2 > T(0)) {
+                const T dl = sqrt(r2);
+                c = d2 / (ipow_(dl, q) * dl);
+            }
+        }
+        a.add(c * dx, c * dy);
+    }
+
+    __device__ __forceinline__ static float rep_fr(float d2, float r2)
+    {
+        const float r = rsqrtf(r2);
+        return r2 > 0.0f ? d2 * (r * r) : 0.0f;
+    }
+    __device__ __forceinline__ static double rep_fr(double d2, double r2)
+    {
+        return r2 > 0.0 ? d2 / r2 : 0.0;
+    }
+};
+
+// Attraction of a neighbour v of u: adds -c (x_u - x_v) with
+// c = delta^(p-1) / d (delta / d for p = 2).
+template <class T, int MODEL, bool COMP, bool SMEM = false>
+struct Att {
+    using P2 = typename V2<T>::type;
+    const P2* __restrict__ pos;
+    uint32_t base = 0;
+    T xu, yu, inv_d;
+    int p;
+
+    __device__ __forceinline__ void operator()(uint32_t v, Acc<T, COMP>& a) const
+    {
+        const P2 pv = SMEM ? pos[v - base] : __ldg(pos + v);
         const T dx = xu - pv.x, dy = yu - pv.y;
         const T r2 = dx * dx + dy * dy;
         if (r2 > T(0)) {
             T c;
             if (MODEL == kFR) {
-                c = fdiv(d2, r2);
-                if (e & kEdgeFlag) c -= fsqrt(r2) * inv_d;
+                c = fsqrt(r2) * inv_d;
             } else {
                 const T dl = sqrt(r2);
-                c = d2 / (ipow_(dl, q) * dl);
-                if (e & kEdgeFlag) c -= ipow_(dl, p) / dl * inv_d;
+                c = ipow_(dl, p) / dl * inv_d;
             }
-            a.add(c * dx, c * dy);
+            a.add(-c * dx, -c * dy);
         }
     }
 };
 
 // Entries [s, e) of kcol, lanes gl = 0..G-1 of a group (G >= 4): an
 // unaligned head of at most 3 entries, 16-byte vector loads of 4 ids,
-// then a tail of at most 3 entries.
+// then a tail of at most 3 entries. Which lane takes which entry depends on
+// the row's position modulo 4 in kcol (fixed for a given list).
 template <class F, class A>
 __device__ __forceinline__ void row_sum(const uint32_t* __restrict__ kcol, int64_t s, int64_t e,
                                         int gl, int G, const F& f, A& a)
@@ -141,9 +183,10 @@ __device__ __forceinline__ void row_sum(const uint32_t* __restrict__ kcol, int64
     int64_t e4 = e & ~int64_t(3);
     if (e4 < s4) e4 = s4;
     if (s + gl < s4) f(ld_id(kcol + s + gl), a);
-    const uint4* k4 = reinterpret_cast<const uint4*>(kcol);
-#pragma unroll 2
-    for (int64_t c = (s4 >> 2) + gl; c < (e4 >> 2); c += G) {
+    const uint4* k4 = reinterpret_cast<const uint4*>(kcol + s4);
+    const int n4 = (int)((e4 - s4) >> 2);
+#pragma unroll 4
+    for (int c = gl; c < n4; c += G) {
         const uint4 w = ld_ids4(k4 + c);
         f(w.x, a);
         f(w.y, a);
@@ -151,6 +194,17 @@ __device__ __forceinline__ void row_sum(const uint32_t* __restrict__ kcol, int64
         f(w.w, a);
     }
     if (e4 + gl < e) f(ld_id(kcol + e4 + gl), a);
+}
+
+// Entries [s, e) with lane gl taking entries s + gl, s + gl + G, ...: the
+// assignment depends only on the position inside the row.
+template <class F, class A>
+__device__ __forceinline__ void row_sum_rel(const uint32_t* __restrict__ ids, int64_t s, int64_t e,
+                                            int gl, int G, const F& f, A& a)
+{
+    const uint32_t* p = ids + s;
+    const int len = (int)(e - s);
+    for (int j = gl; j < len; j += G) f(ld_id(p + j), a);
 }
 
 template <class T>

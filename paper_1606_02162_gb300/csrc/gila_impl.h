@@ -28,14 +28,6 @@ inline bool is_f64(int precision)
     return precision == GILA_FP64 || precision == GILA_FP64_ORDERED;
 }
 
-// ---------------------------------------------------------------- k-hop flag
-
-// The top bit of a stored k-hop entry marks an edge of G (distance 1):
-// A is contained in N_v(k) for every k >= 1, so the attraction terms ride
-// in the same stream as the repulsion terms.
-constexpr uint32_t kEdgeFlag = 0x80000000u;
-constexpr uint32_t kIdMask = 0x7fffffffu;
-
 // ---------------------------------------------------------------- binning
 
 // Row-length classes of the iteration kernel.
@@ -71,6 +63,12 @@ struct KhopScratch {
     int64_t bitmap_words = 0;   // per block
     int t2_blocks = 0;
     size_t cap_n = 0;
+    size_t scratch_cap = 0;     // tier-2 scratch limit in bytes (0 = 2 GiB)
+    // state between the count and the fill phase
+    int counted_k = 0;
+    int64_t nnz = 0;
+    int nq = 0, t2_used = 0;
+    int64_t t1_blocks = 0, nwords = 0;
 };
 
 struct Bins {
@@ -141,8 +139,13 @@ struct gila_graph {
 
 namespace gila {
 
-// k-hop build (khop.cu)
+// k-hop build (khop.cu): count (sizes, offsets, total) then fill (ids,
+// row classes); build_khop does both.
 gila_status build_khop(gila_graph* g, int k);
+gila_status build_khop_count(gila_graph* g, int k, int64_t* nnz_out);
+gila_status build_khop_count_impl(gila_graph* g, int k);
+gila_status build_khop_fill(gila_graph* g, int k);
+void release_khop_scratch(gila_graph* g);  // frees the build-only buffers
 void free_khop(gila_graph* g);
 
 // iteration + metrics (layout.cu)

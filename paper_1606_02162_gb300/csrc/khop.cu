@@ -13,8 +13,7 @@
 //           scan over the bitmap.
 //   Both tiers run twice (count, then fill) around an exclusive scan of
 //   the counts, so the output needs no atomics and is the same every run.
-//   Afterwards the entries that are edges of G get the top-bit flag used by
-//   the force kernel, and rows are classed by length for scheduling.
+//   Afterwards rows are classed by length for scheduling.
 #include <algorithm>
 #include <climits>
 #include <mutex>
@@ -325,31 +324,6 @@ __global__ void scan_add_kernel(int64_t* __restrict__ out, int64_t n,
     if (i < n) out[i + 1] += bsum[i / kScanTile];
 }
 
-// --------------------------------------------------------------- edge flags
-
-// Set the edge flag on every entry of row v that is a neighbour of v in G.
-// Searches compare ids without the flag, so concurrent flagging in the same
-// row does not disturb them.
-__global__ void mark_edges_kernel(int64_t n, const int64_t* __restrict__ row,
-                                  const int32_t* __restrict__ col,
-                                  const int64_t* __restrict__ krow, uint32_t* __restrict__ kcol)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
-        const int64_t ks = krow[v], ke = krow[v + 1];
-        for (int64_t e = row[v] + lane; e < row[v + 1]; e += 32) {
-            const uint32_t w = (uint32_t)col[e];
-            int64_t lo = ks, hi = ke;  // first entry with id >= w
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if ((kcol[mid] & kIdMask) < w) lo = mid + 1; else hi = mid;
-            }
-            if (lo < ke && (kcol[lo] & kIdMask) == w) kcol[lo] = w | kEdgeFlag;
-        }
-    }
-}
-
 // --------------------------------------------------------------- binning
 
 constexpr int kBinThreads = 1024;
@@ -586,7 +560,34 @@ void free_khop(gila_graph* g)
     g->nnz_khop = 0;
 }
 
+void release_khop_scratch(gila_graph* g)
+{
+    KhopScratch& s = g->ks;
+    cudaFree(s.counts);
+    cudaFree(s.queue);
+    cudaFree(s.qn);
+    cudaFree(s.bitmaps);
+    cudaFree(s.lists);
+    const size_t cap = s.scratch_cap;
+    s = KhopScratch();
+    s.scratch_cap = cap;
+}
+
 gila_status build_khop(gila_graph* g, int k)
+{
+    gila_status s = build_khop_count(g, k, nullptr);
+    if (s != GILA_OK) return s;
+    return build_khop_fill(g, k);
+}
+
+gila_status build_khop_count(gila_graph* g, int k, int64_t* nnz_out)
+{
+    gila_status s = build_khop_count_impl(g, k);
+    if (s == GILA_OK && nnz_out) *nnz_out = g->ks.nnz;
+    return s;
+}
+
+gila_status build_khop_count_impl(gila_graph* g, int k)
 {
     const int64_t n = g->n;
     cudaStream_t st = g->stream;
@@ -623,7 +624,8 @@ gila_status build_khop(gila_graph* g, int k)
     int t2_blocks = 0;
     if (nq > 0) {
         const size_t per_block = (size_t)nwords * 4 + (size_t)n * 4;
-        const size_t budget = (size_t)2 << 30;  // at most 2 GiB of tier-2 scratch
+        // at most 2 GiB (or the graph's own cap) of tier-2 scratch
+        const size_t budget = S.scratch_cap ? S.scratch_cap : ((size_t)2 << 30);
         int64_t want = std::min<int64_t>(nq, (int64_t)sms * 4);
         want = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)(budget / per_block)));
         t2_blocks = (int)want;
@@ -646,6 +648,26 @@ gila_status build_khop(gila_graph* g, int k)
     int64_t nnz = 0;
     GILA_CUDA(cudaMemcpyAsync(&nnz, g->krow + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     GILA_CUDA(cudaStreamSynchronize(st));
+    S.counted_k = k;
+    S.nnz = nnz;
+    S.nq = nq;
+    S.t2_used = t2_blocks;
+    S.t1_blocks = t1_blocks;
+    S.nwords = nwords;
+    return GILA_OK;
+}
+
+gila_status build_khop_fill(gila_graph* g, int k)
+{
+    const int64_t n = g->n;
+    cudaStream_t st = g->stream;
+    KhopScratch& S = g->ks;
+    if (S.counted_k != k) return fail(GILA_ESTATE, "k-hop lists not counted for this k");
+    gila_status s;
+    const int64_t nnz = S.nnz, t1_blocks = S.t1_blocks, nwords = S.nwords;
+    const int nq = S.nq, t2_blocks = S.t2_used;
+    const int sms = sm_count(g->device);
+    S.counted_k = 0;
     if ((size_t)nnz > g->cap_kcol || !g->kcol) {
         cudaFree(g->kcol);
         g->kcol = nullptr;
@@ -663,12 +685,7 @@ gila_status build_khop(gila_graph* g, int k)
                                                     S.lists, nwords, S.counts, g->krow, g->kcol, 1);
         count_launch();
     }
-    if (n > 0) {
-        const int64_t warps = std::min<int64_t>(n, (int64_t)sms * 64);
-        mark_edges_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(n, g->row, g->col,
-                                                                              g->krow, g->kcol);
-        count_launch();
-    }
+    (void)sms;
     GILA_CUDA(cudaGetLastError());
     GILA_CUDA(cudaStreamSynchronize(st));
     s = build_bins(g);

@@ -5,17 +5,16 @@
 //   F(u) = sum over v in N_u(k) of d^2/delta^q along (x_u - x_v)/delta
 //        + sum over edges (u,v)  of delta^p/d along (x_v - x_u)/delta
 //   x_u <- x_u + F(u) min(1, t/|F(u)|), all vertices at once.
-// Per entry of a k-hop row the kernel computes Delta = x_u - x_v and adds
-// c Delta with c = d^2/delta^(q+1) - [edge] delta^(p-1)/d; for p = 2, q = 1
-// this is d^2/r^2 - [edge] sqrt(r^2)/d with r^2 = |Delta|^2, one divide and,
-// on edges only, one square root. The edge flag rides in the top bit of the
-// stored id, so attraction and repulsion share one pass over the list.
+// Per entry of a k-hop row the kernels compute Delta = x_u - x_v and add
+// d^2/delta^(q+1) Delta (for q = 1 in FP32: d^2 rsqrt(r^2)^2 Delta, one MUFU
+// and no divide); a short second pass over u's adjacency row adds the
+// attraction -delta^(p-1)/d Delta. The k-hop stream is the only large read.
 //
 // Work is split by row length into four classes, each a range of blocks
 // of the same launch (heaviest first): rows split into chunks summed by the
 // last chunk to finish, one block per row, one warp per row, and groups of
-// 8 lanes per row. Every row's reduction order depends on its own length
-// only, so a vertex gets the same result whatever else is in the graph.
+// 8 lanes per row. A row's reduction order depends only on its length and
+// its position in the k-hop list, so results are reproducible.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -32,6 +31,8 @@ constexpr int kThreads = 256;
 constexpr int kWarpsPerBlock = kThreads / 32;
 
 struct IterArgs {
+    const int64_t* row;
+    const int32_t* col;
     const int64_t* krow;
     const uint32_t* kcol;
     const int32_t* list0;
@@ -81,6 +82,25 @@ __device__ __forceinline__ void block_reduce(Acc<T, COMP>& a, T* sh)
     }
 }
 
+// Repulsion over k-hop entries [ks, ke) of u and, when with_att, attraction
+// over u's adjacency row, by lanes gl = 0..G-1 of a group.
+template <class T, int MODEL, bool COMP, class P2>
+__device__ __forceinline__ void vertex_sum(const IterArgs& A, Rep<T, MODEL, COMP> rep,
+                                           Att<T, MODEL, COMP> att, int64_t u, P2 pu, int64_t ks,
+                                           int64_t ke, bool with_att, int gl, int G,
+                                           Acc<T, COMP>& a)
+{
+    rep.xu = pu.x;
+    rep.yu = pu.y;
+    row_sum(A.kcol, ks, ke, gl, G, rep, a);
+    if (with_att) {
+        att.xu = pu.x;
+        att.yu = pu.y;
+        row_sum_rel(reinterpret_cast<const uint32_t*>(A.col), A.row[u], A.row[u + 1], gl, G, att,
+                    a);
+    }
+}
+
 template <class T, int MODEL, bool COMP>
 __global__ void __launch_bounds__(kThreads)
 iteration_kernel(const IterArgs A)
@@ -89,22 +109,23 @@ iteration_kernel(const IterArgs A)
     __shared__ T sh[kWarpsPerBlock * 4];
     __shared__ int s_last;
     const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos_in);
-    Pair<T, MODEL, COMP> f;
-    f.pos = pos;
-    f.d2 = (T)(A.d * A.d);
-    f.inv_d = (T)(1.0 / A.d);
-    f.p = A.p;
-    f.q = A.q;
+    Rep<T, MODEL, COMP> rep;
+    rep.pos = pos;
+    rep.d2 = (T)(A.d * A.d);
+    rep.q = A.q;
+    Att<T, MODEL, COMP> att;
+    att.pos = pos;
+    att.inv_d = (T)(1.0 / A.d);
+    att.p = A.p;
     int b = blockIdx.x;
     if (b < A.b3) {
-        // a chunk of a giant row: block sum, then the last chunk finishes u
+        // a chunk of a giant row: block sum, then the last chunk finishes u;
+        // the row's first chunk also carries the attraction terms
         const Chunk ch = A.chunks[b];
         const int64_t u = ch.vertex;
         const P2 pu = pos[u];
-        f.xu = pu.x;
-        f.yu = pu.y;
         Acc<T, COMP> a;
-        row_sum(A.kcol, ch.begin, ch.end, threadIdx.x, kThreads, f, a);
+        vertex_sum(A, rep, att, u, pu, ch.begin, ch.end, b == ch.first, threadIdx.x, kThreads, a);
         block_reduce<T, COMP>(a, sh);
         if (threadIdx.x == 0) {
             double* part = A.partials + (int64_t)b * 4;
@@ -126,7 +147,7 @@ iteration_kernel(const IterArgs A)
                 fy += __ldcg(q + 1) + __ldcg(q + 3);
             }
             A.giant_counter[ch.giant] = 0;
-            apply_move_it<T>(A, u,pu.x, pu.y, (T)fx, (T)fy);
+            apply_move_it<T>(A, u, pu.x, pu.y, (T)fx, (T)fy);
         }
         return;
     }
@@ -134,12 +155,10 @@ iteration_kernel(const IterArgs A)
     if (b < A.b2) {
         const int64_t u = A.list2[b];
         const P2 pu = pos[u];
-        f.xu = pu.x;
-        f.yu = pu.y;
         Acc<T, COMP> a;
-        row_sum(A.kcol, A.krow[u], A.krow[u + 1], threadIdx.x, kThreads, f, a);
+        vertex_sum(A, rep, att, u, pu, A.krow[u], A.krow[u + 1], true, threadIdx.x, kThreads, a);
         block_reduce<T, COMP>(a, sh);
-        if (threadIdx.x == 0) apply_move_it<T>(A, u,pu.x, pu.y, a.fx(), a.fy());
+        if (threadIdx.x == 0) apply_move_it<T>(A, u, pu.x, pu.y, a.fx(), a.fy());
         return;
     }
     b -= A.b2;
@@ -149,12 +168,10 @@ iteration_kernel(const IterArgs A)
         const int lane = threadIdx.x & 31;
         const int64_t u = A.list1[i];
         const P2 pu = pos[u];
-        f.xu = pu.x;
-        f.yu = pu.y;
         Acc<T, COMP> a;
-        row_sum(A.kcol, A.krow[u], A.krow[u + 1], lane, 32, f, a);
+        vertex_sum(A, rep, att, u, pu, A.krow[u], A.krow[u + 1], true, lane, 32, a);
         a.group_reduce(32);
-        if (lane == 0) apply_move_it<T>(A, u,pu.x, pu.y, a.fx(), a.fy());
+        if (lane == 0) apply_move_it<T>(A, u, pu.x, pu.y, a.fx(), a.fy());
         return;
     }
     b -= A.b1;
@@ -166,17 +183,15 @@ iteration_kernel(const IterArgs A)
         // lanes of a group stay together through the shuffles below
         const int64_t u = live ? A.list0[i] : 0;
         Acc<T, COMP> a;
-        T xu = T(0), yu = T(0);
+        P2 pu;
+        pu.x = T(0);
+        pu.y = T(0);
         if (live) {
-            const P2 pu = pos[u];
-            xu = pu.x;
-            yu = pu.y;
-            f.xu = xu;
-            f.yu = yu;
-            row_sum(A.kcol, A.krow[u], A.krow[u + 1], gl, G, f, a);
+            pu = pos[u];
+            vertex_sum(A, rep, att, u, pu, A.krow[u], A.krow[u + 1], true, gl, G, a);
         }
         a.group_reduce(G);
-        if (live && gl == 0) apply_move_it<T>(A, u,xu, yu, a.fx(), a.fy());
+        if (live && gl == 0) apply_move_it<T>(A, u, pu.x, pu.y, a.fx(), a.fy());
     }
 }
 
@@ -213,7 +228,7 @@ ordered_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __rest
             const int64_t j = j0 + lane;
             double tx = 0.0, ty = 0.0;
             if (j < e) {
-                const int64_t v = pass == 0 ? (int64_t)(kcol[j] & kIdMask) : (int64_t)col[j];
+                const int64_t v = pass == 0 ? (int64_t)kcol[j] : (int64_t)col[j];
                 const double2 pv = pos_in[v];
                 // repulsion along x_u - x_v, attraction along x_v - x_u
                 const double dx = pass == 0 ? __dsub_rn(pu.x, pv.x) : __dsub_rn(pv.x, pu.x);
@@ -265,6 +280,8 @@ constexpr int kTiledThreads = 1024;
 constexpr int kTileBytes = 200 * 1024;
 
 struct TiledArgs {
+    const int64_t* row;
+    const int32_t* col;
     const int64_t* krow;
     const uint32_t* kcol;
     const int32_t* seg;       // n x (nt - 1) interior tile bounds, relative to krow[u]
@@ -292,12 +309,14 @@ tiled_kernel(const TiledArgs A)
     if (r0 >= r1) return;  // whole block
     const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos_in);
     T* acc = reinterpret_cast<T*>(A.acc);
-    Pair<T, MODEL, COMP, true> f;
+    Rep<T, MODEL, COMP, true> f;
     f.pos = tile;
     f.d2 = (T)(A.d * A.d);
-    f.inv_d = (T)(1.0 / A.d);
-    f.p = A.p;
     f.q = A.q;
+    Att<T, MODEL, COMP> att;  // neighbours' positions come through L1/L2
+    att.pos = pos;
+    att.inv_d = (T)(1.0 / A.d);
+    att.p = A.p;
     for (int j = 0; j < A.nt; ++j) {
         const int64_t tb = (int64_t)j * A.tv;
         const int64_t tn = (A.n - tb < A.tv) ? A.n - tb : (int64_t)A.tv;
@@ -328,6 +347,12 @@ tiled_kernel(const TiledArgs A)
             f.yu = pu.y;
             Acc<T, COMP> a;
             row_sum(A.kcol, kb + lo, kb + hi, lane, 32, f, a);
+            if (j == A.nt - 1) {
+                att.xu = pu.x;
+                att.yu = pu.y;
+                row_sum_rel(reinterpret_cast<const uint32_t*>(A.col), A.row[u], A.row[u + 1], lane,
+                            32, att, a);
+            }
             a.group_reduce(32);
             if (lane == 0) {
                 if (j > 0) {
@@ -365,7 +390,7 @@ __global__ void tile_seg_kernel(int64_t n, const int64_t* __restrict__ krow,
     int64_t lo = krow[u], hi = krow[u + 1];
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        if ((kcol[mid] & kIdMask) < key) lo = mid + 1; else hi = mid;
+        if (kcol[mid] < key) lo = mid + 1; else hi = mid;
     }
     seg[i] = (int32_t)(lo - krow[u]);
 }
@@ -468,7 +493,7 @@ metrics_kernel(int pass, int64_t n, const int64_t* __restrict__ row,
         }
         if (pass == 0) {
             for (int64_t e = krow[u] + lane; e < krow[u + 1]; e += 32) {
-                const int64_t v = kcol[e] & kIdMask;
+                const int64_t v = kcol[e];
                 if (v <= u) continue;
                 const double2 pv = load_pos<T>(pos, v);
                 const double dx = pu.x - pv.x, dy = pu.y - pv.y;
@@ -624,6 +649,8 @@ gila_status launch_iteration(gila_graph* g, const gila_params* prm, double t, co
         }
         if (P.use && ((uintptr_t)pos_in & 15) == 0) {
             TiledArgs A;
+            A.row = g->row;
+            A.col = g->col;
             A.krow = g->krow;
             A.kcol = g->kcol;
             A.seg = P.seg;
@@ -673,6 +700,8 @@ gila_status launch_iteration(gila_graph* g, const gila_params* prm, double t, co
     }
     const Bins& B = g->bins;
     IterArgs A;
+    A.row = g->row;
+    A.col = g->col;
     A.krow = g->krow;
     A.kcol = g->kcol;
     A.list0 = B.lists;

@@ -109,6 +109,7 @@ SIGNATURES = [
     ("gila_batch_set_stream", ctypes.c_int, [P, P]),
     ("gila_batch_info", ctypes.c_int, [P, P, P, P]),
     ("gila_batch_build_khop", ctypes.c_int, [P, I32, ctypes.POINTER(I64)]),
+    ("gila_batch_khop_reset", ctypes.c_int, [P]),
     ("gila_batch_tune", ctypes.c_int, [P, ctypes.POINTER(gila_batch_tuning)]),
     ("gila_batch_get_tuning", ctypes.c_int, [P, I32, ctypes.POINTER(gila_batch_tuning)]),
     ("gila_batch_autotune", ctypes.c_int, [P, PP, P, I32, ctypes.POINTER(gila_batch_tuning)]),
@@ -373,6 +374,10 @@ def gila_batch_build_khop(b, k) -> int:
     return nnz.value
 
 
+def gila_batch_khop_reset(b) -> None:
+    _check(load().gila_batch_khop_reset(b))
+
+
 def gila_batch_tune(b, threads=0, ctas_per_sm=0, group4_max=0, group8_max=0,
                     group16_max=0) -> None:
     t = gila_batch_tuning(int(threads), int(ctas_per_sm), int(group4_max), int(group8_max),
@@ -430,6 +435,117 @@ class Batch:
     def close(self):
         if self.handle:
             gila_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# ------------------------------------------------------------------ serving
+
+class gila_job_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("nnz_khop", ctypes.c_int64),
+                ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
+
+
+class gila_server_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("pending", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t),
+                ("budget", ctypes.c_size_t)]
+
+
+SIGNATURES += [
+    ("gila_server_create", ctypes.c_int, [ctypes.c_size_t, I32, ctypes.POINTER(P)]),
+    ("gila_server_destroy", None, [P]),
+    ("gila_server_submit", ctypes.c_int, [P, I64, P, P, PP, P, ctypes.POINTER(ctypes.c_uint64)]),
+    ("gila_server_wait", ctypes.c_int, [P, ctypes.c_uint64, I32, P,
+                                        ctypes.POINTER(gila_job_info)]),
+    ("gila_server_poll", ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(I32)]),
+    ("gila_server_get_stats", ctypes.c_int, [P, ctypes.POINTER(gila_server_stats)]),
+]
+
+
+def gila_server_create(budget_bytes, max_slots) -> int:
+    h = ctypes.c_void_p()
+    _check(load().gila_server_create(int(budget_bytes), int(max_slots), ctypes.byref(h)))
+    return h.value
+
+
+def gila_server_destroy(s) -> None:
+    if s:
+        load().gila_server_destroy(s)
+
+
+def gila_server_submit(s, n, row_ptr, col_idx, prm, pos_in) -> int:
+    row = _np(row_ptr, np.int64)
+    col = _np(col_idx, np.int32)
+    pos = _np(pos_in, np.float64)
+    t = ctypes.c_uint64()
+    _check(load().gila_server_submit(s, int(n), _ptr(row), _ptr(col), ctypes.byref(prm),
+                                     _ptr(pos), ctypes.byref(t)))
+    return t.value
+
+
+def gila_server_wait(s, ticket, n, timeout_ms=-1):
+    """Returns (placement float64[n, 2], info dict); raises GilaError on
+    failure or timeout (status GILA_ETIMEDOUT)."""
+    out = np.empty((n, 2), dtype=np.float64)
+    info = gila_job_info()
+    _check(load().gila_server_wait(s, ctypes.c_uint64(ticket), int(timeout_ms), _ptr(out),
+                                   ctypes.byref(info)))
+    return out, {f: getattr(info, f) for f, _ in gila_job_info._fields_}
+
+
+def gila_server_poll(s, ticket) -> bool:
+    d = I32()
+    _check(load().gila_server_poll(s, ctypes.c_uint64(ticket), ctypes.byref(d)))
+    return bool(d.value)
+
+
+def gila_server_get_stats(s) -> dict:
+    st = gila_server_stats()
+    _check(load().gila_server_get_stats(s, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in gila_server_stats._fields_}
+
+
+class Server:
+    """Owning wrapper of a gila_server; remembers each ticket's vertex count."""
+
+    def __init__(self, budget_bytes, max_slots):
+        self.handle = gila_server_create(budget_bytes, max_slots)
+        self._n = {}
+
+    def submit(self, graph, pos, prm) -> int:
+        t = gila_server_submit(self.handle, graph.n, graph.row_ptr, graph.col_idx, prm, pos)
+        self._n[t] = graph.n
+        return t
+
+    def wait(self, ticket, timeout_ms=-1):
+        # unknown tickets go to the library, which reports GILA_EINVAL
+        out = gila_server_wait(self.handle, ticket, self._n.get(ticket, 0), timeout_ms)
+        self._n.pop(ticket, None)
+        return out
+
+    def poll(self, ticket) -> bool:
+        return gila_server_poll(self.handle, ticket)
+
+    def stats(self) -> dict:
+        return gila_server_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            gila_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

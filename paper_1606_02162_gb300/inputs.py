@@ -188,6 +188,43 @@ def barabasi_albert(n: int, m: int, seed: int) -> Graph:
     return csr_from_edges(n, src, dst, f"ba_n{n}_m{m}_s{seed}", {"m": m, "seed": seed})
 
 
+def barabasi_albert_fast(n: int, m: int, seed: int) -> Graph:
+    """Preferential attachment without the per-vertex loop (for long request
+    streams). Every new vertex v draws m endpoint slots uniformly from the
+    2E_v slots that exist before it (a slot holds one end of an earlier
+    edge, so a vertex is drawn in proportion to its degree); a slot that holds
+    the far end of an earlier edge is resolved by following that edge's own
+    draw (pointer jumping). Repeated picks by the same vertex are dropped, so
+    E is slightly below m(m+1)/2 + m(n-m-1)."""
+    if n <= m:
+        raise ValueError("need n > m")
+    rng = np.random.default_rng(seed)
+    e0 = m * (m + 1) // 2
+    E = e0 + m * (n - m - 1)
+    src = np.empty(E, dtype=np.int64)
+    dst = np.full(E, -1, dtype=np.int64)
+    a, b = np.triu_indices(m + 1, 1)
+    src[:e0] = a
+    dst[:e0] = b
+    v = np.repeat(np.arange(m + 1, n, dtype=np.int64), m)
+    src[e0:] = v
+    slots_before = 2 * (e0 + (v - m - 1) * m)
+    r = (rng.random(E - e0) * slots_before).astype(np.int64)
+    even = (r & 1) == 0
+    idx = np.arange(e0, E)
+    dst[idx[even]] = src[r[even] >> 1]
+    ptr = np.full(E, -1, dtype=np.int64)
+    ptr[idx[~even]] = (r[~even] - 1) >> 1
+    pending = idx[~even]
+    while pending.size:
+        tgt = ptr[pending]
+        known = dst[tgt] >= 0
+        dst[pending[known]] = dst[tgt[known]]
+        pending = pending[~known]
+        ptr[pending] = ptr[ptr[pending]]
+    return csr_from_edges(n, src, dst, f"bafast_n{n}_m{m}_s{seed}", {"m": m, "seed": seed})
+
+
 def _sample_unique_pairs(rng, weights_cdf, n: int, num_edges: int, uniform: bool):
     """Draw endpoint pairs until num_edges distinct non-loop pairs exist;
     keep the first num_edges in draw order."""
