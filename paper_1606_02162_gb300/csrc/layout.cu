@@ -296,6 +296,39 @@ struct TiledArgs {
     void* disp_out;
 };
 
+// One row's segment for tile j: entries [s, e) of kcol; u < 0 when the
+// CTA's rows are exhausted.
+struct TSeg {
+    int64_t u, s, e;
+};
+
+__device__ __forceinline__ TSeg tiled_seg(const TiledArgs& A, int64_t r0, int64_t r1, int r, int j)
+{
+    TSeg z;
+    z.u = r0 + r;
+    if (z.u >= r1) {
+        z.u = -1;
+        z.s = z.e = 0;
+        return z;
+    }
+    const int64_t kb = A.krow[z.u];
+    const int64_t len = A.krow[z.u + 1] - kb;
+    z.s = kb + ((j == 0) ? 0 : A.seg[z.u * (A.nt - 1) + j - 1]);
+    z.e = kb + ((j == A.nt - 1) ? len : A.seg[z.u * (A.nt - 1) + j]);
+    return z;
+}
+
+// Ask L2 to fetch the 128-byte lines holding ids [s, e) (at most 16 KB),
+// one line per lane per step; nothing waits for these.
+__device__ __forceinline__ void prefetch_ids_l2(const uint32_t* kcol, int64_t s, int64_t e, int lane)
+{
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(kcol + s) & ~uintptr_t(127);
+    uintptr_t a1 = reinterpret_cast<uintptr_t>(kcol + e);
+    if (a1 > a0 + 16384) a1 = a0 + 16384;
+    for (uintptr_t a = a0 + (uintptr_t)lane * 128; a < a1; a += 32 * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 template <class T, int MODEL, bool COMP>
 __global__ void __launch_bounds__(kTiledThreads, 1)
 tiled_kernel(const TiledArgs A)
@@ -332,21 +365,25 @@ tiled_kernel(const TiledArgs A)
         if (threadIdx.x == 0) s_next = 0;
         __syncthreads();
         f.base = (uint32_t)tb;
-        for (;;) {
+        // Each warp holds its next assignment one step ahead: while it works
+        // on `cur`, the ids of `nxt` are pulled into L2 and the bounds of the
+        // one after are on their way.
+        auto grab = [&]() {
             int r = 0;
             if (lane == 0) r = atomicAdd(&s_next, 1);
-            r = __shfl_sync(kFull, r, 0);
-            const int64_t u = r0 + r;
-            if (u >= r1) break;  // warp-uniform
-            const int64_t kb = A.krow[u];
-            const int64_t len = A.krow[u + 1] - kb;
-            const int64_t lo = (j == 0) ? 0 : A.seg[u * (A.nt - 1) + j - 1];
-            const int64_t hi = (j == A.nt - 1) ? len : A.seg[u * (A.nt - 1) + j];
+            return __shfl_sync(kFull, r, 0);
+        };
+        TSeg cur = tiled_seg(A, r0, r1, grab(), j);
+        TSeg nxt = tiled_seg(A, r0, r1, grab(), j);
+        while (cur.u >= 0) {  // warp-uniform
+            if (nxt.u >= 0) prefetch_ids_l2(A.kcol, nxt.s, nxt.e, lane);
+            const TSeg after = tiled_seg(A, r0, r1, grab(), j);
+            const int64_t u = cur.u;
             const P2 pu = pos[u];
             f.xu = pu.x;
             f.yu = pu.y;
             Acc<T, COMP> a;
-            row_sum(A.kcol, kb + lo, kb + hi, lane, 32, f, a);
+            row_sum(A.kcol, cur.s, cur.e, lane, 32, f, a);
             if (j == A.nt - 1) {
                 att.xu = pu.x;
                 att.yu = pu.y;
@@ -373,6 +410,8 @@ tiled_kernel(const TiledArgs A)
                     apply_move<T>(A.t, A.pos_out, A.disp_out, u, pu.x, pu.y, a.fx(), a.fy());
                 }
             }
+            cur = nxt;
+            nxt = after;
         }
     }
 }
