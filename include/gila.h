@@ -173,7 +173,10 @@ gila_status gila_khop_export(const gila_graph* g, int64_t* krow_host, int32_t* k
  * needed. pos_in_dev and pos_out_dev are caller device arrays of n
  * float2 (FP32 modes) or double2 (GILA_FP64) and must not overlap.
  * disp_out_dev (may be NULL) receives the moves, same type. Asynchronous
- * on the graph's stream. */
+ * on the graph's stream. The iteration kernel bounds its waits for the
+ * shared-memory tile copies; a wait that gives up leaves that iteration's
+ * forces incomplete and is reported as GILA_ECUDA by the next
+ * gila_layout_run or gila_layout_metrics call in the process. */
 gila_status gila_layout_step(gila_graph* g, const gila_params* prm, double t,
                              const void* pos_in_dev, void* pos_out_dev, void* disp_out_dev);
 
@@ -186,10 +189,13 @@ gila_status gila_layout_run_device(gila_graph* g, const gila_params* prm, void* 
 /* Whole layout from and to host memory: uploads pos_in_host (double[2n];
  * FP32 modes round once on the device), builds the k-hop lists when needed,
  * runs prm->iters iterations and writes the final placement to
- * pos_out_host (double[2n]; may equal pos_in_host). Returns after the
- * result is on the host. */
+ * pos_out_host (double[2n]; may equal pos_in_host). When metrics_out is not
+ * NULL it receives the quality figures of the final placement, as
+ * gila_layout_metrics computes them. Returns after the result is on the
+ * host. */
 gila_status gila_layout_run(gila_graph* g, const gila_params* prm,
-                            const double* pos_in_host, double* pos_out_host);
+                            const double* pos_in_host, double* pos_out_host,
+                            gila_metrics* metrics_out);
 
 /* Quality figures of a device placement (float2 or double2 per
  * prm->precision) with the k-hop lists of prm->k, in FP64 with a fixed
@@ -198,8 +204,8 @@ gila_status gila_layout_metrics(gila_graph* g, const gila_params* prm, const voi
                                 gila_metrics* out);
 
 /* ------------------------------------------------------------------------
- * Batches: many independent graphs laid out together (SURVEY pattern
- * "thousands of small uneven graphs"). The batch is the disjoint union of
+ * Batches: many independent graphs laid out together (thousands of small
+ * graphs of uneven sizes). The batch is the disjoint union of
  * its graphs, so one k-hop build serves all of them; the layouts then run in
  * one persistent kernel launch in which each CTA takes one graph at a time
  * and carries it through all iterations with its placement staged in shared

@@ -422,7 +422,7 @@ gila_status gila_layout_run_device(gila_graph* g, const gila_params* prm, void* 
 }
 
 gila_status gila_layout_run(gila_graph* g, const gila_params* prm, const double* pos_in_host,
-                            double* pos_out_host)
+                            double* pos_out_host, gila_metrics* metrics_out)
 {
     if (!g) return fail(GILA_EINVAL, "graph is NULL");
     gila_status s = check_params(prm);
@@ -430,7 +430,10 @@ gila_status gila_layout_run(gila_graph* g, const gila_params* prm, const double*
     if (g->n > 0 && (!pos_in_host || !pos_out_host)) return fail(GILA_EINVAL, "placement is NULL");
     if ((s = use_device(g)) != GILA_OK) return s;
     if ((s = ensure_khop(g, prm->k)) != GILA_OK) return s;
-    if (g->n == 0) return GILA_OK;
+    if (g->n == 0) {
+        if (metrics_out) *metrics_out = gila_metrics{};
+        return GILA_OK;
+    }
     const size_t n = (size_t)g->n;
     const size_t bytes = pos_elem(prm->precision) * n;
     if ((s = ensure(&g->pos[0], &g->pos_cap[0], bytes)) != GILA_OK) return s;
@@ -445,6 +448,7 @@ gila_status gila_layout_run(gila_graph* g, const gila_params* prm, const double*
             return s;
     }
     if ((s = run_loop(g, prm, g->pos[0], g->pos[1])) != GILA_OK) return s;
+    if (metrics_out && (s = compute_metrics(g, prm, g->pos[0], metrics_out)) != GILA_OK) return s;
     if (f64) {
         GILA_CUDA(cudaMemcpyAsync(pos_out_host, g->pos[0], 16 * n, cudaMemcpyDeviceToHost,
                                   g->stream));
@@ -455,7 +459,7 @@ gila_status gila_layout_run(gila_graph* g, const gila_params* prm, const double*
                                   g->stream));
     }
     GILA_CUDA(cudaStreamSynchronize(g->stream));
-    return GILA_OK;
+    return blocked_tile_wait_failed(g->stream);
 }
 
 gila_status gila_layout_metrics(gila_graph* g, const gila_params* prm, const void* pos_dev,
@@ -467,7 +471,8 @@ gila_status gila_layout_metrics(gila_graph* g, const gila_params* prm, const voi
     if (g->n > 0 && !pos_dev) return fail(GILA_EINVAL, "placement is NULL");
     if ((s = use_device(g)) != GILA_OK) return s;
     if ((s = ensure_khop(g, prm->k)) != GILA_OK) return s;
-    return compute_metrics(g, prm, pos_dev, out);
+    if ((s = compute_metrics(g, prm, pos_dev, out)) != GILA_OK) return s;
+    return blocked_tile_wait_failed(g->stream);
 }
 
 double gila_temperature(const gila_params* prm, double t0, int32_t i)

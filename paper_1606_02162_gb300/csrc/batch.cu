@@ -160,12 +160,12 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchArgs A)
                 t0 = sqrt((double)n * A.d / a);
             }
         }
-        Rep<T, MODEL, COMP, true> f;
-        f.base = (uint32_t)v0;
+        Rep<T, MODEL, COMP, kSrcGeneric> f;
+        f.src.base = (uint32_t)v0;
         f.d2 = (T)(A.d * A.d);
         f.q = A.q;
-        Att<T, MODEL, COMP, true> att;
-        att.base = (uint32_t)v0;
+        Att<T, MODEL, COMP, kSrcGeneric> att;
+        att.src.base = (uint32_t)v0;
         att.inv_d = (T)(1.0 / A.d);
         att.p = A.p;
         const int groups = blockDim.x / G;
@@ -176,8 +176,8 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchArgs A)
                                   : t0 * (double)(A.iters - it) / (double)A.iters;
             const T t = (T)td;
             // ids are global; the buffer holds this graph's vertices from 0
-            f.pos = cur;
-            att.pos = cur;
+            f.src.pos = cur;
+            att.src.pos = cur;
             for (int64_t vb = 0; vb < n; vb += groups) {
                 const int64_t v = vb + grp;
                 const bool live = v < n;

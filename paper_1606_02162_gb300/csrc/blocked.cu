@@ -1,0 +1,670 @@
+// Blocked iteration path: positions staged in shared memory by tiles, the
+// k-hop ids rearranged once so that every CTA streams one contiguous block.
+//
+// Tiles: tile j holds the positions of ids [j tv, (j+1) tv). Ranges: rows are
+// cut into contiguous ranges of about equal total list length. Block (j, r)
+// holds, for every row u of range r in order, the entries of u's sorted
+// k-hop row that fall in tile j; block starts are 16-byte aligned. One CTA
+// per block loads tile j and the block's row directory into shared memory;
+// each warp streams an equal, aligned stripe of the block with 16-byte id
+// loads and gathers positions from the tile. A row is summed in stripe
+// order by the warps that hold it (the usual case: one warp), combined in
+// warp order, and stored as the row's partial for tile j. A second kernel
+// adds each row's tile partials in tile order, adds its attraction terms
+// and applies the capped move. Every partial has a fixed place in a fixed
+// order, so results do not depend on scheduling.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "device_util.cuh"
+#include "force.cuh"
+#include "gila_impl.h"
+
+namespace gila {
+
+namespace {
+
+constexpr int kBThreads = 1024;
+constexpr int kBWarps = kBThreads / 32;
+constexpr int kSmemCap = 227 * 1024;
+constexpr int kMaxRows = 4096;  // rows per range (directory in shared memory)
+constexpr int kTileBudget = kSmemCap - (kMaxRows + 1) * 4 - 4096;
+constexpr uint32_t kBulkChunk = 32768;      // bytes per bulk copy instruction
+constexpr uint32_t kWaitPolls = 1u << 24;   // bound on mbarrier polls (far above any copy)
+
+// Set when a CTA gave up waiting for its tile copy (the launch's partials
+// are then incomplete); read and cleared by blocked_tile_wait_failed().
+__device__ int g_tile_wait_failed = 0;
+
+struct BlockedArgs {
+    const uint32_t* tk;        // ids in block order
+    const int64_t* toff;       // nt n: start of (tile j, row u) in tk
+    const int64_t* blk;        // 2 nt nr: start and length of block (j, r)
+    const int32_t* range_start;
+    int64_t n;
+    int32_t nt, tv, nr;
+    int q;
+    const void* pos;
+    void* part;                // nt n cells of 4 T: (sx, sy, cx, cy) without the factor d^2
+};
+
+template <class T, bool COMP>
+struct Slot {
+    int32_t row;
+    T v[4];
+};
+
+// Cell (tile j, row u) of the partials, as two position-type pairs.
+template <class T>
+__device__ __forceinline__ typename V2<T>::type* cell_ptr(void* part, int64_t n, int j, int64_t u)
+{
+    using P2 = typename V2<T>::type;
+    return reinterpret_cast<P2*>(part) + ((int64_t)j * n + u) * 2;
+}
+
+template <class T, bool COMP>
+__device__ __forceinline__ void store_cell(typename V2<T>::type* c, const Acc<T, COMP>& a)
+{
+    using P2 = typename V2<T>::type;
+    P2 s;
+    s.x = a.sx;
+    s.y = a.sy;
+    c[0] = s;
+    if (COMP) {
+        P2 k;
+        k.x = a.cx;
+        k.y = a.cy;
+        c[1] = k;
+    }
+}
+
+template <class T, int MODEL, bool COMP>
+__global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs A)
+{
+    using P2 = typename V2<T>::type;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    P2* tile = reinterpret_cast<P2*>(smem_raw);
+    int32_t* D = reinterpret_cast<int32_t*>(smem_raw + (size_t)A.tv * sizeof(P2));
+    __shared__ Slot<T, COMP> head[kBWarps], tail[kBWarps];
+    __shared__ __align__(8) uint64_t tile_bar;
+    __shared__ int tile_ok;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = blockIdx.x / A.nr, r = blockIdx.x % A.nr;
+    const int64_t u0 = A.range_start[r], u1 = A.range_start[r + 1];
+    const int nrows = (int)(u1 - u0);
+    const int64_t bs = A.blk[2 * (int64_t)blockIdx.x];
+    // a block holds at most kMaxRows segments of at most tv entries: < 2^31
+    const int32_t L = (int32_t)A.blk[2 * (int64_t)blockIdx.x + 1];
+    const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos);
+    const int64_t tb = (int64_t)j * A.tv;
+    const int64_t tn = (A.n - tb < A.tv) ? A.n - tb : (int64_t)A.tv;
+    if (threadIdx.x == 0) {
+        // tile j by the bulk-copy engine (tv is even and the placement is
+        // 16-byte aligned, so the source is too); an odd float2 tail by hand
+        const uint32_t bytes = (uint32_t)(((size_t)tn * sizeof(P2)) & ~size_t(15));
+        mbar_init(&tile_bar, 1);
+        mbar_arrive_expect_tx(&tile_bar, bytes);
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(pos + tb);
+        for (uint32_t o = 0; o < bytes; o += kBulkChunk)
+            bulk_g2s(smem_raw + o, src + o, (bytes - o < kBulkChunk) ? bytes - o : kBulkChunk,
+                     &tile_bar);
+        if ((size_t)tn * sizeof(P2) != bytes) tile[tn - 1] = pos[tb + tn - 1];
+    }
+    // meanwhile: the row directory and zero partials for rows with no
+    // entries in this tile
+    for (int i = threadIdx.x; i < nrows; i += kBThreads) {
+        D[i] = (int32_t)(A.toff[(int64_t)j * A.n + u0 + i] - bs);
+        P2* c = cell_ptr<T>(A.part, A.n, j, u0 + i);
+        P2 z;
+        z.x = T(0);
+        z.y = T(0);
+        c[0] = z;
+        if (COMP) c[1] = z;
+    }
+    if (threadIdx.x == 0) D[nrows] = L;
+    if (threadIdx.x < kBWarps) {
+        head[threadIdx.x].row = -1;
+        tail[threadIdx.x].row = -1;
+    }
+    if (threadIdx.x == 0) {
+        bool ok = mbar_wait(&tile_bar, 0, kWaitPolls);
+        if (!ok) {
+            atomicExch(&g_tile_wait_failed, 1);
+            mbar_wait(&tile_bar, 0, kWaitPolls);  // let the copy land before the CTA ends
+        }
+        tile_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!tile_ok) return;  // uniform across the CTA
+    mbar_wait(&tile_bar, 0, kWaitPolls);  // completed: acquires the tile for this thread
+
+    Rep<T, MODEL, COMP, kSrcShared, true> f;  // d^2 is applied when the partials are added
+    f.src.set_shared(tile, (uint32_t)tb);
+    f.d2 = T(1);
+    f.q = A.q;
+    // this warp's stripe [a, b) of the block, 4-entry aligned
+    const int32_t a = (int32_t)(((int64_t)L * warp / kBWarps) & ~int64_t(3));
+    const int32_t b =
+        (warp == kBWarps - 1) ? L : (int32_t)(((int64_t)L * (warp + 1) / kBWarps) & ~int64_t(3));
+    if (a < b) {
+        // first row: the last i with D[i] <= a
+        int lo = 0, hi = nrows;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (D[mid] <= a) lo = mid; else hi = mid - 1;
+        }
+        int ri = lo;
+        while (ri < nrows && D[ri + 1] <= a) ++ri;  // skip empty rows at a
+        int32_t rs = D[ri], re = D[ri + 1];
+        P2 xr = pos[u0 + ri];
+        Acc<T, COMP> acc;
+        const uint4* ids4 = reinterpret_cast<const uint4*>(A.tk + bs);
+        auto finalize = [&](bool started_before, int row) {
+            acc.group_reduce(32);
+            if (lane == 0) {
+                if (started_before) {
+                    head[warp].row = row;
+                    head[warp].v[0] = acc.sx;
+                    head[warp].v[1] = acc.sy;
+                    head[warp].v[2] = acc.cx;
+                    head[warp].v[3] = acc.cy;
+                } else {
+                    store_cell<T, COMP>(cell_ptr<T>(A.part, A.n, j, u0 + row), acc);
+                }
+            }
+            acc = Acc<T, COMP>();
+        };
+        bool done = false;
+        // 16-byte id loads run three steps ahead of the arithmetic
+        auto load_step = [&](int32_t base) {
+            const int32_t p0 = base + 4 * lane;
+            return (base < b && p0 < b) ? ld_ids4(ids4 + (p0 >> 2)) : make_uint4(0, 0, 0, 0);
+        };
+        uint4 c0 = load_step(a), c1 = load_step(a + 128), c2 = load_step(a + 256);
+        for (int32_t base = a; base < b && !done; base += 128) {
+            const uint4 c3 = load_step(base + 384);
+            const int32_t p0 = base + 4 * lane;
+            const int32_t lim = (base + 128 < b) ? base + 128 : b;
+            const uint32_t ids[4] = {c0.x, c0.y, c0.z, c0.w};
+            c0 = c1;
+            c1 = c2;
+            c2 = c3;
+            if (re > lim) {  // the whole step lies in row ri (warp-uniform)
+                f.xu = xr.x;
+                f.yu = xr.y;
+                if (p0 + 3 < b) {
+                    f(ids[0], acc);
+                    f(ids[1], acc);
+                    f(ids[2], acc);
+                    f(ids[3], acc);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (p0 + q < b) f(ids[q], acc);
+                }
+                continue;
+            }
+            // rows ri, ri + 1, ... end inside this step
+            for (;;) {
+                f.xu = xr.x;
+                f.yu = xr.y;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int32_t p = p0 + q;
+                    if (p >= rs && p < re && p < b) f(ids[q], acc);
+                }
+                if (re > lim) break;  // this row goes on in the next step
+                finalize(rs < a, ri);
+                ++ri;
+                while (ri < nrows && D[ri + 1] == D[ri]) ++ri;  // empty rows stay zero
+                if (ri >= nrows || D[ri] >= b) {
+                    done = true;
+                    break;
+                }
+                rs = D[ri];
+                re = D[ri + 1];
+                xr = pos[u0 + ri];
+            }
+        }
+        if (!done && ri < nrows && re > b) {
+            // the stripe ends inside row ri: its part goes to a slot
+            acc.group_reduce(32);
+            if (lane == 0) {
+                Slot<T, COMP>& sl = (rs < a) ? head[warp] : tail[warp];
+                sl.row = ri;
+                sl.v[0] = acc.sx;
+                sl.v[1] = acc.sy;
+                sl.v[2] = acc.cx;
+                sl.v[3] = acc.cy;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // rows cut by stripe bounds: add their slots in warp order
+        int cur = -1;
+        Acc<T, COMP> sum;
+        auto flush = [&]() {
+            if (cur >= 0) store_cell<T, COMP>(cell_ptr<T>(A.part, A.n, j, u0 + cur), sum);
+        };
+        for (int w = 0; w < kBWarps; ++w) {
+            const Slot<T, COMP>* sl[2] = {&head[w], &tail[w]};
+            for (int h = 0; h < 2; ++h) {
+                if (sl[h]->row < 0) continue;
+                if (sl[h]->row != cur) {
+                    flush();
+                    cur = sl[h]->row;
+                    sum = Acc<T, COMP>();
+                }
+                sum.merge(sl[h]->v[0], sl[h]->v[1], sl[h]->v[2], sl[h]->v[3]);
+            }
+        }
+        flush();
+    }
+}
+
+struct CombineArgs {
+    const int64_t* row;
+    const int32_t* col;
+    int64_t n;
+    int32_t nt;
+    double d, t;
+    int p;
+    const void* pos_in;
+    const void* part;
+    void* pos_out;
+    void* disp_out;
+    const int32_t* hubs;  // rows with more than kHubDeg neighbours, one block each
+    int32_t nhub;
+    int32_t nreg;         // blocks of the regular part of the grid
+};
+
+// Regular rows: eight lanes per vertex. Hubs (adjacency rows longer than
+// kHubDeg) take a block of kCombineThreads each, after the regular blocks,
+// so no vertex walks a long row on eight lanes while the rest of the GPU
+// waits.
+constexpr int kCombineLanes = 8;
+constexpr int kCombineThreads = 256;
+constexpr int kHubDeg = 64;
+
+template <class T, bool COMP>
+__device__ __forceinline__ void add_cell(const void* part, int64_t n, int j, int64_t u,
+                                         Acc<T, COMP>& s)
+{
+    using P2 = typename V2<T>::type;
+    const P2* c = cell_ptr<T>(const_cast<void*>(part), n, j, u);
+    const P2 v = c[0];
+    if (COMP) {
+        const P2 k = c[1];
+        s.merge(v.x, v.y, k.x, k.y);
+    } else {
+        s.merge(v.x, v.y, T(0), T(0));
+    }
+}
+
+// F = d^2 (sum of the tile partials) + attraction; then the capped move.
+template <class T, bool COMP>
+__device__ __forceinline__ void finish_vertex(const CombineArgs& A, int64_t u, T xu, T yu,
+                                              Acc<T, COMP> rep, const Acc<T, COMP>& att)
+{
+    const T d2 = (T)(A.d * A.d);
+    rep.sx *= d2;
+    rep.sy *= d2;
+    rep.cx *= d2;
+    rep.cy *= d2;
+    rep.merge(att.sx, att.sy, att.cx, att.cy);
+    apply_move<T>(A.t, A.pos_out, A.disp_out, u, xu, yu, rep.fx(), rep.fy());
+}
+
+template <class T, int MODEL, bool COMP>
+__global__ void __launch_bounds__(kCombineThreads) combine_kernel(const CombineArgs A)
+{
+    using P2 = typename V2<T>::type;
+    const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos_in);
+    Att<T, MODEL, COMP> att;
+    att.src.pos = pos;
+    att.inv_d = (T)(1.0 / A.d);
+    att.p = A.p;
+    Acc<T, COMP> rep, at;
+    if ((int)blockIdx.x >= A.nreg) {
+        // one hub per block
+        __shared__ T sh[kCombineThreads / 32][8];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int64_t u = A.hubs[blockIdx.x - A.nreg];
+        const P2 pu = pos[u];
+        for (int jj = threadIdx.x; jj < A.nt; jj += kCombineThreads)
+            add_cell<T, COMP>(A.part, A.n, jj, u, rep);
+        att.xu = pu.x;
+        att.yu = pu.y;
+        row_sum_rel(reinterpret_cast<const uint32_t*>(A.col), A.row[u], A.row[u + 1],
+                    (int)threadIdx.x, kCombineThreads, att, at);
+        rep.group_reduce(32);
+        at.group_reduce(32);
+        if (lane == 0) {
+            sh[warp][0] = rep.sx;
+            sh[warp][1] = rep.sy;
+            sh[warp][2] = rep.cx;
+            sh[warp][3] = rep.cy;
+            sh[warp][4] = at.sx;
+            sh[warp][5] = at.sy;
+            sh[warp][6] = at.cx;
+            sh[warp][7] = at.cy;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Acc<T, COMP> r2, a2;
+            for (int w = 0; w < kCombineThreads / 32; ++w) {
+                r2.merge(sh[w][0], sh[w][1], sh[w][2], sh[w][3]);
+                a2.merge(sh[w][4], sh[w][5], sh[w][6], sh[w][7]);
+            }
+            finish_vertex<T, COMP>(A, u, pu.x, pu.y, r2, a2);
+        }
+        return;
+    }
+    const int gl = threadIdx.x & (kCombineLanes - 1);
+    const int64_t u = ((int64_t)blockIdx.x * kCombineThreads + threadIdx.x) / kCombineLanes;
+    bool live = u < A.n;
+    int64_t rb = 0, re = 0;
+    if (live) {
+        rb = A.row[u];
+        re = A.row[u + 1];
+        live = re - rb <= kHubDeg;  // hubs are done by their own blocks
+    }
+    P2 pu;
+    pu.x = T(0);
+    pu.y = T(0);
+    if (live) {
+        // tile partials first (independent loads), lane gl takes tiles gl, gl + 8, ...
+        for (int jj = gl; jj < A.nt; jj += kCombineLanes) add_cell<T, COMP>(A.part, A.n, jj, u, rep);
+        pu = pos[u];
+        att.xu = pu.x;
+        att.yu = pu.y;
+        row_sum_rel(reinterpret_cast<const uint32_t*>(A.col), rb, re, gl, kCombineLanes, att, at);
+    }
+    rep.group_reduce(kCombineLanes);
+    at.group_reduce(kCombineLanes);
+    if (live && gl == 0) finish_vertex<T, COMP>(A, u, pu.x, pu.y, rep, at);
+}
+
+// Length of row u's segment in tile j (binary search on the sorted row).
+__device__ __forceinline__ void seg_bounds(const int64_t* __restrict__ krow,
+                                           const uint32_t* __restrict__ kcol, int64_t u, int j,
+                                           int nt, int tv, int64_t* lo, int64_t* hi)
+{
+    const int64_t kb = krow[u], ke = krow[u + 1];
+    auto lower = [&](uint32_t key) {
+        int64_t x = kb, y = ke;
+        while (x < y) {
+            const int64_t mid = (x + y) >> 1;
+            if (kcol[mid] < key) x = mid + 1; else y = mid;
+        }
+        return x;
+    };
+    *lo = (j == 0) ? kb : lower((uint32_t)j * (uint32_t)tv);
+    *hi = (j == nt - 1) ? ke : lower((uint32_t)(j + 1) * (uint32_t)tv);
+}
+
+__global__ void seglen_kernel(int64_t n, const int64_t* __restrict__ krow,
+                              const uint32_t* __restrict__ kcol, int nt, int tv,
+                              int64_t* __restrict__ len)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * nt) return;
+    int64_t lo, hi;
+    seg_bounds(krow, kcol, i % n, (int)(i / n), nt, tv, &lo, &hi);
+    len[i] = hi - lo;
+}
+
+// Copy every (tile, row) segment to its place in the block layout; one warp
+// per segment.
+__global__ void block_copy_kernel(int64_t n, const int64_t* __restrict__ krow,
+                                  const uint32_t* __restrict__ kcol, int nt, int tv,
+                                  const int64_t* __restrict__ toff, uint32_t* __restrict__ tk)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n * nt) return;
+    int64_t lo, hi;
+    seg_bounds(krow, kcol, i % n, (int)(i / n), nt, tv, &lo, &hi);
+    uint32_t* dst = tk + toff[i];
+    for (int64_t e = lo + lane; e < hi; e += 32) dst[e - lo] = kcol[e];
+}
+
+template <class T, int MODEL, bool COMP>
+cudaError_t launch_pair(const BlockedArgs& B, const CombineArgs& C, int grid, size_t smem,
+                        cudaStream_t st, int device)
+{
+    static uint64_t configured = 0;  // one bit per device
+    const uint64_t bit = 1ull << (device & 63);
+    if (!(configured & bit)) {
+        cudaError_t e = cudaFuncSetAttribute(blocked_kernel<T, MODEL, COMP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kSmemCap - 4096);
+        if (e != cudaSuccess) return e;
+        configured |= bit;
+    }
+    blocked_kernel<T, MODEL, COMP><<<grid, kBThreads, smem, st>>>(B);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    combine_kernel<T, MODEL, COMP><<<(unsigned)(C.nreg + C.nhub), kCombineThreads, 0, st>>>(C);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+void invalidate_tile_plans(gila_graph* g)
+{
+    g->tplan[0].ready = false;
+    g->tplan[1].ready = false;
+}
+
+gila_status blocked_tile_wait_failed(cudaStream_t st)
+{
+    int h = 0;
+    const int zero = 0;
+    GILA_CUDA(cudaMemcpyFromSymbolAsync(&h, g_tile_wait_failed, sizeof(int), 0,
+                                        cudaMemcpyDeviceToHost, st));
+    GILA_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        GILA_CUDA(cudaMemcpyToSymbolAsync(g_tile_wait_failed, &zero, sizeof(int), 0,
+                                          cudaMemcpyHostToDevice, st));
+        GILA_CUDA(cudaStreamSynchronize(st));
+        return fail(GILA_ECUDA, "a tile copy of the iteration kernel did not complete in time");
+    }
+    return GILA_OK;
+}
+
+void free_tile_plans(gila_graph* g)
+{
+    for (TilePlan& P : g->tplan) {
+        cudaFree(P.hubs);
+        cudaFree(P.range_start);
+        cudaFree(P.blk);
+        cudaFree(P.toff);
+        cudaFree(P.tk);
+        cudaFree(P.part);
+        cudaFree(P.len);
+        P = TilePlan();
+    }
+}
+
+// Decide whether the blocked path serves g for positions of `esz` bytes and
+// build its layout: tiles, row ranges, block offsets, rearranged ids.
+gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
+{
+    P.ready = true;
+    P.use = false;
+    const int64_t n = g->n;
+    if (n == 0 || g->nnz_khop == 0 || g->tune.tiled == 0) return GILA_OK;
+    int64_t tv_max = kTileBudget / (int64_t)esz;
+    if (g->tune.tile_vertices > 0) tv_max = std::min<int64_t>(tv_max, g->tune.tile_vertices);
+    tv_max = std::max<int64_t>(2, tv_max & ~int64_t(1));
+    const int64_t nt = (n + tv_max - 1) / tv_max;
+    const int64_t tv = std::min<int64_t>(tv_max, (((n + nt - 1) / nt) + 1) & ~int64_t(1));
+    const int min_seg = g->tune.min_segment > 0 ? g->tune.min_segment : 48;
+    const double avg_seg = (double)g->nnz_khop / ((double)n * (double)nt);
+    if (g->tune.tiled < 0 && avg_seg < min_seg) return GILA_OK;
+    const int64_t cells = n * nt;
+    gila_status s = ensure((void**)&P.len, &P.len_cap, sizeof(int64_t) * (size_t)cells);
+    if (s != GILA_OK) return s;
+    seglen_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, g->stream>>>(n, g->krow, g->kcol,
+                                                                        (int)nt, (int)tv, P.len);
+    count_launch();
+    GILA_CUDA(cudaGetLastError());
+    std::vector<int64_t> len((size_t)cells);
+    GILA_CUDA(cudaMemcpyAsync(len.data(), P.len, sizeof(int64_t) * cells, cudaMemcpyDeviceToHost,
+                              g->stream));
+    GILA_CUDA(cudaStreamSynchronize(g->stream));
+    // row ranges of about equal cost (entries + a per-row term), at most
+    // kMaxRows rows each, enough of them for several CTAs per SM in total
+    std::vector<int64_t> cost((size_t)n, 0);
+    int64_t total = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        int64_t c = 8;
+        for (int64_t j = 0; j < nt; ++j) c += len[(size_t)(j * n + u)];
+        cost[(size_t)u] = c;
+        total += c;
+    }
+    const int sms = sm_count(g->device);
+    int64_t nr_target = std::max<int64_t>((4 * (int64_t)sms + nt - 1) / nt, (n + kMaxRows - 1) / kMaxRows);
+    nr_target = std::min<int64_t>(nr_target, n);
+    std::vector<int32_t> rs;
+    rs.push_back(0);
+    {
+        const double per = (double)total / (double)nr_target;
+        double acc = 0.0;
+        int64_t rows = 0;
+        for (int64_t u = 0; u < n; ++u) {
+            if (rows > 0 && (acc + cost[(size_t)u] / 2.0 > per * (double)rs.size() ||
+                             rows >= kMaxRows)) {
+                rs.push_back((int32_t)u);
+                rows = 0;
+            }
+            acc += (double)cost[(size_t)u];
+            ++rows;
+        }
+        rs.push_back((int32_t)n);
+    }
+    const int64_t nr = (int64_t)rs.size() - 1;
+    // block layout: (j, r) blocks in that order, starts aligned to 4 entries
+    std::vector<int64_t> toff((size_t)cells), blk((size_t)(2 * nt * nr));
+    int64_t off = 0;
+    for (int64_t j = 0; j < nt; ++j)
+        for (int64_t r = 0; r < nr; ++r) {
+            off = (off + 3) & ~int64_t(3);
+            const int64_t start = off;
+            for (int64_t u = rs[(size_t)r]; u < rs[(size_t)r + 1]; ++u) {
+                toff[(size_t)(j * n + u)] = off;
+                off += len[(size_t)(j * n + u)];
+            }
+            blk[(size_t)(2 * (j * nr + r))] = start;
+            blk[(size_t)(2 * (j * nr + r) + 1)] = off - start;
+        }
+    const int64_t tk_len = off + 4;
+    if ((s = ensure((void**)&P.toff, &P.toff_cap, sizeof(int64_t) * (size_t)cells)) != GILA_OK)
+        return s;
+    if ((s = ensure((void**)&P.blk, &P.blk_cap, sizeof(int64_t) * blk.size())) != GILA_OK) return s;
+    if ((s = ensure((void**)&P.range_start, &P.range_cap, sizeof(int32_t) * rs.size())) != GILA_OK)
+        return s;
+    if ((s = ensure((void**)&P.tk, &P.tk_cap, sizeof(uint32_t) * (size_t)tk_len)) != GILA_OK)
+        return s;
+    if ((s = ensure(&P.part, &P.part_cap, 2 * esz * (size_t)cells)) != GILA_OK) return s;
+    GILA_CUDA(cudaMemcpyAsync(P.toff, toff.data(), sizeof(int64_t) * cells, cudaMemcpyHostToDevice,
+                              g->stream));
+    GILA_CUDA(cudaMemcpyAsync(P.blk, blk.data(), sizeof(int64_t) * blk.size(),
+                              cudaMemcpyHostToDevice, g->stream));
+    GILA_CUDA(cudaMemcpyAsync(P.range_start, rs.data(), sizeof(int32_t) * rs.size(),
+                              cudaMemcpyHostToDevice, g->stream));
+    block_copy_kernel<<<(unsigned)((cells * 32 + 255) / 256), 256, 0, g->stream>>>(
+        n, g->krow, g->kcol, (int)nt, (int)tv, P.toff, P.tk);
+    count_launch();
+    GILA_CUDA(cudaGetLastError());
+    // hubs of the adjacency for the combine kernel
+    std::vector<int64_t> arow((size_t)n + 1);
+    GILA_CUDA(cudaMemcpyAsync(arow.data(), g->row, sizeof(int64_t) * (n + 1),
+                              cudaMemcpyDeviceToHost, g->stream));
+    GILA_CUDA(cudaStreamSynchronize(g->stream));
+    std::vector<int32_t> hubs;
+    for (int64_t u = 0; u < n; ++u)
+        if (arow[(size_t)u + 1] - arow[(size_t)u] > kHubDeg) hubs.push_back((int32_t)u);
+    if (!hubs.empty()) {
+        if ((s = ensure((void**)&P.hubs, &P.hubs_cap, sizeof(int32_t) * hubs.size())) != GILA_OK)
+            return s;
+        GILA_CUDA(cudaMemcpyAsync(P.hubs, hubs.data(), sizeof(int32_t) * hubs.size(),
+                                  cudaMemcpyHostToDevice, g->stream));
+    }
+    GILA_CUDA(cudaStreamSynchronize(g->stream));  // the host vectors go out of scope
+    P.nhub = (int32_t)hubs.size();
+    P.nt = (int32_t)nt;
+    P.tv = (int32_t)tv;
+    P.nr = (int32_t)nr;
+    P.use = true;
+    return GILA_OK;
+}
+
+gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, const void* pos_in,
+                           void* pos_out, void* disp_out, bool* handled)
+{
+    *handled = false;
+    if (prm->precision == GILA_FP64_ORDERED || g->n == 0) return GILA_OK;
+    const size_t esz = is_f64(prm->precision) ? 16 : 8;
+    TilePlan& P = g->tplan[esz == 16 ? 1 : 0];
+    if (!P.ready) {
+        gila_status s = plan_tiles(g, esz, P);
+        if (s != GILA_OK) return s;
+    }
+    if (!P.use || ((uintptr_t)pos_in & 15) != 0) return GILA_OK;
+    BlockedArgs B;
+    B.tk = P.tk;
+    B.toff = P.toff;
+    B.blk = P.blk;
+    B.range_start = P.range_start;
+    B.n = g->n;
+    B.nt = P.nt;
+    B.tv = P.tv;
+    B.nr = P.nr;
+    B.q = prm->q;
+    B.pos = pos_in;
+    B.part = P.part;
+    CombineArgs C;
+    C.row = g->row;
+    C.col = g->col;
+    C.n = g->n;
+    C.nt = P.nt;
+    C.d = prm->d;
+    C.t = t;
+    C.p = prm->p;
+    C.pos_in = pos_in;
+    C.part = P.part;
+    C.pos_out = pos_out;
+    C.disp_out = disp_out;
+    C.hubs = P.hubs;
+    C.nhub = P.nhub;
+    C.nreg = (int32_t)((g->n * kCombineLanes + kCombineThreads - 1) / kCombineThreads);
+    const int grid = P.nt * P.nr;
+    const size_t smem = (size_t)P.tv * esz + (size_t)(kMaxRows + 1) * 4;
+    const bool fr = (prm->p == 2 && prm->q == 1);
+    cudaError_t e;
+    switch (prm->precision) {
+    case GILA_FP64:
+        e = fr ? launch_pair<double, kFR, false>(B, C, grid, smem, g->stream, g->device)
+               : launch_pair<double, kGeneric, false>(B, C, grid, smem, g->stream, g->device);
+        break;
+    case GILA_FP32_COMPENSATED:
+        e = fr ? launch_pair<float, kFR, true>(B, C, grid, smem, g->stream, g->device)
+               : launch_pair<float, kGeneric, true>(B, C, grid, smem, g->stream, g->device);
+        break;
+    default:
+        e = fr ? launch_pair<float, kFR, false>(B, C, grid, smem, g->stream, g->device)
+               : launch_pair<float, kGeneric, false>(B, C, grid, smem, g->stream, g->device);
+        break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "blocked_kernel");
+    *handled = true;
+    return GILA_OK;
+}
+
+}  // namespace gila

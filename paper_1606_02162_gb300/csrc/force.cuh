@@ -98,34 +98,70 @@ struct Acc {
     __device__ __forceinline__ T fy() const { return COMP ? sy + cy : sy; }
 };
 
+// Where a kernel reads positions from.
+enum Src {
+    kSrcGlobal = 0,   // the whole placement, read-only for the launch (ld.global.nc)
+    kSrcShared = 1,   // a shared-memory tile of ids [base, base + size), 32-bit addresses
+    kSrcGeneric = 2   // a buffer of ids [base, base + size) in shared or global memory
+};
+
+// Reciprocal square root, one approximate MUFU operation (denormals flushed).
+__device__ __forceinline__ float rsqrt_fast(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Position of id v for a kernel reading from `SRC`.
+template <class T, int SRC>
+struct PosSource {
+    using P2 = typename V2<T>::type;
+    const P2* __restrict__ pos = nullptr;  // kSrcGlobal / kSrcGeneric
+    uint32_t base = 0;                     // first id held (kSrcShared / kSrcGeneric)
+    const P2* shp = nullptr;               // kSrcShared: tile shifted so that shp[v] is id v
+
+    // kSrcShared: `tile` holds ids [first, ...). Plain indexing (not inline
+    // ld.shared) leaves the compiler free to schedule the gathers.
+    __device__ __forceinline__ void set_shared(const P2* tile, uint32_t first)
+    {
+        base = first;
+        shp = tile - first;
+    }
+    __device__ __forceinline__ P2 operator()(uint32_t v) const
+    {
+        if (SRC == kSrcShared) return shp[v];
+        if (SRC == kSrcGeneric) return pos[v - base];
+        return __ldg(pos + v);
+    }
+};
+
 // Repulsion of one k-hop entry v on u (Section 3.1 with the repelling set
 // of Section 4.5): adds c (x_u - x_v) with c = d^2 / delta^(q+1). For
 // Fruchterman-Reingold (q = 1) in FP32 that is d^2 * rsqrt(r^2)^2: one MUFU
-// and two multiplies, no divide. A pair at distance 0 adds nothing.
-// Positions come through L1/L2 (SMEM = false: `pos` is the whole placement)
-// or from a buffer holding ids [base, base + size) (SMEM = true; a shared
-// memory tile, or a graph's own slice of a global placement).
-template <class T, int MODEL, bool COMP, bool SMEM = false>
+// and two multiplies, no divide. A pair at distance 0 adds nothing. With
+// UNSCALED the factor d^2 is left out (the caller multiplies the row's sum
+// by it once).
+template <class T, int MODEL, bool COMP, int SRC = kSrcGlobal, bool UNSCALED = false>
 struct Rep {
     using P2 = typename V2<T>::type;
-    const P2* __restrict__ pos;
-    uint32_t base = 0;
+    PosSource<T, SRC> src;
     T xu, yu, d2;
     int q;
 
     __device__ __forceinline__ void operator()(uint32_t v, Acc<T, COMP>& a) const
     {
-        const P2 pv = SMEM ? pos[v - base] : __ldg(pos + v);
+        const P2 pv = src(v);
         const T dx = xu - pv.x, dy = yu - pv.y;
         const T r2 = dx * dx + dy * dy;
         T c;
         if (MODEL == kFR) {
-            c = rep_fr(d2, r2);
+            c = UNSCALED ? rep_fr1(r2) : rep_fr(d2, r2);
         } else {
             c = T(0);
             if (r2 > T(0)) {
                 const T dl = sqrt(r2);
-                c = d2 / (ipow_(dl, q) * dl);
+                c = (UNSCALED ? T(1) : d2) / (ipow_(dl, q) * dl);
             }
         }
         a.add(c * dx, c * dy);
@@ -133,28 +169,38 @@ struct Rep {
 
     __device__ __forceinline__ static float rep_fr(float d2, float r2)
     {
-        const float r = rsqrtf(r2);
+        const float r = rsqrt_fast(r2);
         return r2 > 0.0f ? d2 * (r * r) : 0.0f;
     }
     __device__ __forceinline__ static double rep_fr(double d2, double r2)
     {
         return r2 > 0.0 ? d2 / r2 : 0.0;
     }
+    // 1 / r^2. At r^2 = 0 the approximate rsqrt gives +inf; the clamp turns
+    // that into a finite factor, which then multiplies dx = dy = 0 exactly.
+    __device__ __forceinline__ static float rep_fr1(float r2)
+    {
+        const float r = rsqrt_fast(r2);
+        return fminf(r * r, 3.0e38f);
+    }
+    __device__ __forceinline__ static double rep_fr1(double r2)
+    {
+        return r2 > 0.0 ? 1.0 / r2 : 0.0;
+    }
 };
 
 // Attraction of a neighbour v of u: adds -c (x_u - x_v) with
 // c = delta^(p-1) / d (delta / d for p = 2).
-template <class T, int MODEL, bool COMP, bool SMEM = false>
+template <class T, int MODEL, bool COMP, int SRC = kSrcGlobal>
 struct Att {
     using P2 = typename V2<T>::type;
-    const P2* __restrict__ pos;
-    uint32_t base = 0;
+    PosSource<T, SRC> src;
     T xu, yu, inv_d;
     int p;
 
     __device__ __forceinline__ void operator()(uint32_t v, Acc<T, COMP>& a) const
     {
-        const P2 pv = SMEM ? pos[v - base] : __ldg(pos + v);
+        const P2 pv = src(v);
         const T dx = xu - pv.x, dy = yu - pv.y;
         const T r2 = dx * dx + dy * dy;
         if (r2 > T(0)) {
@@ -204,6 +250,7 @@ __device__ __forceinline__ void row_sum_rel(const uint32_t* __restrict__ ids, in
 {
     const uint32_t* p = ids + s;
     const int len = (int)(e - s);
+#pragma unroll 4
     for (int j = gl; j < len; j += G) f(ld_id(p + j), a);
 }
 

@@ -83,18 +83,28 @@ struct Bins {
     BinConfig cfg;
 };
 
-// Shared-memory tiling plan of the iteration for one position width
-// (index 0: float2, 1: double2). Rebuilt after every k-hop build.
+// Blocked-path plan of the iteration for one position width (index 0:
+// float2, 1: double2): tiles of positions, row ranges and the k-hop ids
+// rearranged block by block. Rebuilt after every k-hop build.
 struct TilePlan {
     bool ready = false;  // decided for the current k-hop lists
-    bool use = false;    // the tiled kernel serves this graph
-    int32_t nt = 0, tv = 0, ncta = 0;
-    int32_t* seg = nullptr;
-    size_t seg_cap = 0;
-    int32_t* cta_rows = nullptr;
-    size_t cta_cap = 0;
-    void* acc = nullptr;
-    size_t acc_cap = 0;
+    bool use = false;    // the blocked path serves this graph
+    int32_t nt = 0, tv = 0, nr = 0;
+    int32_t* range_start = nullptr;  // nr + 1 row bounds
+    size_t range_cap = 0;
+    int64_t* blk = nullptr;          // 2 nt nr: start and length of block (tile j, range r)
+    size_t blk_cap = 0;
+    int64_t* toff = nullptr;         // nt n: start of (tile j, row u) in tk
+    size_t toff_cap = 0;
+    uint32_t* tk = nullptr;          // ids in block order
+    size_t tk_cap = 0;
+    void* part = nullptr;            // nt n x 4 T partial forces
+    size_t part_cap = 0;
+    int32_t* hubs = nullptr;         // vertices of adjacency degree > 64 (combine kernel)
+    size_t hubs_cap = 0;
+    int32_t nhub = 0;
+    int64_t* len = nullptr;          // nt n segment lengths (plan scratch)
+    size_t len_cap = 0;
 };
 
 struct ProfileRec {
@@ -155,6 +165,13 @@ gila_status compute_metrics(gila_graph* g, const gila_params* prm, const void* p
                             gila_metrics* out);
 gila_status bbox_aspect(gila_graph* g, int precision, const void* pos, double* aspect);
 void invalidate_tile_plans(gila_graph* g);
+void free_tile_plans(gila_graph* g);
+// blocked path (blocked.cu): *handled = false when the plain kernel must run
+gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, const void* pos_in,
+                           void* pos_out, void* disp_out, bool* handled);
+// GILA_ECUDA (and clears the flag) when a blocked-path CTA gave up waiting
+// for its tile copy since the last call; synchronises st.
+gila_status blocked_tile_wait_failed(cudaStream_t st);
 gila_status convert_positions(gila_graph* g, int precision, const double* src, void* dst,
                               bool to_device_type);
 void free_layout(gila_graph* g);
@@ -163,6 +180,9 @@ void free_layout(gila_graph* g);
 gila_status ensure(void** p, size_t* cap, size_t bytes);
 
 int sm_count(int device);
+
+// out[0] = 0, out[i + 1] = in[0] + ... + in[i]; synchronises st.
+gila_status scan_exclusive_i64(const int64_t* in, int64_t n, int64_t* out, cudaStream_t st);
 
 // Count one kernel launch issued by the library (all launch sites call it).
 void count_launch();

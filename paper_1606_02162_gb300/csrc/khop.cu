@@ -526,6 +526,11 @@ gila_status build_bins(gila_graph* g)
 
 }  // namespace
 
+gila_status scan_exclusive_i64(const int64_t* in, int64_t n, int64_t* out, cudaStream_t st)
+{
+    return exclusive_scan(in, n, out, st);
+}
+
 int sm_count(int device)
 {
     int v = 0;

@@ -110,11 +110,11 @@ iteration_kernel(const IterArgs A)
     __shared__ int s_last;
     const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos_in);
     Rep<T, MODEL, COMP> rep;
-    rep.pos = pos;
+    rep.src.pos = pos;
     rep.d2 = (T)(A.d * A.d);
     rep.q = A.q;
     Att<T, MODEL, COMP> att;
-    att.pos = pos;
+    att.src.pos = pos;
     att.inv_d = (T)(1.0 / A.d);
     att.p = A.p;
     int b = blockIdx.x;
@@ -264,213 +264,6 @@ ordered_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __rest
     if (disp_out) disp_out[u] = make_double2(mx, my);
 }
 
-// ------------------------------------------------------------- tiled path
-//
-// Positions are staged in shared memory one tile of `tv` consecutive ids at
-// a time, so the gathers of a row segment read shared memory instead of L2.
-// Every k-hop row is sorted, so its entries with ids in tile j form one
-// contiguous segment whose bounds are precomputed (seg). CTA c owns rows
-// [cta_rows[c], cta_rows[c+1]) (balanced by entries); for each tile in
-// order it loads the tile, then its warps take row segments from a shared
-// counter, sum them, and add the partial to the row's running sum (global
-// `acc`) -- or, at the last tile, finish the row and move the vertex. A
-// row's sum is combined in tile order by whichever warp holds it, so the
-// result does not depend on scheduling.
-constexpr int kTiledThreads = 1024;
-constexpr int kTileBytes = 200 * 1024;
-
-struct TiledArgs {
-    const int64_t* row;
-    const int32_t* col;
-    const int64_t* krow;
-    const uint32_t* kcol;
-    const int32_t* seg;       // n x (nt - 1) interior tile bounds, relative to krow[u]
-    const int32_t* cta_rows;  // gridDim.x + 1 row bounds
-    void* acc;                // n x 4 T running sums between tiles (nt > 1)
-    int64_t n;
-    int32_t nt, tv;
-    double d, t;
-    int p, q;
-    const void* pos_in;
-    void* pos_out;
-    void* disp_out;
-};
-
-// One row's segment for tile j: entries [s, e) of kcol; u < 0 when the
-// CTA's rows are exhausted.
-struct TSeg {
-    int64_t u, s, e;
-};
-
-__device__ __forceinline__ TSeg tiled_seg(const TiledArgs& A, int64_t r0, int64_t r1, int r, int j)
-{
-    TSeg z;
-    z.u = r0 + r;
-    if (z.u >= r1) {
-        z.u = -1;
-        z.s = z.e = 0;
-        return z;
-    }
-    const int64_t kb = A.krow[z.u];
-    const int64_t len = A.krow[z.u + 1] - kb;
-    z.s = kb + ((j == 0) ? 0 : A.seg[z.u * (A.nt - 1) + j - 1]);
-    z.e = kb + ((j == A.nt - 1) ? len : A.seg[z.u * (A.nt - 1) + j]);
-    return z;
-}
-
-// Ask L2 to fetch the 128-byte lines holding ids [s, e) (at most 16 KB),
-// one line per lane per step; nothing waits for these.
-__device__ __forceinline__ void prefetch_ids_l2(const uint32_t* kcol, int64_t s, int64_t e, int lane)
-{
-    const uintptr_t a0 = reinterpret_cast<uintptr_t>(kcol + s) & ~uintptr_t(127);
-    uintptr_t a1 = reinterpret_cast<uintptr_t>(kcol + e);
-    if (a1 > a0 + 16384) a1 = a0 + 16384;
-    for (uintptr_t a = a0 + (uintptr_t)lane * 128; a < a1; a += 32 * 128)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
-}
-
-template <class T, int MODEL, bool COMP>
-__global__ void __launch_bounds__(kTiledThreads, 1)
-tiled_kernel(const TiledArgs A)
-{
-    using P2 = typename V2<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    P2* tile = reinterpret_cast<P2*>(smem_raw);
-    __shared__ int s_next;
-    const int lane = threadIdx.x & 31;
-    const int64_t r0 = A.cta_rows[blockIdx.x], r1 = A.cta_rows[blockIdx.x + 1];
-    if (r0 >= r1) return;  // whole block
-    const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos_in);
-    T* acc = reinterpret_cast<T*>(A.acc);
-    Rep<T, MODEL, COMP, true> f;
-    f.pos = tile;
-    f.d2 = (T)(A.d * A.d);
-    f.q = A.q;
-    Att<T, MODEL, COMP> att;  // neighbours' positions come through L1/L2
-    att.pos = pos;
-    att.inv_d = (T)(1.0 / A.d);
-    att.p = A.p;
-    for (int j = 0; j < A.nt; ++j) {
-        const int64_t tb = (int64_t)j * A.tv;
-        const int64_t tn = (A.n - tb < A.tv) ? A.n - tb : (int64_t)A.tv;
-        __syncthreads();  // every warp is done with the previous tile
-        {
-            // 16-byte copies (tv is even, so tile starts are 16-byte aligned)
-            const uint4* src = reinterpret_cast<const uint4*>(pos + tb);
-            uint4* dst = reinterpret_cast<uint4*>(tile);
-            const int64_t nv = (tn * (int64_t)sizeof(P2)) / 16;
-            for (int64_t i = threadIdx.x; i < nv; i += kTiledThreads) dst[i] = src[i];
-            if (sizeof(P2) == 8 && (tn & 1) && threadIdx.x == 0) tile[tn - 1] = pos[tb + tn - 1];
-        }
-        if (threadIdx.x == 0) s_next = 0;
-        __syncthreads();
-        f.base = (uint32_t)tb;
-        // Each warp holds its next assignment one step ahead: while it works
-        // on `cur`, the ids of `nxt` are pulled into L2 and the bounds of the
-        // one after are on their way.
-        auto grab = [&]() {
-            int r = 0;
-            if (lane == 0) r = atomicAdd(&s_next, 1);
-            return __shfl_sync(kFull, r, 0);
-        };
-        TSeg cur = tiled_seg(A, r0, r1, grab(), j);
-        TSeg nxt = tiled_seg(A, r0, r1, grab(), j);
-        while (cur.u >= 0) {  // warp-uniform
-            if (nxt.u >= 0) prefetch_ids_l2(A.kcol, nxt.s, nxt.e, lane);
-            const TSeg after = tiled_seg(A, r0, r1, grab(), j);
-            const int64_t u = cur.u;
-            const P2 pu = pos[u];
-            f.xu = pu.x;
-            f.yu = pu.y;
-            Acc<T, COMP> a;
-            row_sum(A.kcol, cur.s, cur.e, lane, 32, f, a);
-            if (j == A.nt - 1) {
-                att.xu = pu.x;
-                att.yu = pu.y;
-                row_sum_rel(reinterpret_cast<const uint32_t*>(A.col), A.row[u], A.row[u + 1], lane,
-                            32, att, a);
-            }
-            a.group_reduce(32);
-            if (lane == 0) {
-                if (j > 0) {
-                    Acc<T, COMP> s;
-                    s.sx = acc[u * 4 + 0];
-                    s.sy = acc[u * 4 + 1];
-                    s.cx = acc[u * 4 + 2];
-                    s.cy = acc[u * 4 + 3];
-                    s.merge(a.sx, a.sy, a.cx, a.cy);
-                    a = s;
-                }
-                if (j < A.nt - 1) {
-                    acc[u * 4 + 0] = a.sx;
-                    acc[u * 4 + 1] = a.sy;
-                    acc[u * 4 + 2] = a.cx;
-                    acc[u * 4 + 3] = a.cy;
-                } else {
-                    apply_move<T>(A.t, A.pos_out, A.disp_out, u, pu.x, pu.y, a.fx(), a.fy());
-                }
-            }
-            cur = nxt;
-            nxt = after;
-        }
-    }
-}
-
-// seg[u (nt-1) + j - 1] = index (relative to krow[u]) of the first entry of
-// row u with id >= j tv, for j = 1..nt-1.
-__global__ void tile_seg_kernel(int64_t n, const int64_t* __restrict__ krow,
-                                const uint32_t* __restrict__ kcol, int nt, int tv,
-                                int32_t* __restrict__ seg)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n * (nt - 1)) return;
-    const int64_t u = i / (nt - 1);
-    const uint32_t key = (uint32_t)((i % (nt - 1)) + 1) * (uint32_t)tv;
-    int64_t lo = krow[u], hi = krow[u + 1];
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (kcol[mid] < key) lo = mid + 1; else hi = mid;
-    }
-    seg[i] = (int32_t)(lo - krow[u]);
-}
-
-// cta_rows[c] = first row whose cost prefix krow[u] + w u reaches c/ncta of
-// the total cost (w = per-row overhead in entries).
-__global__ void tile_cta_kernel(int64_t n, const int64_t* __restrict__ krow, int ncta, int64_t w,
-                                int32_t* __restrict__ cta_rows)
-{
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c > ncta) return;
-    if (c == ncta) {
-        cta_rows[c] = (int32_t)n;
-        return;
-    }
-    const int64_t total = krow[n] + w * n;
-    const int64_t target = total / ncta * c + (total % ncta) * c / ncta;
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (krow[mid] + w * mid < target) lo = mid + 1; else hi = mid;
-    }
-    cta_rows[c] = (int32_t)lo;
-}
-
-template <class T, int MODEL, bool COMP>
-cudaError_t launch_tiled(const TiledArgs& A, int grid, size_t smem, cudaStream_t st)
-{
-    static bool configured = false;  // per instantiation; all devices take the same limit
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(tiled_kernel<T, MODEL, COMP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kTileBytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    tiled_kernel<T, MODEL, COMP><<<grid, kTiledThreads, smem, st>>>(A);
-    count_launch();
-    return cudaGetLastError();
-}
-
 template <class T, int MODEL, bool COMP>
 cudaError_t launch_typed(const IterArgs& A, unsigned grid, cudaStream_t st)
 {
@@ -530,7 +323,39 @@ metrics_kernel(int pass, int64_t n, const int64_t* __restrict__ row,
                 a0 += (dl - mean) * (dl - mean);
             }
         }
-        if (pass == 0) {
+        if (pass == 0 && sizeof(T) == 4) {
+            // FP32 placements: each pair's term d^2 / delta^q in FP32 (one
+            // approximate reciprocal square root, relative error below 1e-6),
+            // four terms per lane summed in FP32, then added in FP64. FP64
+            // sqrt and divide per pair would make this pass ALU-bound on
+            // GB300's low FP64 rate.
+            const float2* pf = reinterpret_cast<const float2*>(pos);
+            const float2 qu = pf[u];
+            const float d2f = (float)(d * d);
+            const int64_t e1 = krow[u + 1];
+            for (int64_t e0 = krow[u]; e0 < e1; e0 += 128) {
+                float s = 0.f;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t e = e0 + j * 32 + lane;
+                    if (e >= e1) continue;
+                    const int64_t v = kcol[e];
+                    if (v <= u) continue;
+                    const float2 pv = pf[v];
+                    const float dx = qu.x - pv.x, dy = qu.y - pv.y;
+                    const float r2 = dx * dx + dy * dy;
+                    if (r2 >= 1e-30f) {
+                        const float ir = rsqrt_fast(r2);
+                        float w = ir;
+                        for (int i = 1; i < q; ++i) w *= ir;
+                        s += d2f * w;
+                    } else if (r2 > 0.f) {  // tiny distances: exact FP64 term
+                        a3 += d * d / dipow(sqrt((double)r2), q);
+                    }
+                }
+                a3 += (double)s;
+            }
+        } else if (pass == 0) {
             for (int64_t e = krow[u] + lane; e < krow[u + 1]; e += 32) {
                 const int64_t v = kcol[e];
                 if (v <= u) continue;
@@ -625,106 +450,13 @@ gila_status ensure_red(gila_graph* g, size_t doubles)
 
 }  // namespace
 
-void invalidate_tile_plans(gila_graph* g)
-{
-    g->tplan[0].ready = false;
-    g->tplan[1].ready = false;
-}
-
-namespace {
-
-// Decide whether the tiled kernel serves g for positions of `esz` bytes and
-// prepare its segment bounds, CTA row ranges and running-sum buffer.
-gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
-{
-    P.ready = true;
-    P.use = false;
-    const int64_t n = g->n;
-    if (n == 0 || g->nnz_khop == 0 || g->tune.tiled == 0) return GILA_OK;
-    int64_t tv_max = kTileBytes / (int64_t)esz;
-    if (g->tune.tile_vertices > 0) tv_max = std::min<int64_t>(tv_max, g->tune.tile_vertices);
-    tv_max = std::max<int64_t>(2, tv_max & ~int64_t(1));
-    const int64_t nt = (n + tv_max - 1) / tv_max;
-    const int64_t tv = std::min<int64_t>(tv_max, (((n + nt - 1) / nt) + 1) & ~int64_t(1));
-    const int min_seg = g->tune.min_segment > 0 ? g->tune.min_segment : 48;
-    const double avg_seg = (double)g->nnz_khop / ((double)n * (double)nt);
-    if (g->tune.tiled < 0 && avg_seg < min_seg) return GILA_OK;
-    gila_status s;
-    if (nt > 1) {
-        s = ensure((void**)&P.seg, &P.seg_cap, sizeof(int32_t) * (size_t)(n * (nt - 1)));
-        if (s != GILA_OK) return s;
-        s = ensure(&P.acc, &P.acc_cap, 4 * (esz / 2) * (size_t)n);
-        if (s != GILA_OK) return s;
-        const int64_t cnt = n * (nt - 1);
-        tile_seg_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, g->stream>>>(
-            n, g->krow, g->kcol, (int)nt, (int)tv, P.seg);
-        count_launch();
-    }
-    const int ncta = sm_count(g->device);
-    s = ensure((void**)&P.cta_rows, &P.cta_cap, sizeof(int32_t) * (size_t)(ncta + 1));
-    if (s != GILA_OK) return s;
-    tile_cta_kernel<<<(ncta + 1 + 255) / 256, 256, 0, g->stream>>>(n, g->krow, ncta, 32 * nt,
-                                                                  P.cta_rows);
-    count_launch();
-    GILA_CUDA(cudaGetLastError());
-    P.nt = (int32_t)nt;
-    P.tv = (int32_t)tv;
-    P.ncta = ncta;
-    P.use = true;
-    return GILA_OK;
-}
-
-}  // namespace
-
 gila_status launch_iteration(gila_graph* g, const gila_params* prm, double t, const void* pos_in,
                              void* pos_out, void* disp_out)
 {
-    if (prm->precision != GILA_FP64_ORDERED && g->n > 0) {
-        const size_t esz = is_f64(prm->precision) ? 16 : 8;
-        TilePlan& P = g->tplan[esz == 16 ? 1 : 0];
-        if (!P.ready) {
-            gila_status s = plan_tiles(g, esz, P);
-            if (s != GILA_OK) return s;
-        }
-        if (P.use && ((uintptr_t)pos_in & 15) == 0) {
-            TiledArgs A;
-            A.row = g->row;
-            A.col = g->col;
-            A.krow = g->krow;
-            A.kcol = g->kcol;
-            A.seg = P.seg;
-            A.cta_rows = P.cta_rows;
-            A.acc = P.acc;
-            A.n = g->n;
-            A.nt = P.nt;
-            A.tv = P.tv;
-            A.d = prm->d;
-            A.t = t;
-            A.p = prm->p;
-            A.q = prm->q;
-            A.pos_in = pos_in;
-            A.pos_out = pos_out;
-            A.disp_out = disp_out;
-            const size_t smem = (size_t)P.tv * esz;
-            const bool fr = (prm->p == 2 && prm->q == 1);
-            cudaError_t e;
-            switch (prm->precision) {
-            case GILA_FP64:
-                e = fr ? launch_tiled<double, kFR, false>(A, P.ncta, smem, g->stream)
-                       : launch_tiled<double, kGeneric, false>(A, P.ncta, smem, g->stream);
-                break;
-            case GILA_FP32_COMPENSATED:
-                e = fr ? launch_tiled<float, kFR, true>(A, P.ncta, smem, g->stream)
-                       : launch_tiled<float, kGeneric, true>(A, P.ncta, smem, g->stream);
-                break;
-            default:
-                e = fr ? launch_tiled<float, kFR, false>(A, P.ncta, smem, g->stream)
-                       : launch_tiled<float, kGeneric, false>(A, P.ncta, smem, g->stream);
-                break;
-            }
-            if (e != cudaSuccess) return cuda_fail(e, "tiled_kernel");
-            return GILA_OK;
-        }
+    {
+        bool handled = false;
+        gila_status s = launch_blocked(g, prm, t, pos_in, pos_out, disp_out, &handled);
+        if (s != GILA_OK || handled) return s;
     }
     if (prm->precision == GILA_FP64_ORDERED) {
         if (g->n == 0) return GILA_OK;
@@ -876,12 +608,7 @@ void free_layout(gila_graph* g)
     cudaFree(g->pos[1]);
     cudaFree(g->stage);
     cudaFree(g->red);
-    for (TilePlan& P : g->tplan) {
-        cudaFree(P.seg);
-        cudaFree(P.cta_rows);
-        cudaFree(P.acc);
-        P = TilePlan();
-    }
+    free_tile_plans(g);
     g->pos[0] = g->pos[1] = nullptr;
     g->stage = nullptr;
     g->red = nullptr;

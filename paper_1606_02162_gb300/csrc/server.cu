@@ -110,9 +110,11 @@ size_t job_bytes(int64_t n, int64_t nnz_adj, int64_t nnz_khop, int precision)
     b += 4 * (size_t)nnz_khop;                          // k-hop ids
     b += 12 * (size_t)n;                                // row classes, spare
     b += 2 * esz * (size_t)n + 16 * (size_t)n;          // placement buffers, staging
-    const int64_t tv = (200 * 1024) / (int64_t)esz;     // tile plan (worst case)
+    // blocked-path plan (worst case): the ids once more in block order, and
+    // per row and tile an offset, a length and a partial force
+    const int64_t tv = (200 * 1024) / (int64_t)esz;
     const int64_t nt = (n + tv - 1) / std::max<int64_t>(tv, 1);
-    b += 4 * (size_t)n * (size_t)std::max<int64_t>(nt - 1, 0) + 2 * esz * (size_t)n;
+    b += 4 * (size_t)nnz_khop + (16 + 2 * esz) * (size_t)n * (size_t)nt;
     return b + ((size_t)1 << 20);
 }
 

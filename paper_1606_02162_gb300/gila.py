@@ -96,7 +96,7 @@ SIGNATURES = [
     ("gila_khop_export", ctypes.c_int, [P, P, P]),
     ("gila_layout_step", ctypes.c_int, [P, PP, D, P, P, P]),
     ("gila_layout_run_device", ctypes.c_int, [P, PP, P]),
-    ("gila_layout_run", ctypes.c_int, [P, PP, P, P]),
+    ("gila_layout_run", ctypes.c_int, [P, PP, P, P, P]),
     ("gila_layout_metrics", ctypes.c_int, [P, PP, P, ctypes.POINTER(gila_metrics)]),
     ("gila_temperature", D, [PP, D, I32]),
     ("gila_profile_enable", ctypes.c_int, [P, I32]),
@@ -271,11 +271,16 @@ def gila_layout_run_device(g, prm, pos) -> None:
     _check(load().gila_layout_run_device(g, ctypes.byref(prm), _dev_ptr(pos)))
 
 
-def gila_layout_run(g, prm, pos_in, pos_out=None) -> np.ndarray:
-    """Host placement in (float64 [n, 2]), host placement out."""
+def gila_layout_run(g, prm, pos_in, pos_out=None, metrics=False):
+    """Host placement in (float64 [n, 2]), host placement out; with
+    metrics=True also the quality figures of the result: (placement, dict)."""
     src = _np(pos_in, np.float64)
     out = np.empty_like(src) if pos_out is None else pos_out
-    _check(load().gila_layout_run(g, ctypes.byref(prm), _ptr(src), _ptr(out)))
+    m = gila_metrics() if metrics else None
+    _check(load().gila_layout_run(g, ctypes.byref(prm), _ptr(src), _ptr(out),
+                                  ctypes.byref(m) if metrics else None))
+    if metrics:
+        return out, {f: getattr(m, f) for f, _ in gila_metrics._fields_}
     return out
 
 

@@ -85,8 +85,9 @@ def test_whole_layout_quality(ba, k):
     m32, p32 = res[G.GILA_FP32]
     m64, _ = res[G.GILA_FP64]
     # the device reductions agree with the oracle's on the same placement
+    # (FP32 placements: edge figures in FP64, k-hop terms in FP32 summed in FP64)
     mo32 = O.metrics(g.n, g.row_ptr, g.col_idx, okrow, okcol, p32)
-    for key in ("edge_cv", "rep_att_ratio"):
-        assert m32[key] == pytest.approx(mo32[key], rel=1e-9), key
+    for key, rel in (("edge_cv", 1e-9), ("rep_att_ratio", 2e-6)):
+        assert m32[key] == pytest.approx(mo32[key], rel=rel), key
         assert abs(m32[key] - mo[key]) <= 0.02 * abs(mo[key]), (key, m32[key], mo[key])
         assert abs(m32[key] - m64[key]) <= 0.02 * abs(m64[key]), (key, m32[key], m64[key])

@@ -356,6 +356,45 @@ def test_metrics_kernel_matches_oracle():
             assert m[key] == pytest.approx(mo[key], rel=1e-11), key
 
 
+def test_metrics_fp32_placement_matches_oracle():
+    """FP32 placements: the k-hop term of each pair is taken in FP32 and
+    summed in FP64, so rep_total agrees with the oracle on the same (FP32
+    rounded) placement to a few 1e-7; the edge figures stay in FP64."""
+    torch = _torch()
+    g = I.barabasi_albert(8000, 3, 6)
+    pos = I.uniform_positions(g.n, 9).astype(np.float32).astype(np.float64)
+    for p, q in ((2, 1), (3, 2)):
+        prm = G.params(k=2, d=1.3, p=p, q=q, precision=G.GILA_FP32)
+        okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, 2)
+        mo = O.metrics(g.n, g.row_ptr, g.col_idx, okrow, okcol, pos, d=1.3, p=p, q=q)
+        with G.Graph.from_inputs(g) as h:
+            m = G.gila_layout_metrics(h.handle, prm,
+                                      torch.tensor(pos, dtype=torch.float32, device="cuda"))
+        for key in ("edge_mean", "edge_std", "edge_cv", "att_total"):
+            assert m[key] == pytest.approx(mo[key], rel=1e-11), key
+        for key in ("rep_total", "rep_att_ratio"):
+            assert m[key] == pytest.approx(mo[key], rel=2e-6), key
+
+
+def test_layout_run_metrics_output():
+    """gila_layout_run's optional metrics equal gila_layout_metrics of the
+    placement it returns."""
+    torch = _torch()
+    g = I.barabasi_albert(3000, 3, 8)
+    pos = I.uniform_positions(g.n, 10)
+    for prec, dt in ((G.GILA_FP64, torch.float64), (G.GILA_FP32, torch.float32)):
+        prm = G.params(k=2, iters=20, precision=prec)
+        with G.Graph.from_inputs(g) as h:
+            out, m = G.gila_layout_run(h.handle, prm, pos, metrics=True)
+            m2 = G.gila_layout_metrics(h.handle, prm, torch.tensor(out, dtype=dt, device="cuda"))
+        for key in m:
+            assert m[key] == pytest.approx(m2[key], rel=1e-12), key
+    with G.Graph.from_inputs(I.path(1)) as h:
+        out, m = G.gila_layout_run(h.handle, G.params(iters=3), np.array([[0.5, 0.25]]),
+                                   metrics=True)
+        assert m["edge_cv"] == 0.0 and m["rep_total"] == 0.0
+
+
 def test_geometric_schedule_run():
     g = I.grid(20, 12)
     pos = I.uniform_positions(g.n, 5) * np.array([1.0, 0.5])
