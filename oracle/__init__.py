@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY. This package restates, in plain C (gila_oracle.c,
 FP64, OpenMP over vertices with a fixed per-vertex summation order), what
 the paper defines: the k-neighbourhoods of Section 4.5, the forces of
-Section 3.1 and the synchronous capped move of Sections 3.1 and 4.5. It is
+Section 3.1, the synchronous capped move of Sections 3.1 and 4.5, and the
+degree-one pruning and reinsertion of Sections 4.3 and 4.6. It is
 used by the tests, the smoke check and the benchmark's CPU-baseline leg, and
 by nothing else; it shares no code with the CUDA library.
 
@@ -73,6 +74,15 @@ def _load():
         lib.oracle_run.restype = I
         lib.oracle_run.argtypes = [I64, P, P, P, P, P, D, I, I, I, D, I, P]
         lib.oracle_metrics.argtypes = [I64, P, P, P, P, P, D, I, I, P]
+        lib.oracle_forces_w.argtypes = [I64, P, P, P, P, P, P, D, I, I, I64, P, P]
+        lib.oracle_step_w.argtypes = [I64, P, P, P, P, P, P, D, I, I, D, P, P]
+        lib.oracle_run_w.argtypes = [I64, P, P, P, P, P, P, D, I, I, I, D, I, P]
+        lib.oracle_run_w.restype = I
+        lib.oracle_prune.argtypes = [I64, P, P, P, P, P]
+        lib.oracle_prune.restype = I64
+        lib.oracle_pruned_csr.argtypes = [I64, P, P, P, P, P]
+        lib.oracle_pruned_csr.restype = I64
+        lib.oracle_reinsert.argtypes = [I64, P, P, P, P, P, P, P, P, D, P]
         _lib = lib
         return lib
 
@@ -134,35 +144,46 @@ def khop_rows(n, row_ptr, col_idx, k, sources):
     return counts[: src.shape[0]], out[:total]
 
 
-def forces(n, row_ptr, col_idx, krow, kcol, pos, d=1.0, p=2, q=1, sel=None):
+def _wt(wt, n):
+    if wt is None:
+        return None, None
+    w = np.ascontiguousarray(wt, dtype=np.float64)
+    assert w.shape == (n,)
+    return w, _p(w)
+
+
+def forces(n, row_ptr, col_idx, krow, kcol, pos, d=1.0, p=2, q=1, sel=None, wt=None):
     """Resultant force F(u) (Section 3.1 over N_u(k)) for all u, or for the
-    vertices in sel: float64[len, 2]."""
+    vertices in sel: float64[len, 2]. wt (float64[n], optional): the
+    repulsion exerted by v is multiplied by wt[v] (Section 4.6)."""
     lib = _load()
     row, col = _csr(n, row_ptr, col_idx)
     kr, kc = _csr(n, krow, kcol)
     P = _pos(pos, n)
+    w, wp = _wt(wt, n)
     if sel is None:
         F = np.zeros((n, 2), dtype=np.float64)
-        lib.oracle_forces(n, _p(row), _p(col), _p(kr), _p(kc), _p(P), float(d), int(p), int(q),
-                          0, None, _p(F))
+        lib.oracle_forces_w(n, _p(row), _p(col), _p(kr), _p(kc), wp, _p(P), float(d), int(p),
+                            int(q), 0, None, _p(F))
     else:
         s = np.ascontiguousarray(sel, dtype=np.int64)
         F = np.zeros((s.shape[0], 2), dtype=np.float64)
-        lib.oracle_forces(n, _p(row), _p(col), _p(kr), _p(kc), _p(P), float(d), int(p), int(q),
-                          s.shape[0], _p(s), _p(F))
+        lib.oracle_forces_w(n, _p(row), _p(col), _p(kr), _p(kc), wp, _p(P), float(d), int(p),
+                            int(q), s.shape[0], _p(s), _p(F))
     return F
 
 
-def step(n, row_ptr, col_idx, krow, kcol, pos, t, d=1.0, p=2, q=1):
+def step(n, row_ptr, col_idx, krow, kcol, pos, t, d=1.0, p=2, q=1, wt=None):
     """One synchronous capped iteration: (new positions, displacements)."""
     lib = _load()
     row, col = _csr(n, row_ptr, col_idx)
     kr, kc = _csr(n, krow, kcol)
     P = _pos(pos, n)
+    w, wp = _wt(wt, n)
     out = np.zeros((n, 2), dtype=np.float64)
     disp = np.zeros((n, 2), dtype=np.float64)
-    lib.oracle_step(n, _p(row), _p(col), _p(kr), _p(kc), _p(P), float(d), int(p), int(q),
-                    float(t), _p(out), _p(disp))
+    lib.oracle_step_w(n, _p(row), _p(col), _p(kr), _p(kc), wp, _p(P), float(d), int(p), int(q),
+                      float(t), _p(out), _p(disp))
     return out, disp
 
 
@@ -176,15 +197,16 @@ def default_t0(schedule, n, d, pos) -> float:
 
 
 def run(n, row_ptr, col_idx, krow, kcol, pos0, iters, d=1.0, p=2, q=1,
-        schedule=SCHED_LINEAR, t0=0.0):
+        schedule=SCHED_LINEAR, t0=0.0, wt=None):
     """`iters` iterations from pos0; returns the final float64[n, 2]."""
     lib = _load()
     row, col = _csr(n, row_ptr, col_idx)
     kr, kc = _csr(n, krow, kcol)
     P = _pos(pos0, n)
+    w, wp = _wt(wt, n)
     out = np.zeros((n, 2), dtype=np.float64)
-    rc = lib.oracle_run(n, _p(row), _p(col), _p(kr), _p(kc), _p(P), float(d), int(p), int(q),
-                        int(schedule), float(t0), int(iters), _p(out))
+    rc = lib.oracle_run_w(n, _p(row), _p(col), _p(kr), _p(kc), wp, _p(P), float(d), int(p),
+                          int(q), int(schedule), float(t0), int(iters), _p(out))
     if rc != 0:
         raise MemoryError("oracle_run")
     return out
@@ -201,3 +223,63 @@ def metrics(n, row_ptr, col_idx, krow, kcol, pos, d=1.0, p=2, q=1) -> dict:
                        _p(out))
     return {"edge_mean": out[0], "edge_std": out[1], "edge_cv": out[2],
             "rep_total": out[3], "att_total": out[4], "rep_att_ratio": out[5]}
+
+
+def prune(n, row_ptr, col_idx):
+    """Degree-one pruning (Section 4.3): (anchor int32[n], w int32[n],
+    newid int32[n], kept) -- anchor[v] the neighbour a removed v hangs on
+    (else -1), w[v] the number of removed neighbours of v, newid[v] the index
+    of a kept v in the pruned graph (else -1)."""
+    lib = _load()
+    row, col = _csr(n, row_ptr, col_idx)
+    anchor = np.zeros(max(n, 1), dtype=np.int32)
+    w = np.zeros(max(n, 1), dtype=np.int32)
+    newid = np.zeros(max(n, 1), dtype=np.int32)
+    kept = lib.oracle_prune(n, _p(row), _p(col), _p(anchor), _p(w), _p(newid))
+    return anchor[:n], w[:n], newid[:n], int(kept)
+
+
+def pruned_csr(n, row_ptr, col_idx, newid, kept):
+    """The subgraph induced by the kept vertices, renumbered by newid:
+    (prow int64[kept+1], pcol int32[nnz])."""
+    lib = _load()
+    row, col = _csr(n, row_ptr, col_idx)
+    nid = np.ascontiguousarray(newid, dtype=np.int32)
+    prow = np.zeros(kept + 1, dtype=np.int64)
+    pcol = np.zeros(max(col.shape[0], 1), dtype=np.int32)
+    e = lib.oracle_pruned_csr(n, _p(row), _p(col), _p(nid), _p(prow), _p(pcol))
+    return prow, pcol[:e]
+
+
+def reinsert(n, row_ptr, col_idx, newid, anchor, w, prow, pcol, ppos, d=1.0):
+    """Reinsertion (Section 4.6): the full placement float64[n, 2] from the
+    placement ppos of the pruned graph."""
+    lib = _load()
+    row, col = _csr(n, row_ptr, col_idx)
+    kept = prow.shape[0] - 1
+    nid = np.ascontiguousarray(newid, dtype=np.int32)
+    anc = np.ascontiguousarray(anchor, dtype=np.int32)
+    ww = np.ascontiguousarray(w, dtype=np.int32)
+    pr = np.ascontiguousarray(prow, dtype=np.int64)
+    pc = np.ascontiguousarray(pcol, dtype=np.int32)
+    P = _pos(ppos, kept)
+    out = np.zeros((n, 2), dtype=np.float64)
+    lib.oracle_reinsert(n, _p(row), _p(col), _p(nid), _p(anc), _p(ww), _p(pr), _p(pc), _p(P),
+                        float(d), _p(out))
+    return out
+
+
+def pipeline(n, row_ptr, col_idx, pos0, k, iters, d=1.0, p=2, q=1, schedule=SCHED_LINEAR,
+             t0=0.0):
+    """Prune (Section 4.3), lay out the pruned graph with repulsion weights
+    1 + w (Sections 4.5, 4.6; default t0 from the pruned graph), reinsert
+    (Section 4.6). pos0 is the full initial placement; the kept vertices
+    start from their own rows of it. Returns the full final placement."""
+    anchor, w, newid, kept = prune(n, row_ptr, col_idx)
+    prow, pcol = pruned_csr(n, row_ptr, col_idx, newid, kept)
+    keep = newid >= 0
+    ppos0 = np.ascontiguousarray(np.asarray(pos0, dtype=np.float64).reshape(n, 2)[keep])
+    wt = 1.0 + w[keep].astype(np.float64)
+    krow, kcol = khop(kept, prow, pcol, k)
+    ppos = run(kept, prow, pcol, krow, kcol, ppos0, iters, d, p, q, schedule, t0, wt=wt)
+    return reinsert(n, row_ptr, col_idx, newid, anchor, w, prow, pcol, ppos, d)

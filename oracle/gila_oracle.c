@@ -22,6 +22,11 @@
  *                temperature) when longer; t falls over the iterations.
  *   Section 4.5  All vertices move together after every force is known
  *                (positions change only when no message is left).
+ *   Section 4.3  Pruning: degree-one vertices are removed before the layout;
+ *                each kept vertex remembers how many it lost.
+ *   Section 4.6  Reinsertion: the removed vertices are put back on a small
+ *                circle around their neighbour; during the layout a vertex
+ *                repels with a weight that grows with that number.
  *
  * Readings where the paper is silent (kept identical on the CUDA side):
  *   - a vertex does not repel itself; a pair at distance 0 contributes 0;
@@ -29,7 +34,15 @@
  *   - temperature schedules: linear t_i = t0 (iters - i) / iters, or the
  *     geometric form of Section 5.1, t_i = t0 * 0.93^i;
  *   - the attractive and repulsive sums are formed separately in the order
- *     of the CSR rows and then added.
+ *     of the CSR rows and then added;
+ *   - pruning is one pass (vertices that reach degree one only after it stay);
+ *     a single-edge component keeps its smaller id; the repulsion weight of
+ *     a kept vertex is 1 + (number of removed neighbours), since a weight
+ *     of zero would switch off the repulsion of every vertex without
+ *     removed neighbours;
+ *   - reinsertion radius 0.2 * shortest incident edge of the pruned drawing
+ *     (0.2 * d when there is none); removed neighbours evenly spaced on the
+ *     circle, rotated to stay off the vertex's edges (see oracle_reinsert).
  *
  * Every loop over u is independent, so the OpenMP split over vertices does
  * not change any result: the per-vertex summation order is fixed.
@@ -188,11 +201,12 @@ static double ipow(double x, int e)
 
 /*
  * Resultant force on u (Section 3.1 with the repelling set of Section 4.5):
- *   repulsion: for v in N_u(k): magnitude d^2 / delta^q along (x_u - x_v)/delta
+ *   repulsion: for v in N_u(k): magnitude d^2 / delta^q along (x_u - x_v)/delta,
+ *              times wt[v] when repulsion weights are given (wt != NULL)
  *   attraction: for v adjacent to u: magnitude delta^p / d along (x_v - x_u)/delta
  */
 static void force_on(int64_t u, const int64_t *row, const int32_t *col,
-                     const int64_t *krow, const int32_t *kcol,
+                     const int64_t *krow, const int32_t *kcol, const double *wt,
                      const double *pos, double d, int p, int q, double *fx, double *fy)
 {
     const double xu = pos[2 * u], yu = pos[2 * u + 1];
@@ -204,6 +218,7 @@ static void force_on(int64_t u, const int64_t *row, const int32_t *col,
         double delta = sqrt(dx * dx + dy * dy);
         if (delta == 0.0) continue;
         double mag = d * d / ipow(delta, q);
+        if (wt) mag *= wt[v];  /* Section 4.6: v repels with its own weight */
         rx += mag * (dx / delta);
         ry += mag * (dy / delta);
     }
@@ -223,16 +238,24 @@ static void force_on(int64_t u, const int64_t *row, const int32_t *col,
 
 /* F(u) for all u (sel == NULL) or for the nsel listed vertices; F is
  * interleaved (Fx, Fy). */
-void oracle_forces(int64_t n, const int64_t *row, const int32_t *col,
-                   const int64_t *krow, const int32_t *kcol, const double *pos,
-                   double d, int p, int q, int64_t nsel, const int64_t *sel, double *F)
+void oracle_forces_w(int64_t n, const int64_t *row, const int32_t *col,
+                     const int64_t *krow, const int32_t *kcol, const double *wt,
+                     const double *pos, double d, int p, int q, int64_t nsel,
+                     const int64_t *sel, double *F)
 {
     int64_t cnt = sel ? nsel : n;
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < cnt; ++i) {
         int64_t u = sel ? sel[i] : i;
-        force_on(u, row, col, krow, kcol, pos, d, p, q, &F[2 * i], &F[2 * i + 1]);
+        force_on(u, row, col, krow, kcol, wt, pos, d, p, q, &F[2 * i], &F[2 * i + 1]);
     }
+}
+
+void oracle_forces(int64_t n, const int64_t *row, const int32_t *col,
+                   const int64_t *krow, const int32_t *kcol, const double *pos,
+                   double d, int p, int q, int64_t nsel, const int64_t *sel, double *F)
+{
+    oracle_forces_w(n, row, col, krow, kcol, NULL, pos, d, p, q, nsel, sel, F);
 }
 
 /* Section 3.1: the move is the force, cut to length t when it is longer. */
@@ -254,14 +277,15 @@ static void capped(double fx, double fy, double t, double *dx, double *dy)
  * positions at the start of the iteration, then all vertices move.
  * pos_out may not alias pos_in. disp (optional) receives the moves.
  */
-void oracle_step(int64_t n, const int64_t *row, const int32_t *col,
-                 const int64_t *krow, const int32_t *kcol, const double *pos_in,
-                 double d, int p, int q, double t, double *pos_out, double *disp)
+void oracle_step_w(int64_t n, const int64_t *row, const int32_t *col,
+                   const int64_t *krow, const int32_t *kcol, const double *wt,
+                   const double *pos_in, double d, int p, int q, double t, double *pos_out,
+                   double *disp)
 {
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t u = 0; u < n; ++u) {
         double fx, fy, mx, my;
-        force_on(u, row, col, krow, kcol, pos_in, d, p, q, &fx, &fy);
+        force_on(u, row, col, krow, kcol, wt, pos_in, d, p, q, &fx, &fy);
         capped(fx, fy, t, &mx, &my);
         pos_out[2 * u] = pos_in[2 * u] + mx;
         pos_out[2 * u + 1] = pos_in[2 * u + 1] + my;
@@ -270,6 +294,13 @@ void oracle_step(int64_t n, const int64_t *row, const int32_t *col,
             disp[2 * u + 1] = my;
         }
     }
+}
+
+void oracle_step(int64_t n, const int64_t *row, const int32_t *col,
+                 const int64_t *krow, const int32_t *kcol, const double *pos_in,
+                 double d, int p, int q, double t, double *pos_out, double *disp)
+{
+    oracle_step_w(n, row, col, krow, kcol, NULL, pos_in, d, p, q, t, pos_out, disp);
 }
 
 /* Temperature of iteration i (0-based) of `iters`.
@@ -308,10 +339,10 @@ double oracle_default_t0(int schedule, int64_t n, double d, const double *pos)
  * t0 <= 0 selects the default above. Writes the final placement to pos_out.
  * Returns 0, or -1 on allocation failure.
  */
-int oracle_run(int64_t n, const int64_t *row, const int32_t *col,
-               const int64_t *krow, const int32_t *kcol, const double *pos0,
-               double d, int p, int q, int schedule, double t0, int iters,
-               double *pos_out)
+int oracle_run_w(int64_t n, const int64_t *row, const int32_t *col,
+                 const int64_t *krow, const int32_t *kcol, const double *wt,
+                 const double *pos0, double d, int p, int q, int schedule, double t0,
+                 int iters, double *pos_out)
 {
     double *a = (double *)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
     double *b = (double *)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
@@ -320,13 +351,22 @@ int oracle_run(int64_t n, const int64_t *row, const int32_t *col,
     if (t0 <= 0.0) t0 = oracle_default_t0(schedule, n, d, pos0);
     for (int i = 0; i < iters; ++i) {
         double t = oracle_temperature(schedule, t0, i, iters);
-        oracle_step(n, row, col, krow, kcol, a, d, p, q, t, b, NULL);
+        oracle_step_w(n, row, col, krow, kcol, wt, a, d, p, q, t, b, NULL);
         double *s = a; a = b; b = s;
     }
     memcpy(pos_out, a, sizeof(double) * 2 * (size_t)n);
     free(a);
     free(b);
     return 0;
+}
+
+int oracle_run(int64_t n, const int64_t *row, const int32_t *col,
+               const int64_t *krow, const int32_t *kcol, const double *pos0,
+               double d, int p, int q, int schedule, double t0, int iters,
+               double *pos_out)
+{
+    return oracle_run_w(n, row, col, krow, kcol, NULL, pos0, d, p, q, schedule, t0, iters,
+                        pos_out);
 }
 
 /*
@@ -383,4 +423,132 @@ void oracle_metrics(int64_t n, const int64_t *row, const int32_t *col,
     out[3] = rep;
     out[4] = att;
     out[5] = att > 0.0 ? rep / att : 0.0;
+}
+
+/*
+ * Pruning (Section 4.3): every vertex with exactly one neighbour is removed
+ * before the layout and remembered by the neighbour it hangs on. When both
+ * ends of an edge have degree one (a component that is a single edge) only
+ * the end with the larger id is removed, so that every removed vertex has a
+ * kept anchor. Outputs, per original vertex v:
+ *   anchor[v] = the neighbour of v if v is removed, else -1;
+ *   w[v]      = number of removed neighbours of v (0 for removed vertices);
+ *   newid[v]  = index of v among the kept vertices in ascending id order,
+ *               or -1 if v is removed.
+ * Returns the number of kept vertices.
+ */
+int64_t oracle_prune(int64_t n, const int64_t *row, const int32_t *col, int32_t *anchor,
+                     int32_t *w, int32_t *newid)
+{
+    for (int64_t v = 0; v < n; ++v) {
+        anchor[v] = -1;
+        w[v] = 0;
+    }
+    for (int64_t v = 0; v < n; ++v) {
+        if (row[v + 1] - row[v] != 1) continue;
+        int32_t a = col[row[v]];
+        int a_is_leaf = (row[(int64_t)a + 1] - row[a] == 1);
+        if (a_is_leaf && a > v) continue; /* single edge: the smaller id stays */
+        anchor[v] = a;
+    }
+    for (int64_t v = 0; v < n; ++v)
+        if (anchor[v] >= 0) w[anchor[v]] += 1;
+    int64_t kept = 0;
+    for (int64_t v = 0; v < n; ++v) newid[v] = anchor[v] >= 0 ? -1 : (int32_t)kept++;
+    return kept;
+}
+
+/*
+ * The pruned graph: the subgraph induced by the kept vertices, renumbered by
+ * newid (ascending original order, so every row stays sorted). prow has
+ * kept + 1 entries; returns the number of stored entries written to pcol.
+ */
+int64_t oracle_pruned_csr(int64_t n, const int64_t *row, const int32_t *col,
+                          const int32_t *newid, int64_t *prow, int32_t *pcol)
+{
+    int64_t k = 0, e = 0;
+    prow[0] = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        if (newid[v] < 0) continue;
+        for (int64_t j = row[v]; j < row[v + 1]; ++j)
+            if (newid[col[j]] >= 0) pcol[e++] = newid[col[j]];
+        prow[++k] = e;
+    }
+    return e;
+}
+
+/*
+ * Reinsertion (Section 4.6). Given the placement ppos of the pruned graph
+ * (prow, pcol), every kept vertex keeps its position and its removed
+ * neighbours are placed on the circle around it of radius
+ *   rho = 0.2 * (length of the shortest pruned-graph edge at v)
+ * (0.2 * d when v has no such edge), evenly spaced: with m removed
+ * neighbours the i-th (ascending original id) goes to angle theta + i s,
+ * s = 2 pi / m, in the order of v's adjacency row (ascending ids for a
+ * sorted CSR). The rotation theta keeps them off v's edges: among the
+ * REINSERT_CANDIDATES rotations theta_c = s (c + 1/2) / REINSERT_CANDIDATES
+ * it is the one whose smallest angular distance (modulo s) to the direction
+ * of an edge at v is largest, the smallest c on ties. pos_out holds the
+ * full placement (original ids).
+ */
+#define REINSERT_CANDIDATES 64
+#define REINSERT_RHO 0.2
+
+static double angle_mod(double a, double s)
+{
+    double r = a - s * floor(a / s);
+    if (r >= s) r -= s;
+    if (r < 0.0) r = 0.0;
+    return r;
+}
+
+void oracle_reinsert(int64_t n, const int64_t *row, const int32_t *col, const int32_t *newid,
+                     const int32_t *anchor, const int32_t *w, const int64_t *prow,
+                     const int32_t *pcol, const double *ppos, double d, double *pos_out)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int64_t v = 0; v < n; ++v) {
+        if (newid[v] < 0) continue;
+        int64_t pv = newid[v];
+        double xv = ppos[2 * pv], yv = ppos[2 * pv + 1];
+        pos_out[2 * v] = xv;
+        pos_out[2 * v + 1] = yv;
+        int m = w[v];
+        if (m == 0) continue;
+        double s = two_pi / (double)m;
+        double shortest = INFINITY;
+        for (int64_t j = prow[pv]; j < prow[pv + 1]; ++j) {
+            double dx = ppos[2 * (int64_t)pcol[j]] - xv, dy = ppos[2 * (int64_t)pcol[j] + 1] - yv;
+            double len = sqrt(dx * dx + dy * dy);
+            if (len < shortest) shortest = len;
+        }
+        double rho = REINSERT_RHO * (prow[pv + 1] > prow[pv] ? shortest : d);
+        int best = 0;
+        double best_score = -1.0;
+        for (int c = 0; c < REINSERT_CANDIDATES; ++c) {
+            double theta = s * ((double)c + 0.5) / (double)REINSERT_CANDIDATES;
+            double score = INFINITY;
+            for (int64_t j = prow[pv]; j < prow[pv + 1]; ++j) {
+                double dx = ppos[2 * (int64_t)pcol[j]] - xv;
+                double dy = ppos[2 * (int64_t)pcol[j] + 1] - yv;
+                double diff = fabs(angle_mod(atan2(dy, dx), s) - theta);
+                double dist = diff < s - diff ? diff : s - diff;
+                if (dist < score) score = dist;
+            }
+            if (score > best_score) {
+                best_score = score;
+                best = c;
+            }
+        }
+        double theta = s * ((double)best + 0.5) / (double)REINSERT_CANDIDATES;
+        int i = 0;
+        for (int64_t j = row[v]; j < row[v + 1]; ++j) {
+            int32_t u = col[j];
+            if (anchor[u] != v) continue;
+            double a = theta + (double)i * s;
+            pos_out[2 * (int64_t)u] = xv + rho * cos(a);
+            pos_out[2 * (int64_t)u + 1] = yv + rho * sin(a);
+            ++i;
+        }
+    }
 }
