@@ -126,6 +126,36 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, dist, device) -> float:
+    """The sum of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def init_dist(ws, local):
+    """NCCL process group for torchrun replicas (None on one GPU)."""
+    if ws <= 1:
+        return None
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return dist
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -226,6 +256,7 @@ def run_batch(args, wl, ws, rank, local):
     from paper_1606_02162_gb300 import gila as G
     from paper_1606_02162_gb300 import inputs as I
     torch.cuda.set_device(local)
+    dist = init_dist(ws, local)
     graphs = I.batch_mix(4096, 50, 5000, 4)
     pos = [I.uniform_positions(g.n, 400000 + i) for i, g in enumerate(graphs)]
     k, iters = wl["k"], wl["iters"]
@@ -248,15 +279,20 @@ def run_batch(args, wl, ws, rank, local):
         clocks = ClockSampler(local)
         clocks.start()
         l0 = G.gila_kernel_launches()
+        if dist is not None:
+            dist.barrier()
         ms = _timed_region(torch, stream, step, args.steps)
+        if dist is not None:
+            dist.barrier()
+        ms = max_over_ranks(ms, dist, "cuda")
         launches = G.gila_kernel_launches() - l0
         clk = clocks.stop()
         nnz = G.gila_batch_info(b.handle)["nnz_khop"]
         P = nnz + sum(g.nnz for g in graphs)
         b.close()
-        out[name] = {"layouts_per_s": len(graphs) * args.steps / (ms / 1e3),
+        out[name] = {"layouts_per_s": ws * len(graphs) * args.steps / (ms / 1e3),
                      "ms_per_step": ms / args.steps,
-                     "pairs_per_s": P * iters * args.steps / (ms / 1e3),
+                     "pairs_per_s": ws * P * iters * args.steps / (ms / 1e3),
                      "gpu_launches": launches, "clocks": clk}
     # one graph at a time (same kernels of the single-graph path), on a
     # systematic sample of every 16th graph
@@ -279,6 +315,8 @@ def run_batch(args, wl, ws, rank, local):
     for h in hs:
         h.close()
     plain_lps = len(sample) / (pms / 1e3)
+    if dist is not None:
+        dist.destroy_process_group()
     if rank != 0:
         return 0
     line = {
@@ -309,6 +347,7 @@ def run_serve(args, wl, ws, rank, local, count=48, emax=3e5):
     from paper_1606_02162_gb300 import gila as G
     from paper_1606_02162_gb300 import inputs as I
     torch.cuda.set_device(local)
+    dist = init_dist(ws, local)
     reqs = I.serving_requests(count, 5, emax=emax)
     graphs = [I.barabasi_albert_fast(r["n"], 3, r["seed"]) for r in reqs]
     pos = [I.uniform_positions(g.n, r["seed"]) for g, r in zip(graphs, reqs)]
@@ -338,6 +377,8 @@ def run_serve(args, wl, ws, rank, local, count=48, emax=3e5):
             done = start + sv
             plain_lat.append(done - a)
         lat = []
+        if dist is not None:
+            dist.barrier()
         with G.Server(budget, 16) as s:
             t0 = time.perf_counter()
             tickets = []
@@ -349,24 +390,27 @@ def run_serve(args, wl, ws, rank, local, count=48, emax=3e5):
             for tk in tickets:
                 _, info = s.wait(tk)
                 lat.append(info["latency_ms"] / 1e3)
-            makespan = time.perf_counter() - t0
+            makespan = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
             st = s.stats()
         lat = np.array(lat)
         plain_lat = np.array(plain_lat)
         runs.append({"arrival_rate_per_s": rate, "rate_vs_plain_capacity": mult,
-                     "server": {"layouts_per_s": count / makespan,
+                     "server": {"layouts_per_s": ws * count / makespan,
                                 "p50_ms": float(np.percentile(lat, 50) * 1e3),
                                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
                                 "bytes_peak": st["bytes_peak"]},
-                     "plain_one_at_a_time": {"layouts_per_s": count / done,
+                     "plain_one_at_a_time": {"layouts_per_s": ws * count / done,
                                              "p50_ms": float(np.percentile(plain_lat, 50) * 1e3),
                                              "p99_ms": float(np.percentile(plain_lat, 99) * 1e3)}})
+    if dist is not None:
+        dist.destroy_process_group()
     if rank != 0:
         return 0
     top = runs[-1]
     line = {
         "metric": "layouts/s", "value": top["server"]["layouts_per_s"], "unit": "layouts/s",
-        "n_gpus": ws, "steps": 1, "warmup": 2, "ms_per_step": count / top["server"]["layouts_per_s"] * 1e3,
+        "n_gpus": ws, "steps": 1, "warmup": 2,
+        "ms_per_step": ws * count / top["server"]["layouts_per_s"] * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": wl["desc"], "requests": count, "budget": budget,
@@ -409,10 +453,7 @@ def main():
     from paper_1606_02162_gb300 import inputs as I
 
     torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dist = init_dist(ws, local)
 
     def barrier():
         if dist is not None:
@@ -467,10 +508,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     prof = G.gila_profile_read(h.handle)
     G.gila_profile_enable(h.handle, False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_step = ms / args.steps
     value = P * iters * args.steps * ws / (ms / 1e3)
     iter_ms = prof["iter_ms"] / max(prof["iter_launches"], 1)
@@ -514,11 +552,7 @@ def main():
             e2e_step()
         torch.cuda.synchronize()
         barrier()
-        e2e_s = time.perf_counter() - t
-        if dist is not None:
-            tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t, dist, "cuda")
         e2e = {"value": P * iters * args.steps * ws / e2e_s, "unit": "pairs/s",
                "h2d_bytes_per_step": int(row.nbytes + col.nbytes + pin_in.nbytes),
                "d2h_bytes_per_step": int(pin_out.nbytes) + 2 * 32,
