@@ -57,6 +57,37 @@ WORKLOADS = {
                        "[1e3, 3e5], k in {2, 3}, 300 iterations, FP32"),
 }
 PREC = {"fp32": 0, "fp64": 1, "fp32c": 2}
+
+# DRAM traffic of one iteration (ncu dram__bytes_read.sum + dram__bytes_write.sum
+# of its blocked_kernel and combine_kernel launches) on a workload, with the
+# SHA-256 of the kernel sources it was measured on: reported only while those
+# sources are unchanged, else null.
+KERNEL_SOURCES = ("paper_1606_02162_gb300/csrc/blocked.cu",
+                  "paper_1606_02162_gb300/csrc/force.cuh",
+                  "paper_1606_02162_gb300/csrc/device_util.cuh")
+NCU_TRAFFIC = {
+    "ba100k_k3": {"bytes": 965292544 + 7882752 + 10422784,
+                  "kernels": "blocked_kernel + combine_kernel (one iteration)",
+                  "profile": "profiles/blocked_kernel_ba100k_k3.md, "
+                             "profiles/combine_kernel_ba100k_k3.md",
+                  "sources_sha256": "eaa62a7f3b221f628926a592057765c9846615496f75e589b3da07963e0a3ac4"},
+}
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload: str):
+    rec = NCU_TRAFFIC.get(workload)
+    if rec is None or rec["sources_sha256"] != kernel_sources_sha256():
+        return None
+    return rec
 DTYPE_NAME = {"fp32": "f32", "fp64": "f64", "fp32c": "f32"}
 
 
@@ -520,12 +551,20 @@ def main():
     # 8 B position write per vertex
     elem = 16 if prec == G.GILA_FP64 else 8
     alg_bytes = (4 + elem) * P + 8 * (g.n + 1) + 2 * elem * g.n
+    # compulsory DRAM bytes: the ids once, row offsets, own position in and out
+    # (the gathered positions stay on chip)
+    comp_bytes = 4 * P + 8 * (g.n + 1) + 2 * elem * g.n
     hbm, peak_kind = peaks()
     achieved = alg_bytes / (iter_ms / 1e3) / 1e9
+    tr = measured_traffic(args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
-                "kernel": "iteration_kernel", "peak_source": peak_kind,
-                "alg_bytes_per_launch": alg_bytes}
+                "frac": achieved / hbm, "traffic": tr["bytes"] if tr else None,
+                "kernel": tr["kernels"] if tr else "iteration (all kernels of one iteration)",
+                "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                "compulsory_bytes_per_launch": comp_bytes,
+                "compulsory_gbs": comp_bytes / (iter_ms / 1e3) / 1e9,
+                "compulsory_frac": comp_bytes / (iter_ms / 1e3) / 1e9 / hbm,
+                "traffic_source": tr["profile"] if tr else None}
 
     # ------------------------------------------------ end to end (host buffers)
     e2e = None

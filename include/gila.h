@@ -104,8 +104,10 @@ typedef struct gila_tuning {
     int32_t tiled;         /* -1 automatic (default), 0 never, 1 always: stage positions in
                               shared-memory tiles instead of gathering them through L2 */
     int32_t tile_vertices; /* positions per tile; 0 = as many as fit in 200 KiB */
-    int32_t min_segment;   /* automatic mode tiles when nnz_khop / (n * tiles) >= this (48) */
-    int32_t small_max;     /* untiled kernel: rows of length <= this use 8-lane groups (32) */
+    int32_t min_segment;   /* automatic mode tiles FP32 placements with at least 10^8 k-hop
+                              entries when nnz_khop / (n * tiles) >= this (48); FP64 only
+                              when tiled = 1 */
+    int32_t small_max;     /* untiled kernel: rows of length <= this use 8-lane groups (64) */
     int32_t warp_max;      /* ... rows <= this use one warp (8192) */
     int32_t block_max;     /* ... rows <= this use one block (65536); longer rows are chunked */
     int32_t chunk;         /* entries per chunk of a chunked row (32768) */
@@ -316,6 +318,68 @@ gila_status gila_server_poll(gila_server* s, uint64_t ticket, int32_t* done);
 /* Counters: jobs completed / failed / queued / on the GPU, device bytes
  * reserved now and at most, and the budget. */
 gila_status gila_server_get_stats(gila_server* s, gila_server_stats* out);
+
+/* ------------------------------------------------------------------------
+ * Degree-one pruning and reinsertion (Sections 4.3 and 4.6).
+ *
+ * Pruning removes, in one pass, every vertex with exactly one neighbour (of
+ * the two ends of a single-edge component only the larger id) and remembers
+ * the neighbour it hangs on. The kept vertices, in ascending id order, form
+ * the pruned graph (the subgraph they induce), a gila_graph whose vertices
+ * repel with weight 1 + (number of removed neighbours) (Section 4.6: the
+ * repulsion of a vertex grows with the vertices that will be put back
+ * around it). Reinsertion puts the removed neighbours of a kept vertex v on
+ * the circle around v of radius 0.2 x (shortest pruned-graph edge at v, or
+ * 0.2 d when v has none), evenly spaced in the order of v's adjacency row,
+ * at the one of 64 rotations s (c + 1/2) / 64 (s = 2 pi / count) whose
+ * smallest angular distance, modulo s, to the direction of an edge at v is
+ * largest (the smallest c on ties). The paper fixes the radius factor 0.2;
+ * the candidate rotations are this library's reading of "avoiding edge
+ * overlap".
+ * ------------------------------------------------------------------------ */
+typedef struct gila_pruned gila_pruned;
+
+/* Repulsion weights: the repulsion that vertex v exerts is multiplied by
+ * weight_host[v] (double[n], finite, >= 0; copied). NULL removes them.
+ * Applied by the plain iteration kernel (automatic tiling then stays off);
+ * GILA_FP64_ORDERED rejects weighted graphs with GILA_EINVAL. The quality
+ * figures of gila_layout_metrics stay unweighted. */
+gila_status gila_graph_set_repulsion_weights(gila_graph* g, const double* weight_host);
+
+/* Prune g on its device and stream. *out owns the pruned graph (with its
+ * weights set); g must outlive *out. Synchronises g's stream. */
+gila_status gila_prune_degree_one(gila_graph* g, gila_pruned** out);
+void gila_pruned_destroy(gila_pruned* p);
+/* The pruned graph, owned by p: usable with every gila_graph call (k-hop
+ * build, tuning, steps, runs, metrics); ids are 0..kept-1. */
+gila_graph* gila_pruned_graph(gila_pruned* p);
+/* Kept and removed vertex counts (either pointer may be NULL). */
+gila_status gila_pruned_info(const gila_pruned* p, int64_t* kept, int64_t* removed);
+/* Host copies over the original ids (each may be NULL): anchor int32[n]
+ * (neighbour of a removed vertex, else -1), w int32[n] (removed neighbours
+ * of a kept vertex, else 0), newid int32[n] (index in the pruned graph of a
+ * kept vertex, else -1). Synchronous. */
+gila_status gila_pruned_export(const gila_pruned* p, int32_t* anchor, int32_t* w, int32_t* newid);
+/* Gather the kept vertices' rows of a full device placement (n float2 or
+ * double2 per precision) into a pruned placement (kept of the same type).
+ * Asynchronous on g's stream. */
+gila_status gila_pruned_gather(gila_pruned* p, int32_t precision, const void* pos_full_dev,
+                               void* pos_pruned_dev);
+/* Reinsertion: write the full placement (n float2 or double2 per
+ * prm->precision; prm->d gives the radius of vertices without edges) from a
+ * pruned placement. Asynchronous on g's stream. */
+gila_status gila_reinsert_degree_one(gila_pruned* p, const gila_params* prm,
+                                     const void* pos_pruned_dev, void* pos_full_dev);
+/* The whole pipeline on a full device placement (n float2 or double2):
+ * gather the kept vertices, lay out the pruned graph with prm (default t0
+ * from the pruned graph's n), reinsert. The result replaces the input.
+ * GILA_FP64_ORDERED is rejected (weighted repulsion). */
+gila_status gila_layout_pruned_run_device(gila_pruned* p, const gila_params* prm,
+                                          void* pos_full_dev_inout);
+/* The same from and to host memory (double[2n] of the original graph);
+ * returns when the result is on the host. */
+gila_status gila_layout_pruned_run(gila_pruned* p, const gila_params* prm,
+                                   const double* pos_in_host, double* pos_out_host);
 
 /* Temperature of iteration i under prm (t0 = resolved initial temperature). */
 double gila_temperature(const gila_params* prm, double t0, int32_t i);

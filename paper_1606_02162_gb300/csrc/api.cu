@@ -170,6 +170,35 @@ void simplify_csr(int64_t n, const int64_t* row, const int32_t* col, std::vector
 }
 
 }  // namespace
+gila_status graph_create_from_device(int64_t n, const int64_t* row_dev, const int32_t* col_dev,
+                                     int64_t nnz, cudaStream_t st, gila_graph** out)
+{
+    *out = nullptr;
+    gila_graph* g = new (std::nothrow) gila_graph();
+    if (!g) return fail(GILA_ENOMEM, "host allocation");
+    cudaError_t e = cudaGetDevice(&g->device);
+    g->n = n;
+    g->nnz_adj = nnz;
+    g->stream = st;
+    if (e == cudaSuccess) e = cudaMalloc(&g->row, sizeof(int64_t) * (size_t)(n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->row, row_dev, sizeof(int64_t) * (size_t)(n + 1),
+                            cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(g->col, col_dev, sizeof(int32_t) * (size_t)nnz,
+                            cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        gila_status s = cuda_fail(e, "graph copy");
+        gila_graph_destroy(g);
+        return s;
+    }
+    *out = g;
+    return GILA_OK;
+}
+
+
 }  // namespace gila
 
 using namespace gila;
@@ -271,6 +300,19 @@ gila_status gila_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* 
     }
     *out = g;
     return GILA_OK;
+}
+
+
+gila_status gila_graph_set_repulsion_weights(gila_graph* g, const double* weight_host)
+{
+    if (!g) return fail(GILA_EINVAL, "graph is NULL");
+    gila_status s = use_device(g);
+    if (s != GILA_OK) return s;
+    if (weight_host)
+        for (int64_t i = 0; i < g->n; ++i)
+            if (!(weight_host[i] >= 0.0) || !std::isfinite(weight_host[i]))
+                return fail(GILA_EINVAL, "repulsion weights must be finite and >= 0");
+    return set_repulsion_weights(g, weight_host, false);
 }
 
 void gila_graph_destroy(gila_graph* g)

@@ -31,6 +31,7 @@ constexpr int kSmemCap = 227 * 1024;
 constexpr int kMaxRows = 4096;  // rows per range (directory in shared memory)
 constexpr int kTileBudget = kSmemCap - (kMaxRows + 1) * 4 - 4096;
 constexpr uint32_t kBulkChunk = 32768;      // bytes per bulk copy instruction
+constexpr int64_t kBlockedMinNnz = 100000000;  // automatic mode: k-hop entries needed
 constexpr uint32_t kWaitPolls = 1u << 24;   // bound on mbarrier polls (far above any copy)
 
 // Set when a CTA gave up waiting for its tile copy (the launch's partials
@@ -158,6 +159,8 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
         while (ri < nrows && D[ri + 1] <= a) ++ri;  // skip empty rows at a
         int32_t rs = D[ri], re = D[ri + 1];
         P2 xr = pos[u0 + ri];
+        // the next row's own position is fetched one row ahead
+        P2 xn = pos[u0 + (ri + 1 < nrows ? ri + 1 : ri)];
         Acc<T, COMP> acc;
         const uint4* ids4 = reinterpret_cast<const uint4*>(A.tk + bs);
         auto finalize = [&](bool started_before, int row) {
@@ -216,6 +219,7 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                 }
                 if (re > lim) break;  // this row goes on in the next step
                 finalize(rs < a, ri);
+                const int prev = ri;
                 ++ri;
                 while (ri < nrows && D[ri + 1] == D[ri]) ++ri;  // empty rows stay zero
                 if (ri >= nrows || D[ri] >= b) {
@@ -224,7 +228,8 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                 }
                 rs = D[ri];
                 re = D[ri + 1];
-                xr = pos[u0 + ri];
+                xr = (ri == prev + 1) ? xn : pos[u0 + ri];
+                xn = pos[u0 + (ri + 1 < nrows ? ri + 1 : ri)];
             }
         }
         if (!done && ri < nrows && re > b) {
@@ -506,7 +511,14 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
     const int64_t tv = std::min<int64_t>(tv_max, (((n + nt - 1) / nt) + 1) & ~int64_t(1));
     const int min_seg = g->tune.min_segment > 0 ? g->tune.min_segment : 48;
     const double avg_seg = (double)g->nnz_khop / ((double)n * (double)nt);
-    if (g->tune.tiled < 0 && avg_seg < min_seg) return GILA_OK;
+    // automatic mode: only where the gathers, not the arithmetic, bound the
+    // step and the lists are long enough to pay for a tile per CTA: FP64 is
+    // limited by GB300's FP64 rate (and its tiles hold half as many
+    // positions); below about 10^8 entries the plain kernel was faster on
+    // every Barabasi-Albert graph measured (n = 10^3 .. 3 10^4, k = 2, 3)
+    if (g->tune.tiled < 0 &&
+        (avg_seg < min_seg || esz == 16 || g->nnz_khop < kBlockedMinNnz))
+        return GILA_OK;
     const int64_t cells = n * nt;
     gila_status s = ensure((void**)&P.len, &P.len_cap, sizeof(int64_t) * (size_t)cells);
     if (s != GILA_OK) return s;
@@ -609,7 +621,8 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
                            void* pos_out, void* disp_out, bool* handled)
 {
     *handled = false;
-    if (prm->precision == GILA_FP64_ORDERED || g->n == 0) return GILA_OK;
+    // repulsion weights are applied by the plain kernel only
+    if (prm->precision == GILA_FP64_ORDERED || g->n == 0 || g->wt64) return GILA_OK;
     const size_t esz = is_f64(prm->precision) ? 16 : 8;
     TilePlan& P = g->tplan[esz == 16 ? 1 : 0];
     if (!P.ready) {

@@ -141,13 +141,16 @@ struct PosSource {
 // Fruchterman-Reingold (q = 1) in FP32 that is d^2 * rsqrt(r^2)^2: one MUFU
 // and two multiplies, no divide. A pair at distance 0 adds nothing. With
 // UNSCALED the factor d^2 is left out (the caller multiplies the row's sum
-// by it once).
-template <class T, int MODEL, bool COMP, int SRC = kSrcGlobal, bool UNSCALED = false>
+// by it once). With WEIGHTED the term is multiplied by wt[v], the repulsion
+// weight of the repelling vertex (Section 4.6).
+template <class T, int MODEL, bool COMP, int SRC = kSrcGlobal, bool UNSCALED = false,
+          bool WEIGHTED = false>
 struct Rep {
     using P2 = typename V2<T>::type;
     PosSource<T, SRC> src;
     T xu, yu, d2;
     int q;
+    const T* __restrict__ wt = nullptr;
 
     __device__ __forceinline__ void operator()(uint32_t v, Acc<T, COMP>& a) const
     {
@@ -164,6 +167,7 @@ struct Rep {
                 c = (UNSCALED ? T(1) : d2) / (ipow_(dl, q) * dl);
             }
         }
+        if (WEIGHTED) c *= __ldg(wt + v);
         a.add(c * dx, c * dy);
     }
 
@@ -250,7 +254,6 @@ __device__ __forceinline__ void row_sum_rel(const uint32_t* __restrict__ ids, in
 {
     const uint32_t* p = ids + s;
     const int len = (int)(e - s);
-#pragma unroll 4
     for (int j = gl; j < len; j += G) f(ld_id(p + j), a);
 }
 

@@ -37,7 +37,7 @@ inline bool is_f64(int precision)
 //   class 3: longer, split into chunks of kChunk entries, one block each,
 //            summed in chunk order by the last block to finish
 struct BinConfig {
-    int small_max = 32;
+    int small_max = 64;  // rows of 33..64 entries on a whole warp left most lanes idle (mesh: 4x)
     int group_small = 8;
     int warp_max = 8192;
     int block_max = 65536;
@@ -140,6 +140,9 @@ struct gila_graph {
     // FP64 reduction scratch
     double* red = nullptr;
     size_t red_cap = 0;
+    // repulsion weights (Section 4.6), both widths; null when unset
+    double* wt64 = nullptr;
+    float* wt32 = nullptr;
     // profiling
     bool prof_on = false;
     std::vector<gila::ProfileRec> prof;
@@ -174,6 +177,11 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
 gila_status blocked_tile_wait_failed(cudaStream_t st);
 gila_status convert_positions(gila_graph* g, int precision, const double* src, void* dst,
                               bool to_device_type);
+// Repulsion weights from host or device doubles (null clears); synchronises.
+gila_status set_repulsion_weights(gila_graph* g, const double* w, bool w_on_device);
+// Upload a graph from device CSR arrays (copied; ids trusted).
+gila_status graph_create_from_device(int64_t n, const int64_t* row_dev, const int32_t* col_dev,
+                                     int64_t nnz, cudaStream_t st, gila_graph** out);
 void free_layout(gila_graph* g);
 
 // memory helper: grow a device buffer to at least `bytes`

@@ -48,6 +48,7 @@ struct IterArgs {
     const void* pos_in;
     void* pos_out;
     void* disp_out;
+    const void* wt;  // repulsion weights (T[n]) or null
 };
 
 template <class T>
@@ -84,8 +85,8 @@ __device__ __forceinline__ void block_reduce(Acc<T, COMP>& a, T* sh)
 
 // Repulsion over k-hop entries [ks, ke) of u and, when with_att, attraction
 // over u's adjacency row, by lanes gl = 0..G-1 of a group.
-template <class T, int MODEL, bool COMP, class P2>
-__device__ __forceinline__ void vertex_sum(const IterArgs& A, Rep<T, MODEL, COMP> rep,
+template <class T, int MODEL, bool COMP, class R, class P2>
+__device__ __forceinline__ void vertex_sum(const IterArgs& A, R rep,
                                            Att<T, MODEL, COMP> att, int64_t u, P2 pu, int64_t ks,
                                            int64_t ke, bool with_att, int gl, int G,
                                            Acc<T, COMP>& a)
@@ -101,7 +102,7 @@ __device__ __forceinline__ void vertex_sum(const IterArgs& A, Rep<T, MODEL, COMP
     }
 }
 
-template <class T, int MODEL, bool COMP>
+template <class T, int MODEL, bool COMP, bool W>
 __global__ void __launch_bounds__(kThreads)
 iteration_kernel(const IterArgs A)
 {
@@ -109,10 +110,11 @@ iteration_kernel(const IterArgs A)
     __shared__ T sh[kWarpsPerBlock * 4];
     __shared__ int s_last;
     const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos_in);
-    Rep<T, MODEL, COMP> rep;
+    Rep<T, MODEL, COMP, kSrcGlobal, false, W> rep;
     rep.src.pos = pos;
     rep.d2 = (T)(A.d * A.d);
     rep.q = A.q;
+    rep.wt = reinterpret_cast<const T*>(A.wt);
     Att<T, MODEL, COMP> att;
     att.src.pos = pos;
     att.inv_d = (T)(1.0 / A.d);
@@ -125,7 +127,7 @@ iteration_kernel(const IterArgs A)
         const int64_t u = ch.vertex;
         const P2 pu = pos[u];
         Acc<T, COMP> a;
-        vertex_sum(A, rep, att, u, pu, ch.begin, ch.end, b == ch.first, threadIdx.x, kThreads, a);
+        vertex_sum<T, MODEL, COMP>(A, rep, att, u, pu, ch.begin, ch.end, b == ch.first, threadIdx.x, kThreads, a);
         block_reduce<T, COMP>(a, sh);
         if (threadIdx.x == 0) {
             double* part = A.partials + (int64_t)b * 4;
@@ -156,7 +158,7 @@ iteration_kernel(const IterArgs A)
         const int64_t u = A.list2[b];
         const P2 pu = pos[u];
         Acc<T, COMP> a;
-        vertex_sum(A, rep, att, u, pu, A.krow[u], A.krow[u + 1], true, threadIdx.x, kThreads, a);
+        vertex_sum<T, MODEL, COMP>(A, rep, att, u, pu, A.krow[u], A.krow[u + 1], true, threadIdx.x, kThreads, a);
         block_reduce<T, COMP>(a, sh);
         if (threadIdx.x == 0) apply_move_it<T>(A, u, pu.x, pu.y, a.fx(), a.fy());
         return;
@@ -169,7 +171,7 @@ iteration_kernel(const IterArgs A)
         const int64_t u = A.list1[i];
         const P2 pu = pos[u];
         Acc<T, COMP> a;
-        vertex_sum(A, rep, att, u, pu, A.krow[u], A.krow[u + 1], true, lane, 32, a);
+        vertex_sum<T, MODEL, COMP>(A, rep, att, u, pu, A.krow[u], A.krow[u + 1], true, lane, 32, a);
         a.group_reduce(32);
         if (lane == 0) apply_move_it<T>(A, u, pu.x, pu.y, a.fx(), a.fy());
         return;
@@ -188,7 +190,7 @@ iteration_kernel(const IterArgs A)
         pu.y = T(0);
         if (live) {
             pu = pos[u];
-            vertex_sum(A, rep, att, u, pu, A.krow[u], A.krow[u + 1], true, gl, G, a);
+            vertex_sum<T, MODEL, COMP>(A, rep, att, u, pu, A.krow[u], A.krow[u + 1], true, gl, G, a);
         }
         a.group_reduce(G);
         if (live && gl == 0) apply_move_it<T>(A, u, pu.x, pu.y, a.fx(), a.fy());
@@ -267,7 +269,10 @@ ordered_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __rest
 template <class T, int MODEL, bool COMP>
 cudaError_t launch_typed(const IterArgs& A, unsigned grid, cudaStream_t st)
 {
-    iteration_kernel<T, MODEL, COMP><<<grid, kThreads, 0, st>>>(A);
+    if (A.wt)
+        iteration_kernel<T, MODEL, COMP, true><<<grid, kThreads, 0, st>>>(A);
+    else
+        iteration_kernel<T, MODEL, COMP, false><<<grid, kThreads, 0, st>>>(A);
     count_launch();
     return cudaGetLastError();
 }
@@ -459,6 +464,7 @@ gila_status launch_iteration(gila_graph* g, const gila_params* prm, double t, co
         if (s != GILA_OK || handled) return s;
     }
     if (prm->precision == GILA_FP64_ORDERED) {
+        if (g->wt64) return fail(GILA_EINVAL, "GILA_FP64_ORDERED takes no repulsion weights");
         if (g->n == 0) return GILA_OK;
         const unsigned grid = (unsigned)((g->n * 32 + kThreads - 1) / kThreads);
         ordered_kernel<<<grid, kThreads, 0, g->stream>>>(
@@ -496,6 +502,7 @@ gila_status launch_iteration(gila_graph* g, const gila_params* prm, double t, co
     A.pos_in = pos_in;
     A.pos_out = pos_out;
     A.disp_out = disp_out;
+    A.wt = is_f64(prm->precision) ? (const void*)g->wt64 : (const void*)g->wt32;
     const int64_t grid = (int64_t)A.b3 + A.b2 + A.b1 + A.b0;
     if (grid == 0) return GILA_OK;
     const bool fr = (prm->p == 2 && prm->q == 1);
@@ -602,12 +609,47 @@ gila_status convert_positions(gila_graph* g, int precision, const double* src, v
     return GILA_OK;
 }
 
+__global__ void weights_to_f32_kernel(int64_t n, const double* __restrict__ w,
+                                      float* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)w[i];
+}
+
+gila_status set_repulsion_weights(gila_graph* g, const double* w, bool w_on_device)
+{
+    if (!w) {
+        cudaFree(g->wt64);
+        cudaFree(g->wt32);
+        g->wt64 = nullptr;
+        g->wt32 = nullptr;
+        return GILA_OK;
+    }
+    const size_t n = (size_t)std::max<int64_t>(g->n, 1);
+    if (!g->wt64) GILA_CUDA(cudaMalloc(&g->wt64, sizeof(double) * n));
+    if (!g->wt32) GILA_CUDA(cudaMalloc(&g->wt32, sizeof(float) * n));
+    if (g->n == 0) return GILA_OK;
+    GILA_CUDA(cudaMemcpyAsync(g->wt64, w, sizeof(double) * (size_t)g->n,
+                              w_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              g->stream));
+    weights_to_f32_kernel<<<(unsigned)((g->n + 255) / 256), 256, 0, g->stream>>>(g->n, g->wt64,
+                                                                              g->wt32);
+    count_launch();
+    GILA_CUDA(cudaGetLastError());
+    GILA_CUDA(cudaStreamSynchronize(g->stream));
+    return GILA_OK;
+}
+
 void free_layout(gila_graph* g)
 {
     cudaFree(g->pos[0]);
     cudaFree(g->pos[1]);
     cudaFree(g->stage);
     cudaFree(g->red);
+    cudaFree(g->wt64);
+    cudaFree(g->wt32);
+    g->wt64 = nullptr;
+    g->wt32 = nullptr;
     free_tile_plans(g);
     g->pos[0] = g->pos[1] = nullptr;
     g->stage = nullptr;

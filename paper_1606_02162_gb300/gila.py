@@ -116,6 +116,16 @@ SIGNATURES = [
     ("gila_layout_batch_device", ctypes.c_int, [P, PP, P]),
     ("gila_layout_batch_run", ctypes.c_int, [P, PP, P, P]),
     ("gila_layout_batch", ctypes.c_int, [P, I32, PP, P, P]),
+    ("gila_graph_set_repulsion_weights", ctypes.c_int, [P, P]),
+    ("gila_prune_degree_one", ctypes.c_int, [P, ctypes.POINTER(P)]),
+    ("gila_pruned_destroy", None, [P]),
+    ("gila_pruned_graph", P, [P]),
+    ("gila_pruned_info", ctypes.c_int, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+    ("gila_pruned_export", ctypes.c_int, [P, P, P, P]),
+    ("gila_pruned_gather", ctypes.c_int, [P, I32, P, P]),
+    ("gila_reinsert_degree_one", ctypes.c_int, [P, PP, P, P]),
+    ("gila_layout_pruned_run_device", ctypes.c_int, [P, PP, P]),
+    ("gila_layout_pruned_run", ctypes.c_int, [P, PP, P, P]),
 ]
 
 
@@ -551,6 +561,97 @@ class Server:
     def close(self):
         if self.handle:
             gila_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# ------------------------------------------------------------------ pruning
+
+def gila_graph_set_repulsion_weights(g, weights) -> None:
+    """Per-vertex repulsion weights (float64[n]) or None to remove them."""
+    if weights is None:
+        _check(load().gila_graph_set_repulsion_weights(g, None))
+        return
+    w = _np(weights, np.float64)
+    _check(load().gila_graph_set_repulsion_weights(g, _ptr(w)))
+
+
+def gila_prune_degree_one(g) -> int:
+    out = P()
+    _check(load().gila_prune_degree_one(g, ctypes.byref(out)))
+    return out.value
+
+
+def gila_pruned_destroy(p) -> None:
+    load().gila_pruned_destroy(p)
+
+
+def gila_pruned_graph(p) -> int:
+    return load().gila_pruned_graph(p)
+
+
+def gila_pruned_info(p) -> dict:
+    k, r = I64(), I64()
+    _check(load().gila_pruned_info(p, ctypes.byref(k), ctypes.byref(r)))
+    return {"kept": k.value, "removed": r.value}
+
+
+def gila_pruned_export(p, n):
+    """(anchor, w, newid), each int32[n] over the original ids."""
+    a = np.empty(n, dtype=np.int32)
+    w = np.empty(n, dtype=np.int32)
+    i = np.empty(n, dtype=np.int32)
+    _check(load().gila_pruned_export(p, _ptr(a), _ptr(w), _ptr(i)))
+    return a, w, i
+
+
+def gila_pruned_gather(p, precision, pos_full, pos_pruned) -> None:
+    _check(load().gila_pruned_gather(p, int(precision), _dev_ptr(pos_full), _dev_ptr(pos_pruned)))
+
+
+def gila_reinsert_degree_one(p, prm, pos_pruned, pos_full) -> None:
+    _check(load().gila_reinsert_degree_one(p, ctypes.byref(prm), _dev_ptr(pos_pruned),
+                                           _dev_ptr(pos_full)))
+
+
+def gila_layout_pruned_run_device(p, prm, pos_full) -> None:
+    _check(load().gila_layout_pruned_run_device(p, ctypes.byref(prm), _dev_ptr(pos_full)))
+
+
+def gila_layout_pruned_run(p, prm, pos_in, pos_out=None) -> np.ndarray:
+    src = _np(pos_in, np.float64)
+    out = np.empty_like(src) if pos_out is None else pos_out
+    _check(load().gila_layout_pruned_run(p, ctypes.byref(prm), _ptr(src), _ptr(out)))
+    return out
+
+
+class Pruned:
+    """Owning wrapper of a gila_pruned made from a Graph (which must outlive it)."""
+
+    def __init__(self, graph: "Graph"):
+        self.graph = graph
+        self.handle = gila_prune_degree_one(graph.handle)
+        info = gila_pruned_info(self.handle)
+        self.kept, self.removed = info["kept"], info["removed"]
+
+    @property
+    def pruned_graph(self) -> int:
+        return gila_pruned_graph(self.handle)
+
+    def close(self):
+        if self.handle:
+            gila_pruned_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
