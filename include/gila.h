@@ -169,6 +169,14 @@ gila_status gila_khop_reset(gila_graph* g);
  * int32[nnz_khop] (ids, ascending per row). GILA_ESTATE if none are built. */
 gila_status gila_khop_export(const gila_graph* g, int64_t* krow_host, int32_t* kcol_host);
 
+/* Copy selected rows only (for lists too large for the host): counts_host
+ * int64[nsel] receives |N_v(k)| of each sel_host[i]; when cols_host is not
+ * NULL the rows follow back to back (int32, ascending each), at most
+ * cols_cap entries (GILA_EINVAL if the total is larger). GILA_ESTATE if no
+ * lists are built. Synchronous. */
+gila_status gila_khop_export_rows(const gila_graph* g, int64_t nsel, const int64_t* sel_host,
+                                  int64_t* counts_host, int32_t* cols_host, int64_t cols_cap);
+
 /* One synchronous iteration at temperature t (Sections 3.1, 4.5): every
  * F(u) is formed from pos_in_dev, then pos_out_dev[u] = pos_in_dev[u] +
  * F(u) min(1, t / |F(u)|). Builds the k-hop lists for prm->k first when

@@ -423,6 +423,38 @@ gila_status gila_khop_export(const gila_graph* g, int64_t* krow_host, int32_t* k
     return GILA_OK;
 }
 
+gila_status gila_khop_export_rows(const gila_graph* g, int64_t nsel, const int64_t* sel_host,
+                                  int64_t* counts_host, int32_t* cols_host, int64_t cols_cap)
+{
+    if (!g || nsel < 0 || (nsel > 0 && (!sel_host || !counts_host)))
+        return fail(GILA_EINVAL, "graph, selection or counts is NULL");
+    if (!g->krow || g->k_built == 0) return fail(GILA_ESTATE, "no k-hop lists are built");
+    GILA_CUDA(cudaSetDevice(g->device));
+    std::vector<int64_t> b((size_t)nsel), e((size_t)nsel);
+    for (int64_t i = 0; i < nsel; ++i) {
+        if (sel_host[i] < 0 || sel_host[i] >= g->n) return fail(GILA_EINVAL, "vertex out of range");
+        GILA_CUDA(cudaMemcpy(&b[(size_t)i], g->krow + sel_host[i], sizeof(int64_t),
+                             cudaMemcpyDeviceToHost));
+        GILA_CUDA(cudaMemcpy(&e[(size_t)i], g->krow + sel_host[i] + 1, sizeof(int64_t),
+                             cudaMemcpyDeviceToHost));
+    }
+    int64_t total = 0;
+    for (int64_t i = 0; i < nsel; ++i) {
+        counts_host[i] = e[(size_t)i] - b[(size_t)i];
+        total += counts_host[i];
+    }
+    if (!cols_host) return GILA_OK;
+    if (total > cols_cap) return fail(GILA_EINVAL, "cols_cap is smaller than the rows' total");
+    int64_t o = 0;
+    for (int64_t i = 0; i < nsel; ++i) {
+        if (counts_host[i] > 0)
+            GILA_CUDA(cudaMemcpy(cols_host + o, g->kcol + b[(size_t)i],
+                                 sizeof(int32_t) * (size_t)counts_host[i], cudaMemcpyDeviceToHost));
+        o += counts_host[i];
+    }
+    return GILA_OK;
+}
+
 gila_status gila_layout_step(gila_graph* g, const gila_params* prm, double t,
                              const void* pos_in_dev, void* pos_out_dev, void* disp_out_dev)
 {

@@ -411,6 +411,16 @@ gila_status exclusive_scan(const int64_t* in, int64_t n, int64_t* out, cudaStrea
     return GILA_OK;
 }
 
+// Offsets (begin, end) of the giant rows, gathered for the host.
+__global__ void giant_bounds_kernel(int64_t ng, const int32_t* __restrict__ giants,
+                                    const int64_t* __restrict__ krow, int64_t* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ng) return;
+    out[2 * i] = krow[giants[i]];
+    out[2 * i + 1] = krow[giants[i] + 1];
+}
+
 gila_status build_bins(gila_graph* g)
 {
     Bins& B = g->bins;
@@ -452,8 +462,11 @@ gila_status build_bins(gila_graph* g)
         B.cap_lists = std::max<size_t>(nlist, 1);
     }
     int32_t* d_giants = nullptr;
+    int64_t* d_gk = nullptr;
     s = dev_alloc(&d_giants, (size_t)std::max<int64_t>(tot[3], 1));
     if (s != GILA_OK) { cudaFree(d_bc); return s; }
+    s = dev_alloc(&d_gk, (size_t)std::max<int64_t>(2 * tot[3], 2));
+    if (s != GILA_OK) { cudaFree(d_bc); cudaFree(d_giants); return s; }
     if (nb > 0) {
         cudaMemcpyAsync(d_bc, boff.data(), sizeof(int) * nb * 4, cudaMemcpyHostToDevice, st);
         bin_scatter_kernel<<<(unsigned)nb, kBinThreads, 0, st>>>(n, g->krow, B.cfg, d_bc, B.lists,
@@ -463,19 +476,18 @@ gila_status build_bins(gila_graph* g)
     // chunk table of the giant rows, built on the host
     std::vector<int32_t> giants((size_t)tot[3]);
     std::vector<int64_t> gk((size_t)tot[3] * 2);
-    if (tot[3] > 0)
+    if (tot[3] > 0) {
+        giant_bounds_kernel<<<(unsigned)((tot[3] + 255) / 256), 256, 0, st>>>(tot[3], d_giants,
+                                                                             g->krow, d_gk);
+        count_launch();
         cudaMemcpyAsync(giants.data(), d_giants, sizeof(int32_t) * tot[3], cudaMemcpyDeviceToHost,
                         st);
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) { cudaFree(d_bc); cudaFree(d_giants); return cuda_fail(e, "bin_scatter"); }
-    for (int64_t i = 0; i < tot[3]; ++i) {
-        e = cudaMemcpyAsync(&gk[2 * i], g->krow + giants[i], 2 * sizeof(int64_t),
-                            cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) break;
+        cudaMemcpyAsync(gk.data(), d_gk, sizeof(int64_t) * 2 * tot[3], cudaMemcpyDeviceToHost, st);
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    e = cudaStreamSynchronize(st);
     cudaFree(d_bc);
     cudaFree(d_giants);
+    cudaFree(d_gk);
     if (e != cudaSuccess) return cuda_fail(e, "giant rows");
     std::vector<Chunk> chunks;
     for (int64_t i = 0; i < tot[3]; ++i) {

@@ -94,6 +94,7 @@ SIGNATURES = [
     ("gila_build_khop", ctypes.c_int, [P, I32, ctypes.POINTER(I64)]),
     ("gila_khop_reset", ctypes.c_int, [P]),
     ("gila_khop_export", ctypes.c_int, [P, P, P]),
+    ("gila_khop_export_rows", ctypes.c_int, [P, I64, P, P, P, I64]),
     ("gila_layout_step", ctypes.c_int, [P, PP, D, P, P, P]),
     ("gila_layout_run_device", ctypes.c_int, [P, PP, P]),
     ("gila_layout_run", ctypes.c_int, [P, PP, P, P, P]),
@@ -270,6 +271,17 @@ def gila_khop_export(g):
     kcol = np.zeros(max(info["nnz_khop"], 1), dtype=np.int32)
     _check(load().gila_khop_export(g, _ptr(krow), _ptr(kcol)))
     return krow, kcol[: info["nnz_khop"]]
+
+
+def gila_khop_export_rows(g, sel):
+    """Rows of the selected vertices: (counts int64[s], concatenated int32 rows)."""
+    sel = _np(sel, np.int64)
+    counts = np.zeros(max(len(sel), 1), dtype=np.int64)
+    _check(load().gila_khop_export_rows(g, len(sel), _ptr(sel), _ptr(counts), None, 0))
+    total = int(counts[: len(sel)].sum())
+    cols = np.zeros(max(total, 1), dtype=np.int32)
+    _check(load().gila_khop_export_rows(g, len(sel), _ptr(sel), _ptr(counts), _ptr(cols), total))
+    return counts[: len(sel)], cols[:total]
 
 
 def gila_layout_step(g, prm, t, pos_in, pos_out, disp_out=None) -> None:
