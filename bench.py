@@ -471,6 +471,9 @@ def run_serve(args, wl, ws, rank, local, count=48, emax=3e5):
         lat = []
         if dist is not None:
             dist.barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        l0 = G.gila_kernel_launches()
         with G.Server(budget, 16) as s:
             t0 = time.perf_counter()
             tickets = []
@@ -484,9 +487,12 @@ def run_serve(args, wl, ws, rank, local, count=48, emax=3e5):
                 lat.append(info["latency_ms"] / 1e3)
             makespan = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
             st = s.stats()
+        launches = G.gila_kernel_launches() - l0
+        clk = clocks.stop()
         lat = np.array(lat)
         plain_lat = np.array(plain_lat)
         runs.append({"arrival_rate_per_s": rate, "rate_vs_plain_capacity": mult,
+                     "gpu_launches": launches, "clocks": clk,
                      "server": {"layouts_per_s": ws * count / makespan,
                                 "p50_ms": float(np.percentile(lat, 50) * 1e3),
                                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
@@ -508,6 +514,7 @@ def run_serve(args, wl, ws, rank, local, count=48, emax=3e5):
         "config": {"workload": wl["desc"], "requests": count, "budget": budget,
                    "plain_capacity_layouts_per_s": capacity,
                    "mean_service_ms": float(service.mean() * 1e3), "runs": runs},
+        "gpu_launches": top["gpu_launches"], "clocks": top["clocks"],
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -617,6 +617,25 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
     return GILA_OK;
 }
 
+bool blocked_auto_applies(int64_t n, int64_t nnz_khop, size_t esz, const gila_tuning& tune)
+{
+    if (n == 0 || nnz_khop == 0 || tune.tiled == 0 || esz == 16) return tune.tiled == 1 && n > 0;
+    if (tune.tiled == 1) return true;
+    int64_t tv_max = kTileBudget / (int64_t)esz;
+    if (tune.tile_vertices > 0) tv_max = std::min<int64_t>(tv_max, tune.tile_vertices);
+    tv_max = std::max<int64_t>(2, tv_max & ~int64_t(1));
+    const int64_t nt = (n + tv_max - 1) / tv_max;
+    const int min_seg = tune.min_segment > 0 ? tune.min_segment : 48;
+    return nnz_khop >= kBlockedMinNnz && (double)nnz_khop / ((double)n * (double)nt) >= min_seg;
+}
+
+gila_status prepare_iteration(gila_graph* g, const gila_params* prm)
+{
+    if (prm->precision == GILA_FP64_ORDERED || g->n == 0 || g->wt64) return GILA_OK;
+    TilePlan& P = g->tplan[is_f64(prm->precision) ? 1 : 0];
+    return P.ready ? GILA_OK : plan_tiles(g, is_f64(prm->precision) ? 16 : 8, P);
+}
+
 gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, const void* pos_in,
                            void* pos_out, void* disp_out, bool* handled)
 {

@@ -172,6 +172,10 @@ void free_tile_plans(gila_graph* g);
 // blocked path (blocked.cu): *handled = false when the plain kernel must run
 gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, const void* pos_in,
                            void* pos_out, void* disp_out, bool* handled);
+// Whether automatic mode (or the tuning) puts a graph of these sizes on the
+// blocked path; and building its plan ahead of the first iteration.
+bool blocked_auto_applies(int64_t n, int64_t nnz_khop, size_t esz, const gila_tuning& tune);
+gila_status prepare_iteration(gila_graph* g, const gila_params* prm);
 // GILA_ECUDA (and clears the flag) when a blocked-path CTA gave up waiting
 // for its tile copy since the last call; synchronises st.
 gila_status blocked_tile_wait_failed(cudaStream_t st);

@@ -9,12 +9,14 @@
 //              uploads the placement. A job that can never fit fails with
 //              GILA_EBUDGET.
 //   runner     keeps every admitted job's placement and temperature resident
-//              on the device and advances all of them together: each round
-//              enqueues the next chunk of iterations of every job on the
-//              job's own stream (at most two chunks in flight per job), so
-//              the kernels of different jobs overlap on the GPU; finished
-//              jobs are copied back, their memory is returned and waiters
-//              are woken.
+//              on the device and advances them oldest first: each round
+//              enqueues the next chunk of iterations of every running job on
+//              the job's own stream (at most two chunks in flight per job),
+//              so the kernels of different jobs overlap on the GPU; a job
+//              that has not started joins while the running jobs' work per
+//              iteration is below what fills the GPU (large jobs run nearly
+//              alone, small ones side by side); finished jobs are copied
+//              back, their memory is returned and waiters are woken.
 // Requests arriving while others run are admitted as soon as memory and a
 // slot free up (continuous batching). A job runs exactly the kernels it
 // would run alone, so its result does not depend on the mix.
@@ -102,7 +104,8 @@ namespace {
 size_t pos_size(int precision) { return is_f64(precision) ? 16 : 8; }
 
 // Device bytes a job holds while it runs (upper estimate, exact list size).
-size_t job_bytes(int64_t n, int64_t nnz_adj, int64_t nnz_khop, int precision)
+size_t job_bytes(int64_t n, int64_t nnz_adj, int64_t nnz_khop, int precision,
+                 const gila_tuning& tune)
 {
     const size_t esz = pos_size(precision);
     size_t b = 0;
@@ -110,13 +113,21 @@ size_t job_bytes(int64_t n, int64_t nnz_adj, int64_t nnz_khop, int precision)
     b += 4 * (size_t)nnz_khop;                          // k-hop ids
     b += 12 * (size_t)n;                                // row classes, spare
     b += 2 * esz * (size_t)n + 16 * (size_t)n;          // placement buffers, staging
-    // blocked-path plan (worst case): the ids once more in block order, and
-    // per row and tile an offset, a length and a partial force
-    const int64_t tv = (200 * 1024) / (int64_t)esz;
-    const int64_t nt = (n + tv - 1) / std::max<int64_t>(tv, 1);
-    b += 4 * (size_t)nnz_khop + (16 + 2 * esz) * (size_t)n * (size_t)nt;
+    if (blocked_auto_applies(n, nnz_khop, esz, tune)) {
+        // blocked-path plan: the ids once more in block order, and per row
+        // and tile an offset, a length and a partial force
+        const int64_t tv = (200 * 1024) / (int64_t)esz;
+        const int64_t nt = (n + tv - 1) / std::max<int64_t>(tv, 1);
+        b += 4 * (size_t)nnz_khop + (16 + 2 * esz) * (size_t)n * (size_t)nt + (1 << 16);
+    }
     return b + ((size_t)1 << 20);
 }
+
+// Per-iteration work (k-hop plus adjacency entries) of the jobs already
+// running beyond which a job that has not started waits: about what keeps
+// the GPU busy on its own (measured: a Barabasi-Albert graph with 1.4e7
+// k-hop entries already runs at 70% of the largest graphs' pair rate).
+constexpr double kSaturationPairs = 2e7;
 
 void finish_job(gila_server* s, const JobPtr& j, gila_status st, const std::string& err)
 {
@@ -180,7 +191,7 @@ gila_status admit_job(gila_server* s, const JobPtr& j, std::string* err)
         *err = gila_last_error();
         return st;
     }
-    const size_t need = job_bytes(j->n, j->g->nnz_adj, nnz, j->prm.precision);
+    const size_t need = job_bytes(j->n, j->g->nnz_adj, nnz, j->prm.precision, j->g->tune);
     if (need > s->budget) {
         *err = "job needs " + std::to_string(need) + " device bytes, budget is " +
                std::to_string(s->budget);
@@ -211,6 +222,11 @@ gila_status admit_job(gila_server* s, const JobPtr& j, std::string* err)
     j->g->k_built = j->prm.k;
     j->nnz_khop = nnz;
     release_khop_scratch(j->g);
+    // plan the blocked path here, not on the runner thread
+    if ((st = prepare_iteration(j->g, &j->prm)) != GILA_OK) {
+        *err = gila_last_error();
+        return st;
+    }
     const size_t n = (size_t)j->n;
     const size_t esz = pos_size(j->prm.precision);
     if (n > 0) {
@@ -344,6 +360,9 @@ void runner_loop(gila_server* s)
             }
         }
         bool progressed = false;
+        // oldest first: a job that has not started joins only while the
+        // running jobs leave the GPU short of work
+        double running_work = 0.0;
         for (size_t i = 0; i < active.size();) {
             JobPtr j = active[i];
             std::string err;
@@ -354,6 +373,12 @@ void runner_loop(gila_server* s)
                 active.erase(active.begin() + i);
                 continue;
             }
+            const bool started = j->chunks_issued > 0;
+            if (!started && running_work >= kSaturationPairs) {
+                ++i;
+                continue;
+            }
+            if (!j->download_issued) running_work += (double)(j->nnz_khop + j->g->nnz_adj);
             if (advance(s, *j, &err, &st)) progressed = true;
             if (st != GILA_OK) {
                 free_job_device(s, j);
