@@ -83,6 +83,10 @@ def _load():
         lib.oracle_pruned_csr.argtypes = [I64, P, P, P, P, P]
         lib.oracle_pruned_csr.restype = I64
         lib.oracle_reinsert.argtypes = [I64, P, P, P, P, P, P, P, P, D, P]
+        lib.oracle_components.argtypes = [I64, P, P, P]
+        lib.oracle_components.restype = ctypes.c_int32
+        lib.oracle_pack.argtypes = [ctypes.c_int32, P, P, D, P]
+        lib.oracle_pack.restype = I
         _lib = lib
         return lib
 
@@ -283,3 +287,62 @@ def pipeline(n, row_ptr, col_idx, pos0, k, iters, d=1.0, p=2, q=1, schedule=SCHE
     krow, kcol = khop(kept, prow, pcol, k)
     ppos = run(kept, prow, pcol, krow, kcol, ppos0, iters, d, p, q, schedule, t0, wt=wt)
     return reinsert(n, row_ptr, col_idx, newid, anchor, w, prow, pcol, ppos, d)
+
+
+def components(n, row_ptr, col_idx):
+    """Connected components (Section 4.6): (label int32[n], count), numbered
+    in the order of their smallest vertex id."""
+    lib = _load()
+    row, col = _csr(n, row_ptr, col_idx)
+    label = np.zeros(max(n, 1), dtype=np.int32)
+    count = lib.oracle_components(n, _p(row), _p(col), _p(label))
+    if count < 0:
+        raise MemoryError("oracle_components")
+    return label[:n], int(count)
+
+
+def pack(bbox, size, gap):
+    """Shelf packing of component boxes (float64[c, 4]: xmin, ymin, xmax,
+    ymax) by decreasing size: the translations float64[c, 2]."""
+    lib = _load()
+    bb = np.ascontiguousarray(bbox, dtype=np.float64).reshape(-1, 4)
+    sz = np.ascontiguousarray(size, dtype=np.int64)
+    c = bb.shape[0]
+    off = np.zeros((max(c, 1), 2), dtype=np.float64)
+    if lib.oracle_pack(c, _p(bb), _p(sz), float(gap), _p(off)) != 0:
+        raise MemoryError("oracle_pack")
+    return off[:c]
+
+
+def components_layout(n, row_ptr, col_idx, pos0, k, iters, d=1.0, p=2, q=1,
+                      schedule=SCHED_LINEAR, t0=0.0, gap=0.0):
+    """Every connected component laid out on its own (its own default initial
+    temperature from its own n and initial frame, Section 5.1), then the
+    drawings packed into rows (Section 4.6). gap <= 0 means d. Returns the
+    full final placement."""
+    row, col = _csr(n, row_ptr, col_idx)
+    P0 = _pos(pos0, n)
+    label, count = components(n, row, col)
+    out = np.zeros((n, 2), dtype=np.float64)
+    bbox = np.zeros((count, 4), dtype=np.float64)
+    size = np.bincount(label, minlength=count).astype(np.int64)
+    order = np.argsort(label, kind="stable")  # vertices by component, ascending ids
+    starts = np.concatenate([[0], np.cumsum(size)])
+    local = np.zeros(n, dtype=np.int64)
+    for c in range(count):
+        vs = order[starts[c]:starts[c + 1]]
+        local[vs] = np.arange(len(vs))
+    for c in range(count):
+        vs = order[starts[c]:starts[c + 1]]
+        # the component's CSR in local ids (rows stay ascending)
+        lens = row[vs + 1] - row[vs]
+        crow = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        ccol = local[np.concatenate([col[row[v]:row[v + 1]] for v in vs])] \
+            if crow[-1] > 0 else np.zeros(0, dtype=np.int64)
+        ccol = ccol.astype(np.int32)
+        krow, kcol = khop(len(vs), crow, ccol, k)
+        res = run(len(vs), crow, ccol, krow, kcol, P0[vs], iters, d, p, q, schedule, t0)
+        out[vs] = res
+        bbox[c] = [res[:, 0].min(), res[:, 1].min(), res[:, 0].max(), res[:, 1].max()]
+    off = pack(bbox, size, d if gap <= 0 else gap)
+    return out + off[label]

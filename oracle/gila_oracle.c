@@ -552,3 +552,92 @@ void oracle_reinsert(int64_t n, const int64_t *row, const int32_t *col, const in
         }
     }
 }
+
+/*
+ * Connected components (Section 4.6: the pipeline runs on every connected
+ * component on its own). label[v] = index of v's component, components
+ * numbered in the order of their smallest vertex id (a breadth-first search
+ * from each vertex not yet reached, in ascending order). Returns the count.
+ */
+int32_t oracle_components(int64_t n, const int64_t *row, const int32_t *col, int32_t *label)
+{
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!queue) return -1;
+    for (int64_t v = 0; v < n; ++v) label[v] = -1;
+    int32_t count = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        if (label[s] >= 0) continue;
+        int64_t head = 0, tail = 0;
+        queue[tail++] = (int32_t)s;
+        label[s] = count;
+        while (head < tail) {
+            int32_t u = queue[head++];
+            for (int64_t j = row[u]; j < row[u + 1]; ++j) {
+                int32_t w = col[j];
+                if (label[w] < 0) {
+                    label[w] = count;
+                    queue[tail++] = w;
+                }
+            }
+        }
+        ++count;
+    }
+    free(queue);
+    return count;
+}
+
+/*
+ * Arrangement of the component drawings "in a matrix" (Section 4.6), read as
+ * shelf packing: boxes (bbox[4c..4c+3] = xmin, ymin, xmax, ymax of component
+ * c) are taken by decreasing vertex count (size[c]), ties by component index;
+ * rows are filled left to right with `gap` between boxes, a new row starting
+ * `gap` above the tallest box of the previous one when the next box would
+ * pass the row width W = max(widest box, sqrt(sum over boxes of
+ * (width + gap)(height + gap))). offset[2c], offset[2c+1] receive the
+ * translation that moves box c's lower-left corner to its place; the first
+ * box sits at the origin.
+ */
+static const int64_t *pack_size_key;
+static int pack_cmp(const void *a, const void *b)
+{
+    int32_t i = *(const int32_t *)a, j = *(const int32_t *)b;
+    if (pack_size_key[i] != pack_size_key[j]) return pack_size_key[i] > pack_size_key[j] ? -1 : 1;
+    return (i > j) - (i < j);
+}
+
+int oracle_pack(int32_t count, const double *bbox, const int64_t *size, double gap,
+                double *offset)
+{
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(count > 0 ? count : 1));
+    if (!order) return -1;
+    double area = 0.0, widest = 0.0;
+    for (int32_t c = 0; c < count; ++c) {
+        order[c] = c;
+        double w = bbox[4 * c + 2] - bbox[4 * c], h = bbox[4 * c + 3] - bbox[4 * c + 1];
+        area += (w + gap) * (h + gap);
+        if (w > widest) widest = w;
+    }
+    pack_size_key = size;
+    qsort(order, (size_t)count, sizeof(int32_t), pack_cmp);
+    double W = sqrt(area);
+    if (widest > W) W = widest;
+    double x = 0.0, y = 0.0, row_h = 0.0;
+    int in_row = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        int32_t c = order[i];
+        double w = bbox[4 * c + 2] - bbox[4 * c], h = bbox[4 * c + 3] - bbox[4 * c + 1];
+        if (in_row > 0 && x + w > W) {
+            y += row_h + gap;
+            x = 0.0;
+            row_h = 0.0;
+            in_row = 0;
+        }
+        offset[2 * c] = x - bbox[4 * c];
+        offset[2 * c + 1] = y - bbox[4 * c + 1];
+        x += w + gap;
+        if (h > row_h) row_h = h;
+        ++in_row;
+    }
+    free(order);
+    return 0;
+}
