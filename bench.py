@@ -55,7 +55,7 @@ WORKLOADS = {
                            "grids, G(n, 4/(n-1))), k=2, 200 iterations each, one persistent launch"),
     "serve": dict(iters=300, precision="fp32",
                   desc="Poisson stream of Barabasi-Albert layout requests, E log-uniform in "
-                       "[1e3, 3e5], k in {2, 3}, 300 iterations, FP32"),
+                       "[1e3, 1e6], k in {2, 3}, 300 iterations, FP32"),
 }
 PREC = {"fp32": 0, "fp64": 1, "fp32c": 2}
 
@@ -428,7 +428,7 @@ def run_batch(args, wl, ws, rank, local):
     return 0
 
 
-def run_serve(args, wl, ws, rank, local, count=48, emax=3e5):
+def run_serve(args, wl, ws, rank, local, count=48, emax=1e6):
     """Serving stream: layout requests arriving as a Poisson process, served
     by the continuous-batching server, against one-at-a-time service of the
     same requests (a FIFO single server fed by the same arrivals)."""

@@ -389,6 +389,36 @@ gila_status gila_layout_pruned_run_device(gila_pruned* p, const gila_params* prm
 gila_status gila_layout_pruned_run(gila_pruned* p, const gila_params* prm,
                                    const double* pos_in_host, double* pos_out_host);
 
+/* ------------------------------------------------------------------------
+ * Per-component layout (Section 4.6: the pipeline is applied to every
+ * connected component on its own and the drawings are arranged without
+ * overlap; Section 5.1: a component's maximum displacement follows its own
+ * n and initial frame).
+ * ------------------------------------------------------------------------ */
+
+/* Connected components on the device: label_host int32[n] receives the
+ * index of each vertex's component, components numbered in the order of
+ * their smallest vertex id; *count (may be NULL) their number. Synchronous. */
+gila_status gila_graph_components(gila_graph* g, int32_t* label_host, int32_t* count);
+
+/* Lay out every connected component on its own with prm (with prm->t0 <= 0
+ * each component takes its own default initial temperature: 0.1 sqrt(n_c)
+ * linear, sqrt(n_c d / a_c) geometric with a_c the height/width of its own
+ * initial frame): components of up to 4096 vertices together in one
+ * persistent batch launch, larger ones one by one on the single-graph
+ * kernels, isolated vertices unchanged. The drawings are then packed into
+ * rows: boxes by decreasing vertex count (ties by component index), left to
+ * right with `gap` between boxes (gap <= 0: prm->d), a new row `gap` above
+ * the tallest box of the last one when the next box would pass the width
+ * W = max(widest box, sqrt(sum over boxes of (width + gap)(height + gap)));
+ * the first box's lower-left corner sits at the origin. The paper says only
+ * that the drawings are "arranged in a matrix" to avoid overlap; the row
+ * packing is this library's reading. Host placements double[2n];
+ * *count_out (may be NULL) receives the number of components. */
+gila_status gila_layout_components_run(gila_graph* g, const gila_params* prm, double gap,
+                                       const double* pos_in_host, double* pos_out_host,
+                                       int32_t* count_out);
+
 /* Temperature of iteration i under prm (t0 = resolved initial temperature). */
 double gila_temperature(const gila_params* prm, double t0, int32_t i);
 

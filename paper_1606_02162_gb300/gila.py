@@ -127,6 +127,8 @@ SIGNATURES = [
     ("gila_reinsert_degree_one", ctypes.c_int, [P, PP, P, P]),
     ("gila_layout_pruned_run_device", ctypes.c_int, [P, PP, P]),
     ("gila_layout_pruned_run", ctypes.c_int, [P, PP, P, P]),
+    ("gila_graph_components", ctypes.c_int, [P, P, ctypes.POINTER(I32)]),
+    ("gila_layout_components_run", ctypes.c_int, [P, PP, D, P, P, ctypes.POINTER(I32)]),
 ]
 
 
@@ -677,3 +679,23 @@ class Pruned:
 
     def __exit__(self, *a):
         self.close()
+
+
+# --------------------------------------------------------------- components
+
+def gila_graph_components(g, n):
+    """(label int32[n], count) of the connected components."""
+    label = np.zeros(max(n, 1), dtype=np.int32)
+    c = I32()
+    _check(load().gila_graph_components(g, _ptr(label), ctypes.byref(c)))
+    return label[:n], c.value
+
+
+def gila_layout_components_run(g, prm, pos_in, gap=0.0, pos_out=None):
+    """Per-component layout and packing: (placement float64[n, 2], count)."""
+    src = _np(pos_in, np.float64)
+    out = np.empty_like(src) if pos_out is None else pos_out
+    c = I32()
+    _check(load().gila_layout_components_run(g, ctypes.byref(prm), float(gap), _ptr(src),
+                                             _ptr(out), ctypes.byref(c)))
+    return out, c.value
