@@ -179,57 +179,64 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
             acc = Acc<T, COMP>();
         };
         bool done = false;
-        // 16-byte id loads run three steps ahead of the arithmetic
+        f.xu = xr.x;  // the row's own position, set again only when the row changes
+        f.yu = xr.y;
+        // 16-byte id loads run four steps (512 entries) ahead: each of the
+        // four unrolled steps below consumes its own ring register and
+        // refills it, so the ring needs no register moves
         auto load_step = [&](int32_t base) {
             const int32_t p0 = base + 4 * lane;
-            return (base < b && p0 < b) ? ld_ids4(ids4 + (p0 >> 2)) : make_uint4(0, 0, 0, 0);
+            return (p0 < b) ? ld_ids4(ids4 + (p0 >> 2)) : make_uint4(0, 0, 0, 0);
         };
-        uint4 c0 = load_step(a), c1 = load_step(a + 128), c2 = load_step(a + 256);
-        for (int32_t base = a; base < b && !done; base += 128) {
-            const uint4 c3 = load_step(base + 384);
-            const int32_t p0 = base + 4 * lane;
-            const int32_t lim = (base + 128 < b) ? base + 128 : b;
-            const uint32_t ids[4] = {c0.x, c0.y, c0.z, c0.w};
-            c0 = c1;
-            c1 = c2;
-            c2 = c3;
-            if (re > lim) {  // the whole step lies in row ri (warp-uniform)
-                f.xu = xr.x;
-                f.yu = xr.y;
-                if (p0 + 3 < b) {
-                    f(ids[0], acc);
-                    f(ids[1], acc);
-                    f(ids[2], acc);
-                    f(ids[3], acc);
-                } else {
+        uint4 ring[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (p0 + q < b) f(ids[q], acc);
-                }
-                continue;
-            }
-            // rows ri, ri + 1, ... end inside this step
-            for (;;) {
-                f.xu = xr.x;
-                f.yu = xr.y;
+        for (int st = 0; st < 4; ++st) ring[st] = load_step(a + 128 * st);
+        for (int32_t base = a; base < b && !done; base += 512) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int32_t p = p0 + q;
-                    if (p >= rs && p < re && p < b) f(ids[q], acc);
+            for (int st = 0; st < 4; ++st) {
+                const int32_t sb = base + 128 * st;
+                if (sb >= b || done) break;  // warp-uniform
+                const uint4 c = ring[st];
+                ring[st] = load_step(sb + 512);
+                const uint32_t ids[4] = {c.x, c.y, c.z, c.w};
+                const int32_t p0 = sb + 4 * lane;
+                const int32_t lim = (sb + 128 < b) ? sb + 128 : b;
+                if (re > lim) {  // the whole step lies in row ri (warp-uniform)
+                    if (sb + 128 <= b) {
+                        f(ids[0], acc);
+                        f(ids[1], acc);
+                        f(ids[2], acc);
+                        f(ids[3], acc);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (p0 + q < b) f(ids[q], acc);
+                    }
+                    continue;
                 }
-                if (re > lim) break;  // this row goes on in the next step
-                finalize(rs < a, ri);
-                const int prev = ri;
-                ++ri;
-                while (ri < nrows && D[ri + 1] == D[ri]) ++ri;  // empty rows stay zero
-                if (ri >= nrows || D[ri] >= b) {
-                    done = true;
-                    break;
+                // rows ri, ri + 1, ... end inside this step
+                for (;;) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int32_t p = p0 + q;
+                        if (p >= rs && p < re && p < b) f(ids[q], acc);
+                    }
+                    if (re > lim) break;  // this row goes on in the next step
+                    finalize(rs < a, ri);
+                    const int prev = ri;
+                    ++ri;
+                    while (ri < nrows && D[ri + 1] == D[ri]) ++ri;  // empty rows stay zero
+                    if (ri >= nrows || D[ri] >= b) {
+                        done = true;
+                        break;
+                    }
+                    rs = D[ri];
+                    re = D[ri + 1];
+                    xr = (ri == prev + 1) ? xn : pos[u0 + ri];
+                    xn = pos[u0 + (ri + 1 < nrows ? ri + 1 : ri)];
+                    f.xu = xr.x;
+                    f.yu = xr.y;
                 }
-                rs = D[ri];
-                re = D[ri + 1];
-                xr = (ri == prev + 1) ? xn : pos[u0 + ri];
-                xn = pos[u0 + (ri + 1 < nrows ? ri + 1 : ri)];
             }
         }
         if (!done && ri < nrows && re > b) {
