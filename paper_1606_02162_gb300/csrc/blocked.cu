@@ -203,10 +203,21 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                 const int32_t lim = (sb + 128 < b) ? sb + 128 : b;
                 if (re > lim) {  // the whole step lies in row ri (warp-uniform)
                     if (sb + 128 <= b) {
-                        f(ids[0], acc);
-                        f(ids[1], acc);
-                        f(ids[2], acc);
-                        f(ids[3], acc);
+                        if (COMP) {
+                            // compensated mode: the step's four terms summed
+                            // plainly, the partial added with its error term
+                            Acc<T, false> s4;
+                            f(ids[0], s4);
+                            f(ids[1], s4);
+                            f(ids[2], s4);
+                            f(ids[3], s4);
+                            acc.merge(s4.sx, s4.sy, T(0), T(0));
+                        } else {
+                            f(ids[0], acc);
+                            f(ids[1], acc);
+                            f(ids[2], acc);
+                            f(ids[3], acc);
+                        }
                     } else {
 #pragma unroll
                         for (int q = 0; q < 4; ++q)

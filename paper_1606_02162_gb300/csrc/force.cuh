@@ -152,7 +152,8 @@ struct Rep {
     int q;
     const T* __restrict__ wt = nullptr;
 
-    __device__ __forceinline__ void operator()(uint32_t v, Acc<T, COMP>& a) const
+    template <bool C = COMP>
+    __device__ __forceinline__ void operator()(uint32_t v, Acc<T, C>& a) const
     {
         const P2 pv = src(v);
         const T dx = xu - pv.x, dy = yu - pv.y;
