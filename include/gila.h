@@ -111,6 +111,8 @@ typedef struct gila_tuning {
     int32_t warp_max;      /* ... rows <= this use one warp (8192) */
     int32_t block_max;     /* ... rows <= this use one block (65536); longer rows are chunked */
     int32_t chunk;         /* entries per chunk of a chunked row (32768) */
+    int32_t ctas_per_sm;   /* blocked path: row ranges per tile chosen so that the grid holds
+                              about this many CTAs per SM (4; 8 from 2e9 k-hop entries) */
 } gila_tuning;
 
 typedef struct gila_graph gila_graph;

@@ -344,7 +344,7 @@ gila_status gila_graph_tune(gila_graph* g, const gila_tuning* t)
     if (!g || !t) return fail(GILA_EINVAL, "graph or tuning is NULL");
     if (t->tiled < -1 || t->tiled > 1) return fail(GILA_EINVAL, "tiled must be -1, 0 or 1");
     if (t->tile_vertices < 0 || t->min_segment < 0 || t->small_max < 0 || t->warp_max < 0 ||
-        t->block_max < 0 || t->chunk < 0)
+        t->block_max < 0 || t->chunk < 0 || t->ctas_per_sm < 0)
         return fail(GILA_EINVAL, "tuning values must be >= 0");
     BinConfig c;  // defaults
     if (t->small_max) c.small_max = t->small_max;
@@ -369,6 +369,8 @@ gila_status gila_graph_get_tuning(const gila_graph* g, gila_tuning* out)
     if (!g || !out) return fail(GILA_EINVAL, "graph or out is NULL");
     *out = g->tune;
     out->min_segment = g->tune.min_segment > 0 ? g->tune.min_segment : 48;
+    out->ctas_per_sm = g->tune.ctas_per_sm > 0 ? g->tune.ctas_per_sm
+                                               : (g->nnz_khop >= 2000000000LL ? 8 : 4);
     out->small_max = g->bins.cfg.small_max;
     out->warp_max = g->bins.cfg.warp_max;
     out->block_max = g->bins.cfg.block_max;

@@ -559,7 +559,13 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
         total += c;
     }
     const int sms = sm_count(g->device);
-    int64_t nr_target = std::max<int64_t>((4 * (int64_t)sms + nt - 1) / nt, (n + kMaxRows - 1) / kMaxRows);
+    // default CTAs per SM: 4, or 8 for lists of 2e9 entries and more, where
+    // a CTA streams tens of MB and the end of the grid waits on the slowest
+    // (measured: Barabasi-Albert 2.4e8 entries best at 4, Chung-Lu 1.1e10 at 8)
+    const int64_t per_sm = g->tune.ctas_per_sm > 0 ? g->tune.ctas_per_sm
+                                                   : (g->nnz_khop >= 2000000000LL ? 8 : 4);
+    int64_t nr_target =
+        std::max<int64_t>((per_sm * (int64_t)sms + nt - 1) / nt, (n + kMaxRows - 1) / kMaxRows);
     nr_target = std::min<int64_t>(nr_target, n);
     std::vector<int32_t> rs;
     rs.push_back(0);
