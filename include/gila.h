@@ -102,7 +102,9 @@ typedef struct gila_metrics {
  * FP32 sums (different summation trees). Zero fields keep the defaults. */
 typedef struct gila_tuning {
     int32_t tiled;         /* -1 automatic (default), 0 never, 1 always: stage positions in
-                              shared-memory tiles instead of gathering them through L2 */
+                              shared-memory tiles instead of gathering them through L2 (with
+                              1, graphs whose row ranges touch narrow id windows get one
+                              window per range, read in place) */
     int32_t tile_vertices; /* positions per tile; 0 = as many as fit in 200 KiB */
     int32_t min_segment;   /* automatic mode tiles FP32 placements with at least 10^8 k-hop
                               entries when nnz_khop / (n * tiles) >= this (48); FP64 only

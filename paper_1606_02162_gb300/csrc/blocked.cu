@@ -31,7 +31,7 @@ constexpr int kSmemCap = 227 * 1024;
 constexpr int kMaxRows = 4096;  // rows per range (directory in shared memory)
 constexpr int kTileBudget = kSmemCap - (kMaxRows + 1) * 4 - 4096;
 constexpr uint32_t kBulkChunk = 32768;      // bytes per bulk copy instruction
-constexpr int64_t kBlockedMinNnz = 100000000;  // automatic mode: k-hop entries needed
+constexpr int64_t kBlockedMinNnz = 100000000;  // automatic mode: k-hop entries needed (tiles)
 constexpr uint32_t kWaitPolls = 1u << 24;   // bound on mbarrier polls (far above any copy)
 
 // Set when a CTA gave up waiting for its tile copy (the launch's partials
@@ -48,6 +48,7 @@ struct BlockedArgs {
     int q;
     const void* pos;
     void* part;                // nt n cells of 4 T: (sx, sy, cx, cy) without the factor d^2
+    const int64_t* wtile;      // window mode: first id and length of range r's tile, else null
 };
 
 template <class T, bool COMP>
@@ -98,8 +99,14 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
     // a block holds at most kMaxRows segments of at most tv entries: < 2^31
     const int32_t L = (int32_t)A.blk[2 * (int64_t)blockIdx.x + 1];
     const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos);
-    const int64_t tb = (int64_t)j * A.tv;
-    const int64_t tn = (A.n - tb < A.tv) ? A.n - tb : (int64_t)A.tv;
+    int64_t tb, tn;
+    if (A.wtile) {  // window mode: this range's own window of ids (first id even)
+        tb = A.wtile[2 * r];
+        tn = A.wtile[2 * r + 1];
+    } else {
+        tb = (int64_t)j * A.tv;
+        tn = (A.n - tb < A.tv) ? A.n - tb : (int64_t)A.tv;
+    }
     if (threadIdx.x == 0) {
         // tile j by the bulk-copy engine (tv is even and the placement is
         // 16-byte aligned, so the source is too); an odd float2 tail by hand
@@ -201,7 +208,7 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                 const uint32_t ids[4] = {c.x, c.y, c.z, c.w};
                 const int32_t p0 = sb + 4 * lane;
                 const int32_t lim = (sb + 128 < b) ? sb + 128 : b;
-                if (re > lim) {  // the whole step lies in row ri (warp-uniform)
+                if (re > lim && rs <= sb) {  // the whole step lies in row ri (warp-uniform)
                     if (sb + 128 <= b) {
                         if (COMP) {
                             // compensated mode: the step's four terms summed
@@ -410,6 +417,101 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(const CombineA
     if (live && gl == 0) finish_vertex<T, COMP>(A, u, pu.x, pu.y, rep, at);
 }
 
+// Window mode: one CTA per row range with the range's window of positions in
+// shared memory. Every row lies wholly in its range's window (attraction
+// too: the neighbours of u are in N_u(k)), so groups of G lanes form whole
+// rows, reduce them by shuffles and apply the capped move at once: no tile
+// partials and no second kernel. Groups advance together through the range
+// (warp-uniform trip counts) so the shuffles see whole warps.
+struct WindowArgs {
+    int32_t tv;                 // positions the shared-memory window holds
+    const int64_t* krow;
+    const uint32_t* kcol;
+    const int64_t* row;
+    const int32_t* col;
+    const int64_t* wtile;       // 2 nr: first id and length of range r's window
+    const int32_t* range_start;
+    int64_t n;
+    double d, t;
+    int p, q;
+    const void* pos_in;
+    void* pos_out;
+    void* disp_out;
+};
+
+template <class T, int MODEL, bool COMP, int G>
+__global__ void __launch_bounds__(kBThreads, 1) window_kernel(const WindowArgs A)
+{
+    using P2 = typename V2<T>::type;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    P2* tile = reinterpret_cast<P2*>(smem_raw);
+    __shared__ __align__(8) uint64_t tile_bar;
+    __shared__ int tile_ok;
+    const int r = blockIdx.x;
+    const int64_t u0 = A.range_start[r], u1 = A.range_start[r + 1];
+    const int64_t tb = A.wtile[2 * r], tn = A.wtile[2 * r + 1];
+    // the range's k-hop and adjacency row offsets, staged beside the window
+    int64_t* KR = reinterpret_cast<int64_t*>(smem_raw + (size_t)A.tv * sizeof(P2));
+    int64_t* AR = KR + (kMaxRows + 1);
+    for (int64_t i = threadIdx.x; i <= u1 - u0; i += kBThreads) {
+        KR[i] = A.krow[u0 + i];
+        AR[i] = A.row[u0 + i];
+    }
+    const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos_in);
+    if (threadIdx.x == 0) {
+        // the window by the bulk-copy engine (first id even, placement
+        // 16-byte aligned); an odd float2 tail by hand
+        const uint32_t bytes = (uint32_t)(((size_t)tn * sizeof(P2)) & ~size_t(15));
+        mbar_init(&tile_bar, 1);
+        mbar_arrive_expect_tx(&tile_bar, bytes);
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(pos + tb);
+        for (uint32_t o = 0; o < bytes; o += kBulkChunk)
+            bulk_g2s(smem_raw + o, src + o, (bytes - o < kBulkChunk) ? bytes - o : kBulkChunk,
+                     &tile_bar);
+        if ((size_t)tn * sizeof(P2) != bytes) tile[tn - 1] = pos[tb + tn - 1];
+        bool ok = mbar_wait(&tile_bar, 0, kWaitPolls);
+        if (!ok) {
+            atomicExch(&g_tile_wait_failed, 1);
+            mbar_wait(&tile_bar, 0, kWaitPolls);
+        }
+        tile_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!tile_ok) return;
+    mbar_wait(&tile_bar, 0, kWaitPolls);
+    Rep<T, MODEL, COMP, kSrcShared> rep;
+    rep.src.set_shared(tile, (uint32_t)tb);
+    rep.d2 = (T)(A.d * A.d);
+    rep.q = A.q;
+    Att<T, MODEL, COMP, kSrcShared> att;
+    att.src.set_shared(tile, (uint32_t)tb);
+    att.inv_d = (T)(1.0 / A.d);
+    att.p = A.p;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane & (G - 1);
+    constexpr int kGroups = kBThreads / G, kPerWarp = 32 / G;
+    for (int64_t ub = u0 + (int64_t)warp * kPerWarp; ub < u1; ub += kGroups) {
+        const int64_t u = ub + lane / G;
+        const bool live = u < u1;
+        Acc<T, COMP> a;
+        P2 pu;
+        pu.x = T(0);
+        pu.y = T(0);
+        if (live) {
+            pu = pos[u];
+            rep.xu = pu.x;
+            rep.yu = pu.y;
+            const int64_t i = u - u0;
+            row_sum(A.kcol, KR[i], KR[i + 1], gl, G, rep, a);
+            att.xu = pu.x;
+            att.yu = pu.y;
+            row_sum_rel(reinterpret_cast<const uint32_t*>(A.col), AR[i], AR[i + 1], gl, G, att, a);
+        }
+        a.group_reduce(G);
+        if (live && gl == 0) apply_move<T>(A.t, A.pos_out, A.disp_out, u, pu.x, pu.y, a.fx(), a.fy());
+    }
+}
+
 // Length of row u's segment in tile j (binary search on the sorted row).
 __device__ __forceinline__ void seg_bounds(const int64_t* __restrict__ krow,
                                            const uint32_t* __restrict__ kcol, int64_t u, int j,
@@ -452,6 +554,32 @@ __global__ void block_copy_kernel(int64_t n, const int64_t* __restrict__ krow,
     seg_bounds(krow, kcol, i % n, (int)(i / n), nt, tv, &lo, &hi);
     uint32_t* dst = tk + toff[i];
     for (int64_t e = lo + lane; e < hi; e += 32) dst[e - lo] = kcol[e];
+}
+
+template <class T, int MODEL, bool COMP, int G>
+cudaError_t launch_window_g(const WindowArgs& W, int grid, size_t smem, cudaStream_t st,
+                            int device)
+{
+    static uint64_t configured = 0;  // one bit per device
+    const uint64_t bit = 1ull << (device & 63);
+    if (!(configured & bit)) {
+        cudaError_t e = cudaFuncSetAttribute(window_kernel<T, MODEL, COMP, G>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kSmemCap - 4096);
+        if (e != cudaSuccess) return e;
+        configured |= bit;
+    }
+    window_kernel<T, MODEL, COMP, G><<<grid, kBThreads, smem, st>>>(W);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <class T, int MODEL, bool COMP>
+cudaError_t launch_window(const WindowArgs& W, int grid, size_t smem, cudaStream_t st, int device,
+                          bool wide)
+{
+    return wide ? launch_window_g<T, MODEL, COMP, 32>(W, grid, smem, st, device)
+                : launch_window_g<T, MODEL, COMP, 8>(W, grid, smem, st, device);
 }
 
 template <class T, int MODEL, bool COMP>
@@ -504,6 +632,8 @@ void free_tile_plans(gila_graph* g)
 {
     for (TilePlan& P : g->tplan) {
         cudaFree(P.hubs);
+        cudaFree(P.wtile);
+        cudaFree(P.rowspan);
         cudaFree(P.range_start);
         cudaFree(P.blk);
         cudaFree(P.toff);
@@ -514,12 +644,164 @@ void free_tile_plans(gila_graph* g)
     }
 }
 
+// First and last id of every k-hop row (rows are sorted); INT32_MAX and -1
+// for empty rows.
+__global__ void rowspan_kernel(int64_t n, const int64_t* __restrict__ krow,
+                               const uint32_t* __restrict__ kcol, int32_t* __restrict__ span)
+{
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const int64_t b = krow[u], e = krow[u + 1];
+    span[2 * u] = b < e ? (int32_t)kcol[b] : INT32_MAX;
+    span[2 * u + 1] = b < e ? (int32_t)kcol[e - 1] : -1;
+}
+
+// Row ranges of about equal cost (entries + a per-row term), at most
+// kMaxRows rows each: rs[r] .. rs[r + 1].
+std::vector<int32_t> partition_rows(const std::vector<int64_t>& cost, int64_t total,
+                                    int64_t nr_target)
+{
+    const int64_t n = (int64_t)cost.size();
+    std::vector<int32_t> rs;
+    rs.push_back(0);
+    const double per = (double)total / (double)std::max<int64_t>(nr_target, 1);
+    double acc = 0.0;
+    int64_t rows = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        if (rows > 0 &&
+            (acc + cost[(size_t)u] / 2.0 > per * (double)rs.size() || rows >= kMaxRows)) {
+            rs.push_back((int32_t)u);
+            rows = 0;
+        }
+        acc += (double)cost[(size_t)u];
+        ++rows;
+    }
+    rs.push_back((int32_t)n);
+    return rs;
+}
+
+// Number of row ranges per tile that gives the grid about ctas_per_sm CTAs
+// per SM: 4 by default, 8 for lists of 2e9 entries and more, where a CTA
+// streams tens of MB and the end of the grid waits on the slowest
+// (measured: Barabasi-Albert 2.4e8 entries best at 4, Chung-Lu 1.1e10 at 8).
+int64_t ranges_target(const gila_graph* g, int64_t nt)
+{
+    const int64_t n = g->n;
+    const int64_t per_sm = g->tune.ctas_per_sm > 0 ? g->tune.ctas_per_sm
+                                                   : (g->nnz_khop >= 2000000000LL ? 8 : 4);
+    const int sms = sm_count(g->device);
+    const int64_t t = std::max<int64_t>((per_sm * (int64_t)sms + nt - 1) / nt,
+                                        (n + kMaxRows - 1) / kMaxRows);
+    return std::min<int64_t>(t, n);
+}
+
+// The adjacency rows longer than kHubDeg, which the combine kernel gives a
+// block each.
+gila_status plan_hubs(gila_graph* g, TilePlan& P)
+{
+    const int64_t n = g->n;
+    std::vector<int64_t> arow((size_t)n + 1);
+    GILA_CUDA(cudaMemcpyAsync(arow.data(), g->row, sizeof(int64_t) * (n + 1),
+                              cudaMemcpyDeviceToHost, g->stream));
+    GILA_CUDA(cudaStreamSynchronize(g->stream));
+    std::vector<int32_t> hubs;
+    for (int64_t u = 0; u < n; ++u)
+        if (arow[(size_t)u + 1] - arow[(size_t)u] > kHubDeg) hubs.push_back((int32_t)u);
+    if (!hubs.empty()) {
+        gila_status s = ensure((void**)&P.hubs, &P.hubs_cap, sizeof(int32_t) * hubs.size());
+        if (s != GILA_OK) return s;
+        GILA_CUDA(cudaMemcpyAsync(P.hubs, hubs.data(), sizeof(int32_t) * hubs.size(),
+                                  cudaMemcpyHostToDevice, g->stream));
+    }
+    GILA_CUDA(cudaStreamSynchronize(g->stream));  // the host vector goes out of scope
+    P.nhub = (int32_t)hubs.size();
+    return GILA_OK;
+}
+
+// Window mode: when every row range's k-hop ids lie in a window of at most
+// tv_max consecutive ids (meshes, grids, locality-preserving vertex orders),
+// each range gets that window as its own tile and streams its rows from
+// kcol in place (no rearranged copy). *fits tells whether it applies.
+gila_status plan_window(gila_graph* g, size_t esz, int64_t tv_max, TilePlan& P, bool* fits)
+{
+    *fits = false;
+    const int64_t n = g->n;
+    // automatic mode does not choose windows: on the 1000 x 1000 mesh (k = 3,
+    // rows of 36 entries) the window kernel took 0.176 ms per iteration
+    // against 0.161 ms for the plain kernel, whose smaller blocks keep more
+    // rows in flight; forced tiling (tiled = 1) uses windows where they fit
+    if (g->tune.tiled < 0) return GILA_OK;
+    std::vector<int64_t> krow((size_t)n + 1);
+    GILA_CUDA(cudaMemcpyAsync(krow.data(), g->krow, sizeof(int64_t) * (n + 1),
+                              cudaMemcpyDeviceToHost, g->stream));
+    gila_status s = ensure((void**)&P.rowspan, &P.rowspan_cap, sizeof(int32_t) * 2 * (size_t)n);
+    if (s != GILA_OK) return s;
+    rowspan_kernel<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(n, g->krow, g->kcol,
+                                                                      P.rowspan);
+    count_launch();
+    GILA_CUDA(cudaGetLastError());
+    std::vector<int32_t> span(2 * (size_t)n);
+    GILA_CUDA(cudaMemcpyAsync(span.data(), P.rowspan, sizeof(int32_t) * 2 * n,
+                              cudaMemcpyDeviceToHost, g->stream));
+    GILA_CUDA(cudaStreamSynchronize(g->stream));
+    std::vector<int64_t> cost((size_t)n);
+    int64_t total = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        cost[(size_t)u] = 8 + krow[(size_t)u + 1] - krow[(size_t)u];
+        total += cost[(size_t)u];
+    }
+    const std::vector<int32_t> rs = partition_rows(cost, total, ranges_target(g, 1));
+    const int64_t nr = (int64_t)rs.size() - 1;
+    std::vector<int64_t> wt(2 * (size_t)nr), blk(2 * (size_t)nr);
+    int64_t widest = 0;
+    for (int64_t r = 0; r < nr; ++r) {
+        int64_t lo = INT64_MAX, hi = -1;
+        for (int64_t u = rs[(size_t)r]; u < rs[(size_t)r + 1]; ++u) {
+            lo = std::min<int64_t>(lo, span[2 * (size_t)u]);
+            hi = std::max<int64_t>(hi, span[2 * (size_t)u + 1]);
+        }
+        if (hi < 0) lo = hi = rs[(size_t)r];  // no entries: a one-id window
+        const int64_t base = lo & ~int64_t(1);  // even first id: a 16-byte aligned float2 tile
+        wt[2 * (size_t)r] = base;
+        wt[2 * (size_t)r + 1] = hi - base + 1;
+        widest = std::max<int64_t>(widest, hi - base + 1);
+        const int64_t start = krow[(size_t)rs[(size_t)r]] & ~int64_t(3);  // 16-byte aligned ids
+        blk[2 * (size_t)r] = start;
+        blk[2 * (size_t)r + 1] = krow[(size_t)rs[(size_t)r + 1]] - start;
+    }
+    // the window shares the CTA's shared memory with the range's row offsets
+    const int64_t window_max =
+        std::min<int64_t>(tv_max, (kSmemCap - 4096 - 2 * (kMaxRows + 1) * 8) / (int64_t)esz);
+    if (widest + 1 > window_max) return GILA_OK;
+    if ((s = ensure((void**)&P.blk, &P.blk_cap, sizeof(int64_t) * blk.size())) != GILA_OK) return s;
+    if ((s = ensure((void**)&P.wtile, &P.wtile_cap, sizeof(int64_t) * wt.size())) != GILA_OK)
+        return s;
+    if ((s = ensure((void**)&P.range_start, &P.range_cap, sizeof(int32_t) * rs.size())) != GILA_OK)
+        return s;
+    GILA_CUDA(cudaMemcpyAsync(P.blk, blk.data(), sizeof(int64_t) * blk.size(),
+                              cudaMemcpyHostToDevice, g->stream));
+    GILA_CUDA(cudaMemcpyAsync(P.wtile, wt.data(), sizeof(int64_t) * wt.size(),
+                              cudaMemcpyHostToDevice, g->stream));
+    GILA_CUDA(cudaMemcpyAsync(P.range_start, rs.data(), sizeof(int32_t) * rs.size(),
+                              cudaMemcpyHostToDevice, g->stream));
+    GILA_CUDA(cudaStreamSynchronize(g->stream));  // the host vectors go out of scope
+    P.window = true;
+    P.nt = 1;
+    P.tv = (int32_t)((widest + 1) & ~int64_t(1));
+    P.nr = (int32_t)nr;
+    P.use = true;
+    *fits = true;
+    return GILA_OK;
+}
+
 // Decide whether the blocked path serves g for positions of `esz` bytes and
-// build its layout: tiles, row ranges, block offsets, rearranged ids.
+// build its layout: a window per row range (window mode), or tiles, row
+// ranges, block offsets and rearranged ids.
 gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
 {
     P.ready = true;
     P.use = false;
+    P.window = false;
     const int64_t n = g->n;
     if (n == 0 || g->nnz_khop == 0 || g->tune.tiled == 0) return GILA_OK;
     int64_t tv_max = kTileBudget / (int64_t)esz;
@@ -534,9 +816,14 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
     // limited by GB300's FP64 rate (and its tiles hold half as many
     // positions); below about 10^8 entries the plain kernel was faster on
     // every Barabasi-Albert graph measured (n = 10^3 .. 3 10^4, k = 2, 3)
-    if (g->tune.tiled < 0 &&
-        (avg_seg < min_seg || esz == 16 || g->nnz_khop < kBlockedMinNnz))
-        return GILA_OK;
+    if (g->tune.tiled < 0 && esz == 16) return GILA_OK;
+    const bool tiles_pay = !(g->tune.tiled < 0 && avg_seg < min_seg);
+    if (esz == 8 || g->tune.tiled == 1) {
+        bool fits = false;
+        gila_status s = plan_window(g, esz, tv_max, P, &fits);
+        if (s != GILA_OK || fits) return s;
+    }
+    if (!tiles_pay || (g->tune.tiled < 0 && g->nnz_khop < kBlockedMinNnz)) return GILA_OK;
     const int64_t cells = n * nt;
     gila_status s = ensure((void**)&P.len, &P.len_cap, sizeof(int64_t) * (size_t)cells);
     if (s != GILA_OK) return s;
@@ -558,32 +845,7 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
         cost[(size_t)u] = c;
         total += c;
     }
-    const int sms = sm_count(g->device);
-    // default CTAs per SM: 4, or 8 for lists of 2e9 entries and more, where
-    // a CTA streams tens of MB and the end of the grid waits on the slowest
-    // (measured: Barabasi-Albert 2.4e8 entries best at 4, Chung-Lu 1.1e10 at 8)
-    const int64_t per_sm = g->tune.ctas_per_sm > 0 ? g->tune.ctas_per_sm
-                                                   : (g->nnz_khop >= 2000000000LL ? 8 : 4);
-    int64_t nr_target =
-        std::max<int64_t>((per_sm * (int64_t)sms + nt - 1) / nt, (n + kMaxRows - 1) / kMaxRows);
-    nr_target = std::min<int64_t>(nr_target, n);
-    std::vector<int32_t> rs;
-    rs.push_back(0);
-    {
-        const double per = (double)total / (double)nr_target;
-        double acc = 0.0;
-        int64_t rows = 0;
-        for (int64_t u = 0; u < n; ++u) {
-            if (rows > 0 && (acc + cost[(size_t)u] / 2.0 > per * (double)rs.size() ||
-                             rows >= kMaxRows)) {
-                rs.push_back((int32_t)u);
-                rows = 0;
-            }
-            acc += (double)cost[(size_t)u];
-            ++rows;
-        }
-        rs.push_back((int32_t)n);
-    }
+    const std::vector<int32_t> rs = partition_rows(cost, total, ranges_target(g, nt));
     const int64_t nr = (int64_t)rs.size() - 1;
     // block layout: (j, r) blocks in that order, starts aligned to 4 entries
     std::vector<int64_t> toff((size_t)cells), blk((size_t)(2 * nt * nr));
@@ -618,22 +880,9 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
         n, g->krow, g->kcol, (int)nt, (int)tv, P.toff, P.tk);
     count_launch();
     GILA_CUDA(cudaGetLastError());
-    // hubs of the adjacency for the combine kernel
-    std::vector<int64_t> arow((size_t)n + 1);
-    GILA_CUDA(cudaMemcpyAsync(arow.data(), g->row, sizeof(int64_t) * (n + 1),
-                              cudaMemcpyDeviceToHost, g->stream));
-    GILA_CUDA(cudaStreamSynchronize(g->stream));
-    std::vector<int32_t> hubs;
-    for (int64_t u = 0; u < n; ++u)
-        if (arow[(size_t)u + 1] - arow[(size_t)u] > kHubDeg) hubs.push_back((int32_t)u);
-    if (!hubs.empty()) {
-        if ((s = ensure((void**)&P.hubs, &P.hubs_cap, sizeof(int32_t) * hubs.size())) != GILA_OK)
-            return s;
-        GILA_CUDA(cudaMemcpyAsync(P.hubs, hubs.data(), sizeof(int32_t) * hubs.size(),
-                                  cudaMemcpyHostToDevice, g->stream));
-    }
-    GILA_CUDA(cudaStreamSynchronize(g->stream));  // the host vectors go out of scope
-    P.nhub = (int32_t)hubs.size();
+    // hubs of the adjacency for the combine kernel; synchronises, so the
+    // host vectors above stay valid until their copies are done
+    if ((s = plan_hubs(g, P)) != GILA_OK) return s;
     P.nt = (int32_t)nt;
     P.tv = (int32_t)tv;
     P.nr = (int32_t)nr;
@@ -673,9 +922,50 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
         if (s != GILA_OK) return s;
     }
     if (!P.use || ((uintptr_t)pos_in & 15) != 0) return GILA_OK;
+    if (P.window) {
+        WindowArgs W;
+        W.krow = g->krow;
+        W.kcol = g->kcol;
+        W.row = g->row;
+        W.col = g->col;
+        W.wtile = P.wtile;
+        W.range_start = P.range_start;
+        W.n = g->n;
+        W.d = prm->d;
+        W.t = t;
+        W.p = prm->p;
+        W.q = prm->q;
+        W.pos_in = pos_in;
+        W.pos_out = pos_out;
+        W.disp_out = disp_out;
+        W.tv = P.tv;
+        const size_t wsmem = (size_t)P.tv * esz + 2 * (size_t)(kMaxRows + 1) * sizeof(int64_t);
+        // groups of 8 lanes for rows of up to 64 entries on average, else warps
+        const bool wide = g->nnz_khop > 64 * g->n;
+        const bool fr = (prm->p == 2 && prm->q == 1);
+        cudaError_t e;
+        switch (prm->precision) {
+        case GILA_FP64:
+            e = fr ? launch_window<double, kFR, false>(W, P.nr, wsmem, g->stream, g->device, wide)
+                   : launch_window<double, kGeneric, false>(W, P.nr, wsmem, g->stream, g->device, wide);
+            break;
+        case GILA_FP32_COMPENSATED:
+            e = fr ? launch_window<float, kFR, true>(W, P.nr, wsmem, g->stream, g->device, wide)
+                   : launch_window<float, kGeneric, true>(W, P.nr, wsmem, g->stream, g->device, wide);
+            break;
+        default:
+            e = fr ? launch_window<float, kFR, false>(W, P.nr, wsmem, g->stream, g->device, wide)
+                   : launch_window<float, kGeneric, false>(W, P.nr, wsmem, g->stream, g->device, wide);
+            break;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "window_kernel");
+        *handled = true;
+        return GILA_OK;
+    }
     BlockedArgs B;
-    B.tk = P.tk;
-    B.toff = P.toff;
+    B.tk = P.window ? g->kcol : P.tk;
+    B.toff = P.window ? g->krow : P.toff;
+    B.wtile = P.window ? P.wtile : nullptr;
     B.blk = P.blk;
     B.range_start = P.range_start;
     B.n = g->n;

@@ -105,6 +105,13 @@ struct TilePlan {
     int32_t nhub = 0;
     int64_t* len = nullptr;          // nt n segment lengths (plan scratch)
     size_t len_cap = 0;
+    // window mode: one tile per row range, the window of ids its rows touch;
+    // the ids are read from kcol in place (offsets krow)
+    bool window = false;
+    int64_t* wtile = nullptr;        // 2 nr: first id and length of range r's window
+    size_t wtile_cap = 0;
+    int32_t* rowspan = nullptr;      // 2 n: first and last id of each row (plan scratch)
+    size_t rowspan_cap = 0;
 };
 
 struct ProfileRec {

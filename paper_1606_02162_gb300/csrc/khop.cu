@@ -689,7 +689,9 @@ gila_status build_khop_fill(gila_graph* g, int k)
         cudaFree(g->kcol);
         g->kcol = nullptr;
         g->cap_kcol = 0;
-        if ((s = dev_alloc(&g->kcol, (size_t)nnz)) != GILA_OK) return s;
+        // 4 spare entries: the blocked path's window mode reads kcol in
+        // 16-byte steps that may end up to 12 bytes past the last row
+        if ((s = dev_alloc(&g->kcol, (size_t)nnz + 4)) != GILA_OK) return s;
         g->cap_kcol = (size_t)nnz;
     }
     if (n > 0) {

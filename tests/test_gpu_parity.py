@@ -174,6 +174,41 @@ def test_step_parity_tunings(name, maker, k, tname, tune, prec):
     assert np.abs(got - odisp).max() <= TOL[prec] * np.abs(odisp).max()
 
 
+def _mesh_with_isolated(r, c, extra):
+    g = I.tri_mesh(r, c)
+    u = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    keep = u < g.col_idx
+    return I.csr_from_edges(g.n + extra, u[keep], g.col_idx[keep])
+
+
+@pytest.mark.parametrize("prec", [G.GILA_FP32, G.GILA_FP32_COMPENSATED, G.GILA_FP64],
+                         ids=["fp32", "fp32c", "fp64"])
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("tune", [dict(tiled=1), dict(tiled=1, ctas_per_sm=1),
+                                  dict(tiled=1, ctas_per_sm=12)], ids=["cps4", "cps1", "cps12"])
+def test_step_parity_window_mode(k, prec, tune):
+    """Banded ids (a triangulated mesh, then 37 isolated vertices with empty
+    rows): every row range gets its own window of positions and reads kcol in
+    place, starting at a 16-byte boundary before its first row."""
+    torch = _torch()
+    g = _mesh_with_isolated(37, 41, 37)
+    pos = I.uniform_positions(g.n, 6)
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, k)
+    for t in (0.1 * math.sqrt(g.n), 1e30):
+        with G.Graph.from_inputs(g) as h:
+            G.gila_graph_tune(h.handle, **tune)
+            p_in = torch.tensor(pos, dtype=_dt(prec), device="cuda")
+            p_out = torch.empty_like(p_in)
+            disp = torch.empty_like(p_in)
+            G.gila_layout_step(h.handle, G.params(k=k, precision=prec), t, p_in, p_out, disp)
+            torch.cuda.synchronize()
+            base = p_in.double().cpu().numpy()
+            got = disp.double().cpu().numpy()
+        _, odisp = O.step(g.n, g.row_ptr, g.col_idx, okrow, okcol, base, t)
+        assert np.abs(got - odisp).max() <= TOL[prec] * np.abs(odisp).max()
+        assert (got[g.n - 37:] == 0).all()  # isolated vertices do not move
+
+
 def _np_dt(prec):
     return np.float64 if prec in (G.GILA_FP64, G.GILA_FP64_ORDERED) else np.float32
 
