@@ -48,7 +48,6 @@ struct BlockedArgs {
     int q;
     const void* pos;
     void* part;                // nt n cells of 4 T: (sx, sy, cx, cy) without the factor d^2
-    const int64_t* wtile;      // window mode: first id and length of range r's tile, else null
 };
 
 template <class T, bool COMP>
@@ -99,14 +98,8 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
     // a block holds at most kMaxRows segments of at most tv entries: < 2^31
     const int32_t L = (int32_t)A.blk[2 * (int64_t)blockIdx.x + 1];
     const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos);
-    int64_t tb, tn;
-    if (A.wtile) {  // window mode: this range's own window of ids (first id even)
-        tb = A.wtile[2 * r];
-        tn = A.wtile[2 * r + 1];
-    } else {
-        tb = (int64_t)j * A.tv;
-        tn = (A.n - tb < A.tv) ? A.n - tb : (int64_t)A.tv;
-    }
+    const int64_t tb = (int64_t)j * A.tv;
+    const int64_t tn = (A.n - tb < A.tv) ? A.n - tb : (int64_t)A.tv;
     if (threadIdx.x == 0) {
         // tile j by the bulk-copy engine (tv is even and the placement is
         // 16-byte aligned, so the source is too); an odd float2 tail by hand
@@ -188,27 +181,29 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
         bool done = false;
         f.xu = xr.x;  // the row's own position, set again only when the row changes
         f.yu = xr.y;
-        // 16-byte id loads run four steps (512 entries) ahead: each of the
-        // four unrolled steps below consumes its own ring register and
-        // refills it, so the ring needs no register moves
+        // 16-byte id loads run kRing steps ahead (four, three with the
+        // compensated sums, which need the registers): each of the kRing
+        // unrolled steps below consumes its own ring register and refills
+        // it, so the ring needs no register moves
+        constexpr int kRing = COMP ? 3 : 4;
         auto load_step = [&](int32_t base) {
             const int32_t p0 = base + 4 * lane;
             return (p0 < b) ? ld_ids4(ids4 + (p0 >> 2)) : make_uint4(0, 0, 0, 0);
         };
-        uint4 ring[4];
+        uint4 ring[kRing];
 #pragma unroll
-        for (int st = 0; st < 4; ++st) ring[st] = load_step(a + 128 * st);
-        for (int32_t base = a; base < b && !done; base += 512) {
+        for (int st = 0; st < kRing; ++st) ring[st] = load_step(a + 128 * st);
+        for (int32_t base = a; base < b && !done; base += 128 * kRing) {
 #pragma unroll
-            for (int st = 0; st < 4; ++st) {
+            for (int st = 0; st < kRing; ++st) {
                 const int32_t sb = base + 128 * st;
                 if (sb >= b || done) break;  // warp-uniform
                 const uint4 c = ring[st];
-                ring[st] = load_step(sb + 512);
+                ring[st] = load_step(sb + 128 * kRing);
                 const uint32_t ids[4] = {c.x, c.y, c.z, c.w};
                 const int32_t p0 = sb + 4 * lane;
                 const int32_t lim = (sb + 128 < b) ? sb + 128 : b;
-                if (re > lim && rs <= sb) {  // the whole step lies in row ri (warp-uniform)
+                if (re > lim) {  // the whole step lies in row ri (warp-uniform)
                     if (sb + 128 <= b) {
                         if (COMP) {
                             // compensated mode: the step's four terms summed
@@ -963,9 +958,8 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
         return GILA_OK;
     }
     BlockedArgs B;
-    B.tk = P.window ? g->kcol : P.tk;
-    B.toff = P.window ? g->krow : P.toff;
-    B.wtile = P.window ? P.wtile : nullptr;
+    B.tk = P.tk;
+    B.toff = P.toff;
     B.blk = P.blk;
     B.range_start = P.range_start;
     B.n = g->n;

@@ -269,6 +269,117 @@ t2_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __restrict_
     }
 }
 
+// Tier 2 with the visited bitmap in shared memory (graphs of up to
+// kT2SmemWords * 32 vertices): the same breadth-first search as t2_kernel,
+// but every visit is a shared-memory atomicOr, and the frontier slot that
+// owns an edge is found without a search: each slot marks where its edges
+// start in the current chunk of kT2Threads edges and an inclusive max-scan
+// over the marks gives every edge its slot.
+constexpr int64_t kT2SmemWords = (160 * 1024) / 4;
+
+template <bool FILL>
+__global__ void __launch_bounds__(kT2Threads)
+t2s_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __restrict__ col, int k,
+           const int32_t* __restrict__ queue, int nq, int32_t* __restrict__ lists,
+           int64_t nwords, int64_t* __restrict__ counts, const int64_t* __restrict__ krow,
+           uint32_t* __restrict__ kcol)
+{
+    extern __shared__ uint32_t B[];  // visited bitmap of the current source
+    __shared__ int64_t s_first[kT2Threads];
+    __shared__ int64_t s_start[kT2Threads];
+    __shared__ int32_t s_mark[kT2Threads];
+    __shared__ int32_t s_wmax[kT2Threads / 32];
+    __shared__ int64_t s_wt[kT2Threads / 32 + 1];
+    __shared__ int s_cnt;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int32_t* V = lists + (int64_t)blockIdx.x * n;
+    for (int64_t i = tid; i < nwords; i += kT2Threads) B[i] = 0u;
+    __syncthreads();
+    for (int qi = blockIdx.x; qi < nq; qi += gridDim.x) {
+        const int32_t src = queue[qi];
+        if (tid == 0) {
+            B[src >> 5] |= 1u << (src & 31);
+            V[0] = src;
+            s_cnt = 1;
+        }
+        __syncthreads();
+        int64_t lb = 0, le = 1;
+        for (int depth = 1; depth <= k && lb < le; ++depth) {
+            for (int64_t fb = lb; fb < le; fb += kT2Threads) {
+                const int64_t f = fb + tid;
+                int64_t start = 0, deg = 0;
+                if (f < le) {
+                    const int32_t w = V[f];
+                    start = row[w];
+                    deg = row[w + 1] - start;
+                }
+                int64_t total;
+                const int64_t incl = block_inclusive_scan<int64_t, kT2Threads>(deg, s_wt, &total);
+                const int64_t first = incl - deg;
+                s_first[tid] = first;
+                s_start[tid] = start;
+                for (int64_t base = 0; base < total; base += kT2Threads) {
+                    s_mark[tid] = -1;
+                    __syncthreads();
+                    // a slot marks the first position of its edges in this chunk
+                    if (deg > 0) {
+                        if (first >= base && first < base + kT2Threads)
+                            s_mark[first - base] = tid;
+                        else if (first < base && incl > base)
+                            s_mark[0] = tid;  // its edges run into this chunk
+                    }
+                    __syncthreads();
+                    // inclusive max-scan: the owner of edge base + tid
+                    int32_t o = s_mark[tid];
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int32_t y = __shfl_up_sync(kFull, o, d);
+                        if (lane >= d) o = max(o, y);
+                    }
+                    if (lane == 31) s_wmax[warp] = o;
+                    __syncthreads();
+                    for (int w = 0; w < warp; ++w) o = max(o, s_wmax[w]);
+                    const int64_t e = base + tid;
+                    if (e < total) {
+                        const int32_t x = col[s_start[o] + (e - s_first[o])];
+                        const uint32_t bit = 1u << (x & 31);
+                        const uint32_t old = atomicOr(&B[x >> 5], bit);
+                        if (!(old & bit)) V[atomicAdd(&s_cnt, 1)] = x;
+                    }
+                    __syncthreads();
+                }
+            }
+            lb = le;
+            le = s_cnt;
+            __syncthreads();
+        }
+        const int cnt = s_cnt;
+        if (!FILL) {
+            if (tid == 0) counts[src] = cnt - 1;
+        } else {
+            uint32_t* out = kcol + krow[src];
+            int64_t base = 0;
+            for (int64_t w0 = 0; w0 < nwords; w0 += kT2Threads) {
+                const int64_t wi = w0 + tid;
+                uint32_t w = (wi < nwords) ? B[wi] : 0u;
+                if (wi == (src >> 5)) w &= ~(1u << (src & 31));
+                int64_t total;
+                const int64_t incl =
+                    block_inclusive_scan<int64_t, kT2Threads>((int64_t)__popc(w), s_wt, &total);
+                int64_t o = base + incl - __popc(w);
+                while (w) {
+                    const int b = __ffs(w) - 1;
+                    out[o++] = (uint32_t)(wi * 32 + b);
+                    w &= w - 1;
+                }
+                base += total;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < cnt; i += kT2Threads) B[V[i] >> 5] = 0u;
+        __syncthreads();
+    }
+}
+
 // --------------------------------------------------------------- scan
 
 constexpr int kScanThreads = 256;
@@ -646,7 +757,24 @@ gila_status build_khop_count_impl(gila_graph* g, int k)
         int64_t want = std::min<int64_t>(nq, (int64_t)sms * 4);
         want = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)(budget / per_block)));
         t2_blocks = (int)want;
-        if (S.t2_blocks < t2_blocks || S.bitmap_words != nwords || !S.bitmaps) {
+        if (nwords <= kT2SmemWords) {
+            // bitmaps in shared memory: only the visit lists are global scratch
+            const int64_t lw = std::max<int64_t>(1, std::min<int64_t>(
+                std::min<int64_t>(nq, (int64_t)sms * 4), (int64_t)(budget / ((size_t)n * 4))));
+            t2_blocks = (int)lw;
+            if (S.t2_blocks < t2_blocks || !S.lists) {
+                cudaFree(S.lists);
+                S.lists = nullptr;
+                if ((s = dev_alloc(&S.lists, (size_t)n * t2_blocks)) != GILA_OK) return s;
+                S.t2_blocks = t2_blocks;
+            }
+            const size_t smem = (size_t)nwords * 4;
+            GILA_CUDA(cudaFuncSetAttribute(t2s_kernel<false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            t2s_kernel<false><<<t2_blocks, kT2Threads, smem, st>>>(
+                n, g->row, g->col, k, S.queue, nq, S.lists, nwords, S.counts, nullptr, nullptr);
+            count_launch();
+        } else if (S.t2_blocks < t2_blocks || S.bitmap_words != nwords || !S.bitmaps) {
             cudaFree(S.bitmaps);
             cudaFree(S.lists);
             S.bitmaps = nullptr; S.lists = nullptr;
@@ -656,9 +784,12 @@ gila_status build_khop_count_impl(gila_graph* g, int k)
             S.t2_blocks = t2_blocks;
             S.bitmap_words = nwords;
         }
-        t2_kernel<<<t2_blocks, kT2Threads, 0, st>>>(n, g->row, g->col, k, S.queue, nq, S.bitmaps,
-                                                    S.lists, nwords, S.counts, nullptr, nullptr, 0);
-        count_launch();
+        if (nwords > kT2SmemWords) {
+            t2_kernel<<<t2_blocks, kT2Threads, 0, st>>>(n, g->row, g->col, k, S.queue, nq,
+                                                        S.bitmaps, S.lists, nwords, S.counts,
+                                                        nullptr, nullptr, 0);
+            count_launch();
+        }
     }
     s = exclusive_scan(S.counts, n, g->krow, st);
     if (s != GILA_OK) return s;
@@ -699,7 +830,14 @@ gila_status build_khop_fill(gila_graph* g, int k)
                                                                       S.counts, g->krow, g->kcol);
         count_launch();
     }
-    if (nq > 0) {
+    if (nq > 0 && nwords <= kT2SmemWords) {
+        const size_t smem = (size_t)nwords * 4;
+        GILA_CUDA(cudaFuncSetAttribute(t2s_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+        t2s_kernel<true><<<t2_blocks, kT2Threads, smem, st>>>(
+            n, g->row, g->col, k, S.queue, nq, S.lists, nwords, S.counts, g->krow, g->kcol);
+        count_launch();
+    } else if (nq > 0) {
         t2_kernel<<<t2_blocks, kT2Threads, 0, st>>>(n, g->row, g->col, k, S.queue, nq, S.bitmaps,
                                                     S.lists, nwords, S.counts, g->krow, g->kcol, 1);
         count_launch();
