@@ -209,6 +209,30 @@ def test_step_parity_window_mode(k, prec, tune):
         assert (got[g.n - 37:] == 0).all()  # isolated vertices do not move
 
 
+@pytest.mark.parametrize("tiled", [0, 1], ids=["plain", "blocked"])
+def test_fp64_two_vertex_force_across_scales(tiled):
+    """FP64 repulsion uses a Newton-Raphson reciprocal: the force of a single
+    edge (k = 1, uncapped) matches the closed form d^2/delta - delta^2/d to
+    1e-14 relative at distances from 1e-6 to 1e6."""
+    torch = _torch()
+    g = I.path(2)
+    d = 1.7
+    with G.Graph.from_inputs(g) as h:
+        G.gila_graph_tune(h.handle, tiled=tiled)
+        for delta in (1e-6, 3.3e-3, 0.37, 1.0, 2.9, 29.0, 4.1e3, 1e6):  # away from delta = d
+            pos = np.array([[0.25, -1.5], [0.25 + delta * 0.6, -1.5 + delta * 0.8]])
+            x = torch.tensor(pos, dtype=torch.float64, device="cuda")
+            y, disp = torch.empty_like(x), torch.empty_like(x)
+            G.gila_layout_step(h.handle, G.params(k=1, d=d, precision=G.GILA_FP64), 1e300, x, y,
+                               disp)
+            got = disp.cpu().numpy()
+            dl = math.hypot(pos[1, 0] - pos[0, 0], pos[1, 1] - pos[0, 1])
+            mag = d * d / dl - dl * dl / d  # along (x_0 - x_1) / delta on vertex 0
+            ux, uy = (pos[0] - pos[1]) / dl
+            assert got[0] == pytest.approx([mag * ux, mag * uy], rel=1e-14, abs=0), delta
+            assert got[1] == pytest.approx([-mag * ux, -mag * uy], rel=1e-14, abs=0), delta
+
+
 def _np_dt(prec):
     return np.float64 if prec in (G.GILA_FP64, G.GILA_FP64_ORDERED) else np.float32
 
