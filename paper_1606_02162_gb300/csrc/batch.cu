@@ -16,6 +16,7 @@
 // default t0 uses that graph's n (and, for geometric cooling, the aspect of
 // its own initial bounding box).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -262,11 +263,16 @@ cudaError_t launch_batch(const BatchArgs& A, int grid, int threads, size_t smem,
     return cudaGetLastError();
 }
 
-// Shared-memory opt-in for every instantiation (outside any stream capture).
+// Shared-memory opt-in for every instantiation on the current device
+// (outside any stream capture); once per device, callers may race.
 cudaError_t configure_batch_kernels()
 {
-    static bool done = false;
-    if (done) return cudaSuccess;
+    static std::atomic<uint64_t> done{0};
+    int device = 0;
+    cudaError_t de = cudaGetDevice(&device);
+    if (de != cudaSuccess) return de;
+    const uint64_t bit = 1ull << (device & 63);
+    if (done.load() & bit) return cudaSuccess;
     const int lim = 227 * 1024;
     cudaError_t e = cudaSuccess;
 #define GILA_OPT_IN(T, M, C)                                                                 \
@@ -280,7 +286,7 @@ cudaError_t configure_batch_kernels()
     GILA_OPT_IN(double, kFR, false)
     GILA_OPT_IN(double, kGeneric, false)
 #undef GILA_OPT_IN
-    if (e == cudaSuccess) done = true;
+    if (e == cudaSuccess) done.fetch_or(bit);
     return e;
 }
 

@@ -14,6 +14,7 @@
 // and applies the capped move. Every partial has a fixed place in a fixed
 // order, so results do not depend on scheduling.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <vector>
 
@@ -555,14 +556,14 @@ template <class T, int MODEL, bool COMP, int G>
 cudaError_t launch_window_g(const WindowArgs& W, int grid, size_t smem, cudaStream_t st,
                             int device)
 {
-    static uint64_t configured = 0;  // one bit per device
+    static std::atomic<uint64_t> configured{0};  // one bit per device; callers may race
     const uint64_t bit = 1ull << (device & 63);
-    if (!(configured & bit)) {
+    if (!(configured.load() & bit)) {
         cudaError_t e = cudaFuncSetAttribute(window_kernel<T, MODEL, COMP, G>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kSmemCap - 4096);
         if (e != cudaSuccess) return e;
-        configured |= bit;
+        configured.fetch_or(bit);
     }
     window_kernel<T, MODEL, COMP, G><<<grid, kBThreads, smem, st>>>(W);
     count_launch();
@@ -581,14 +582,14 @@ template <class T, int MODEL, bool COMP>
 cudaError_t launch_pair(const BlockedArgs& B, const CombineArgs& C, int grid, size_t smem,
                         cudaStream_t st, int device)
 {
-    static uint64_t configured = 0;  // one bit per device
+    static std::atomic<uint64_t> configured{0};  // one bit per device; callers may race
     const uint64_t bit = 1ull << (device & 63);
-    if (!(configured & bit)) {
+    if (!(configured.load() & bit)) {
         cudaError_t e = cudaFuncSetAttribute(blocked_kernel<T, MODEL, COMP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kSmemCap - 4096);
         if (e != cudaSuccess) return e;
-        configured |= bit;
+        configured.fetch_or(bit);
     }
     blocked_kernel<T, MODEL, COMP><<<grid, kBThreads, smem, st>>>(B);
     count_launch();
