@@ -423,6 +423,15 @@ gila_status gila_layout_components_run(gila_graph* g, const gila_params* prm, do
                                        const double* pos_in_host, double* pos_out_host,
                                        int32_t* count_out);
 
+/* Test hook for failure detection: while on (1), the blocked path's CTAs
+ * announce their shared-memory tile on its mbarrier but issue no copy, so
+ * every tile wait runs out after 1 ms instead of the normal 1 s bound; the
+ * CTAs then return without computing, and the next synchronising call
+ * (gila_layout_run, gila_layout_metrics) reports GILA_ECUDA. Nothing is left
+ * in flight and the CUDA context stays usable; turn it off (0) to resume
+ * normal iterations. For tests only. */
+gila_status gila_graph_set_wait_test(gila_graph* g, int32_t on);
+
 /* Temperature of iteration i under prm (t0 = resolved initial temperature). */
 double gila_temperature(const gila_params* prm, double t0, int32_t i);
 

@@ -303,6 +303,13 @@ gila_status gila_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* 
 }
 
 
+gila_status gila_graph_set_wait_test(gila_graph* g, int32_t on)
+{
+    if (!g) return fail(GILA_EINVAL, "graph is NULL");
+    g->wait_test = on ? 1 : 0;
+    return GILA_OK;
+}
+
 gila_status gila_graph_set_repulsion_weights(gila_graph* g, const double* weight_host)
 {
     if (!g) return fail(GILA_EINVAL, "graph is NULL");

@@ -33,7 +33,8 @@ constexpr int kMaxRows = 4096;  // rows per range (directory in shared memory)
 constexpr int kTileBudget = kSmemCap - (kMaxRows + 1) * 4 - 4096;
 constexpr uint32_t kBulkChunk = 32768;      // bytes per bulk copy instruction
 constexpr int64_t kBlockedMinNnz = 100000000;  // automatic mode: k-hop entries needed (tiles)
-constexpr uint32_t kWaitPolls = 1u << 24;   // bound on mbarrier polls (far above any copy)
+constexpr uint64_t kWaitNs = 1000000000ull;  // bound on a tile wait (1 s, far above any copy)
+constexpr uint64_t kTestWaitNs = 1000000ull;   // the bound while the wait test hook is on
 
 // Set when a CTA gave up waiting for its tile copy (the launch's partials
 // are then incomplete); read and cleared by blocked_tile_wait_failed().
@@ -49,6 +50,8 @@ struct BlockedArgs {
     int q;
     const void* pos;
     void* part;                // nt n cells of 4 T: (sx, sy, cx, cy) without the factor d^2
+    uint64_t wait_ns;          // bound on the tile wait
+    int skip_copy;             // test hook: announce the tile but copy nothing
 };
 
 template <class T, bool COMP>
@@ -108,7 +111,7 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
         mbar_init(&tile_bar, 1);
         mbar_arrive_expect_tx(&tile_bar, bytes);
         const unsigned char* src = reinterpret_cast<const unsigned char*>(pos + tb);
-        for (uint32_t o = 0; o < bytes; o += kBulkChunk)
+        for (uint32_t o = 0; o < bytes && !A.skip_copy; o += kBulkChunk)
             bulk_g2s(smem_raw + o, src + o, (bytes - o < kBulkChunk) ? bytes - o : kBulkChunk,
                      &tile_bar);
         if ((size_t)tn * sizeof(P2) != bytes) tile[tn - 1] = pos[tb + tn - 1];
@@ -130,16 +133,16 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
         tail[threadIdx.x].row = -1;
     }
     if (threadIdx.x == 0) {
-        bool ok = mbar_wait(&tile_bar, 0, kWaitPolls);
+        bool ok = mbar_wait(&tile_bar, 0, A.wait_ns);
         if (!ok) {
             atomicExch(&g_tile_wait_failed, 1);
-            mbar_wait(&tile_bar, 0, kWaitPolls);  // let the copy land before the CTA ends
+            mbar_wait(&tile_bar, 0, A.wait_ns);  // let the copy land before the CTA ends
         }
         tile_ok = ok ? 1 : 0;
     }
     __syncthreads();
     if (!tile_ok) return;  // uniform across the CTA
-    mbar_wait(&tile_bar, 0, kWaitPolls);  // completed: acquires the tile for this thread
+    mbar_wait(&tile_bar, 0, A.wait_ns);  // completed: acquires the tile for this thread
 
     Rep<T, MODEL, COMP, kSrcShared, true> f;  // d^2 is applied when the partials are added
     f.src.set_shared(tile, (uint32_t)tb);
@@ -433,6 +436,8 @@ struct WindowArgs {
     const void* pos_in;
     void* pos_out;
     void* disp_out;
+    uint64_t wait_ns;           // bound on the tile wait
+    int skip_copy;              // test hook: announce the tile but copy nothing
 };
 
 template <class T, int MODEL, bool COMP, int G>
@@ -461,20 +466,20 @@ __global__ void __launch_bounds__(kBThreads, 1) window_kernel(const WindowArgs A
         mbar_init(&tile_bar, 1);
         mbar_arrive_expect_tx(&tile_bar, bytes);
         const unsigned char* src = reinterpret_cast<const unsigned char*>(pos + tb);
-        for (uint32_t o = 0; o < bytes; o += kBulkChunk)
+        for (uint32_t o = 0; o < bytes && !A.skip_copy; o += kBulkChunk)
             bulk_g2s(smem_raw + o, src + o, (bytes - o < kBulkChunk) ? bytes - o : kBulkChunk,
                      &tile_bar);
         if ((size_t)tn * sizeof(P2) != bytes) tile[tn - 1] = pos[tb + tn - 1];
-        bool ok = mbar_wait(&tile_bar, 0, kWaitPolls);
+        bool ok = mbar_wait(&tile_bar, 0, A.wait_ns);
         if (!ok) {
             atomicExch(&g_tile_wait_failed, 1);
-            mbar_wait(&tile_bar, 0, kWaitPolls);
+            mbar_wait(&tile_bar, 0, A.wait_ns);
         }
         tile_ok = ok ? 1 : 0;
     }
     __syncthreads();
     if (!tile_ok) return;
-    mbar_wait(&tile_bar, 0, kWaitPolls);
+    mbar_wait(&tile_bar, 0, A.wait_ns);
     Rep<T, MODEL, COMP, kSrcShared> rep;
     rep.src.set_shared(tile, (uint32_t)tb);
     rep.d2 = (T)(A.d * A.d);
@@ -934,6 +939,8 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
         W.pos_in = pos_in;
         W.pos_out = pos_out;
         W.disp_out = disp_out;
+        W.wait_ns = g->wait_test ? kTestWaitNs : kWaitNs;
+        W.skip_copy = g->wait_test ? 1 : 0;
         W.tv = P.tv;
         const size_t wsmem = (size_t)P.tv * esz + 2 * (size_t)(kMaxRows + 1) * sizeof(int64_t);
         // groups of 8 lanes for rows of up to 64 entries on average, else warps
@@ -970,6 +977,8 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
     B.q = prm->q;
     B.pos = pos_in;
     B.part = P.part;
+    B.wait_ns = g->wait_test ? kTestWaitNs : kWaitNs;
+    B.skip_copy = g->wait_test ? 1 : 0;
     CombineArgs C;
     C.row = g->row;
     C.col = g->col;

@@ -98,12 +98,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Wait until phase `parity` of `bar` has completed; gives up after
-// `max_polls` unsuccessful polls and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_polls)
+// `limit_ns` nanoseconds and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
 {
     const uint32_t a = smem_addr(bar);
-    for (uint32_t i = 0; i < max_polls; ++i) {
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
         uint32_t done;
         asm volatile(
             "{\n"
@@ -115,8 +123,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
-    return false;
 }
 
 }  // namespace gila

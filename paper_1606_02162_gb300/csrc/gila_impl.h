@@ -150,6 +150,9 @@ struct gila_graph {
     // repulsion weights (Section 4.6), both widths; null when unset
     double* wt64 = nullptr;
     float* wt32 = nullptr;
+    // test hook: blocked-path tiles are announced but not copied, so their
+    // bounded waits run out (failure-detection test)
+    int wait_test = 0;
     // profiling
     bool prof_on = false;
     std::vector<gila::ProfileRec> prof;

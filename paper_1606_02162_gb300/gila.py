@@ -128,6 +128,7 @@ SIGNATURES = [
     ("gila_layout_pruned_run_device", ctypes.c_int, [P, PP, P]),
     ("gila_layout_pruned_run", ctypes.c_int, [P, PP, P, P]),
     ("gila_graph_components", ctypes.c_int, [P, P, ctypes.POINTER(I32)]),
+    ("gila_graph_set_wait_test", ctypes.c_int, [P, I32]),
     ("gila_layout_components_run", ctypes.c_int, [P, PP, D, P, P, ctypes.POINTER(I32)]),
 ]
 
@@ -699,3 +700,8 @@ def gila_layout_components_run(g, prm, pos_in, gap=0.0, pos_out=None):
     _check(load().gila_layout_components_run(g, ctypes.byref(prm), float(gap), _ptr(src),
                                              _ptr(out), ctypes.byref(c)))
     return out, c.value
+
+
+def gila_graph_set_wait_test(g, on) -> None:
+    """Failure-detection test hook (see include/gila.h)."""
+    _check(load().gila_graph_set_wait_test(g, 1 if on else 0))
