@@ -359,6 +359,11 @@ def run_batch(args, wl, ws, rank, local):
         b = G.Batch(graphs)
         x0 = torch.tensor(np.concatenate(pos), dtype=dt, device="cuda")
         x = torch.empty_like(x0)
+        # launch shape and lane thresholds picked by the library's autotuner
+        # on this batch (10 probe iterations per candidate; one-time setup)
+        t_tune = time.perf_counter()
+        tuning = G.gila_batch_autotune(b.handle, prm, x0, 10)
+        t_tune = time.perf_counter() - t_tune
 
         def step():
             G.gila_batch_khop_reset(b.handle)
@@ -385,7 +390,8 @@ def run_batch(args, wl, ws, rank, local):
         out[name] = {"layouts_per_s": ws * len(graphs) * args.steps / (ms / 1e3),
                      "ms_per_step": ms / args.steps,
                      "pairs_per_s": ws * P * iters * args.steps / (ms / 1e3),
-                     "gpu_launches": launches, "clocks": clk}
+                     "gpu_launches": launches, "clocks": clk,
+                     "tuning": tuning, "autotune_s": round(t_tune, 3)}
     # one graph at a time (same kernels of the single-graph path), on a
     # systematic sample of every 16th graph
     sample = graphs[::16]

@@ -574,7 +574,7 @@ gila_status gila_batch_autotune(gila_batch* b, const gila_params* prm, const voi
     gila_params q = *prm;
     q.iters = probe_iters;
     static const int kThreadsSet[3] = {256, 512, 1024};
-    static const int kCtasSet[3] = {1, 2, 4};
+    static const int kCtasSet[4] = {1, 2, 4, 8};
     static const int kGroups[3][3] = {{8, 24, 64}, {4, 12, 32}, {16, 48, 128}};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     GILA_CUDA(cudaEventCreate(&e0));
@@ -584,7 +584,7 @@ gila_status gila_batch_autotune(gila_batch* b, const gila_params* prm, const voi
     float best_ms = INFINITY;
     s = GILA_OK;
     for (int ti = 0; ti < 3 && s == GILA_OK; ++ti)
-        for (int ci = 0; ci < 3 && s == GILA_OK; ++ci) {
+        for (int ci = 0; ci < 4 && s == GILA_OK; ++ci) {
             if (kCtasSet[ci] * kThreadsSet[ti] > 2048) continue;
             for (int gi = 0; gi < 3 && s == GILA_OK; ++gi) {
                 gila_batch_tuning c = {kThreadsSet[ti], kCtasSet[ci], kGroups[gi][0],
