@@ -12,7 +12,13 @@
  *   - Section 4.5: the repelling set of v is its k-neighbourhood N_v(k),
  *     the vertices at graph distance 1..k; all vertices move together once
  *     every force is known.
- *   - Section 5.1: the geometric cooling t_h = sqrt(n d / a) 0.93^h.
+ *   - Section 5.1: the geometric cooling t_h = sqrt(n d / a) 0.93^h, with n
+ *     and a taken per connected component.
+ *   - Sections 4.3 and 4.6: degree-one vertices are pruned before the layout
+ *     and reinserted around their neighbour after it; meanwhile a vertex
+ *     repels with a weight that grows with its pruned neighbours. The
+ *     pipeline runs on each connected component, whose drawings are then
+ *     arranged without overlap.
  *
  * Conventions for every call:
  *   - Every call returns a gila_status; nothing throws across the ABI. On
@@ -87,7 +93,9 @@ typedef struct gila_params {
     int32_t precision; /* GILA_FP32 | GILA_FP64 | GILA_FP32_COMPENSATED | GILA_FP64_ORDERED */
 } gila_params;
 
-/* Layout quality figures of a placement, all accumulated in FP64. */
+/* Layout quality figures of a placement, all accumulated in FP64 (for
+ * FP32 placements each k-hop term d^2 / delta^q is formed in FP32, relative
+ * error below 1e-6; the edge figures are FP64 throughout). */
 typedef struct gila_metrics {
     double edge_mean;     /* mean edge length over the undirected edges */
     double edge_std;      /* population standard deviation of edge lengths */
