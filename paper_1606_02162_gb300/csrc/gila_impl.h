@@ -60,6 +60,9 @@ struct KhopScratch {
     int* qn = nullptr;          // 1
     uint32_t* bitmaps = nullptr;
     int32_t* lists = nullptr;
+    uint32_t* store = nullptr;  // tier-2 balls kept from count to fill (or null)
+    bool keep_balls = true;     // allow the store (the server turns it off: it may wait
+                                // between count and fill, outside its memory accounting)
     int64_t bitmap_words = 0;   // per block
     int t2_blocks = 0;
     size_t cap_n = 0;

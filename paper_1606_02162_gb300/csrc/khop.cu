@@ -276,13 +276,14 @@ t2_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __restrict_
 // start in the current chunk of kT2Threads edges and an inclusive max-scan
 // over the marks gives every edge its slot.
 constexpr int64_t kT2SmemWords = (160 * 1024) / 4;
+constexpr size_t kStoreCap = (size_t)16 << 30;  // device bytes for the stored tier-2 balls
 
 template <bool FILL>
 __global__ void __launch_bounds__(kT2Threads)
 t2s_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __restrict__ col, int k,
            const int32_t* __restrict__ queue, int nq, int32_t* __restrict__ lists,
            int64_t nwords, int64_t* __restrict__ counts, const int64_t* __restrict__ krow,
-           uint32_t* __restrict__ kcol)
+           uint32_t* __restrict__ kcol, uint32_t* __restrict__ store)
 {
     extern __shared__ uint32_t B[];  // visited bitmap of the current source
     __shared__ int64_t s_first[kT2Threads];
@@ -355,6 +356,11 @@ t2s_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __restrict
         const int cnt = s_cnt;
         if (!FILL) {
             if (tid == 0) counts[src] = cnt - 1;
+            if (store) {  // keep the ball for the fill pass (nwords is a multiple of 4)
+                uint4* dst = reinterpret_cast<uint4*>(store + (int64_t)qi * nwords);
+                const uint4* b4 = reinterpret_cast<const uint4*>(B);
+                for (int64_t i = tid; i < nwords / 4; i += kT2Threads) dst[i] = b4[i];
+            }
         } else {
             uint32_t* out = kcol + krow[src];
             int64_t base = 0;
@@ -377,6 +383,38 @@ t2s_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __restrict
         __syncthreads();
         for (int i = tid; i < cnt; i += kT2Threads) B[V[i] >> 5] = 0u;
         __syncthreads();
+    }
+}
+
+// Fill from the balls the count pass stored: each block writes the sorted
+// rows of its sources straight from their bitmaps (no second search).
+__global__ void __launch_bounds__(kT2Threads)
+t2_fill_stored_kernel(const int32_t* __restrict__ queue, int nq, int64_t nwords,
+                      const uint32_t* __restrict__ store, const int64_t* __restrict__ krow,
+                      uint32_t* __restrict__ kcol)
+{
+    __shared__ int64_t s_wt[kT2Threads / 32 + 1];
+    const int tid = threadIdx.x;
+    for (int qi = blockIdx.x; qi < nq; qi += gridDim.x) {
+        const int32_t src = queue[qi];
+        const uint32_t* B = store + (int64_t)qi * nwords;
+        uint32_t* out = kcol + krow[src];
+        int64_t base = 0;
+        for (int64_t w0 = 0; w0 < nwords; w0 += kT2Threads) {
+            const int64_t wi = w0 + tid;
+            uint32_t w = (wi < nwords) ? B[wi] : 0u;
+            if (wi == (src >> 5)) w &= ~(1u << (src & 31));
+            int64_t total;
+            const int64_t incl =
+                block_inclusive_scan<int64_t, kT2Threads>((int64_t)__popc(w), s_wt, &total);
+            int64_t o = base + incl - __popc(w);
+            while (w) {
+                const int b = __ffs(w) - 1;
+                out[o++] = (uint32_t)(wi * 32 + b);
+                w &= w - 1;
+            }
+            base += total;
+        }
     }
 }
 
@@ -670,6 +708,7 @@ void free_khop(gila_graph* g)
     cudaFree(s.qn);
     cudaFree(s.bitmaps);
     cudaFree(s.lists);
+    cudaFree(s.store);
     s = KhopScratch();
     cudaFree(g->krow);
     cudaFree(g->kcol);
@@ -696,9 +735,12 @@ void release_khop_scratch(gila_graph* g)
     cudaFree(s.qn);
     cudaFree(s.bitmaps);
     cudaFree(s.lists);
+    cudaFree(s.store);
     const size_t cap = s.scratch_cap;
+    const bool keep = s.keep_balls;
     s = KhopScratch();
     s.scratch_cap = cap;
+    s.keep_balls = keep;
 }
 
 gila_status build_khop(gila_graph* g, int k)
@@ -769,10 +811,21 @@ gila_status build_khop_count_impl(gila_graph* g, int k)
                 S.t2_blocks = t2_blocks;
             }
             const size_t smem = (size_t)nwords * 4;
+            // keep every tier-2 ball for the fill pass when they fit in
+            // kStoreCap bytes of device memory (else the fill searches again)
+            const size_t store_bytes = (size_t)nq * (size_t)nwords * 4;
+            cudaFree(S.store);
+            S.store = nullptr;
+            if (S.keep_balls && store_bytes <= kStoreCap) {
+                void* p = nullptr;
+                if (cudaMalloc(&p, store_bytes) == cudaSuccess) S.store = (uint32_t*)p;
+                else cudaGetLastError();
+            }
             GILA_CUDA(cudaFuncSetAttribute(t2s_kernel<false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             t2s_kernel<false><<<t2_blocks, kT2Threads, smem, st>>>(
-                n, g->row, g->col, k, S.queue, nq, S.lists, nwords, S.counts, nullptr, nullptr);
+                n, g->row, g->col, k, S.queue, nq, S.lists, nwords, S.counts, nullptr, nullptr,
+                S.store);
             count_launch();
         } else if (S.t2_blocks < t2_blocks || S.bitmap_words != nwords || !S.bitmaps) {
             cudaFree(S.bitmaps);
@@ -830,12 +883,17 @@ gila_status build_khop_fill(gila_graph* g, int k)
                                                                       S.counts, g->krow, g->kcol);
         count_launch();
     }
-    if (nq > 0 && nwords <= kT2SmemWords) {
+    if (nq > 0 && nwords <= kT2SmemWords && S.store) {
+        t2_fill_stored_kernel<<<(unsigned)std::min<int64_t>(nq, (int64_t)sms * 8), kT2Threads, 0,
+                                st>>>(S.queue, nq, nwords, S.store, g->krow, g->kcol);
+        count_launch();
+    } else if (nq > 0 && nwords <= kT2SmemWords) {
         const size_t smem = (size_t)nwords * 4;
         GILA_CUDA(cudaFuncSetAttribute(t2s_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
         t2s_kernel<true><<<t2_blocks, kT2Threads, smem, st>>>(
-            n, g->row, g->col, k, S.queue, nq, S.lists, nwords, S.counts, g->krow, g->kcol);
+            n, g->row, g->col, k, S.queue, nq, S.lists, nwords, S.counts, g->krow, g->kcol,
+            nullptr);
         count_launch();
     } else if (nq > 0) {
         t2_kernel<<<t2_blocks, kT2Threads, 0, st>>>(n, g->row, g->col, k, S.queue, nq, S.bitmaps,
@@ -845,6 +903,8 @@ gila_status build_khop_fill(gila_graph* g, int k)
     (void)sms;
     GILA_CUDA(cudaGetLastError());
     GILA_CUDA(cudaStreamSynchronize(st));
+    cudaFree(S.store);  // the stored balls served their one fill
+    S.store = nullptr;
     s = build_bins(g);
     if (s != GILA_OK) return s;
     g->nnz_khop = nnz;

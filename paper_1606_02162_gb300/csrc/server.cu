@@ -185,6 +185,7 @@ gila_status admit_job(gila_server* s, const JobPtr& j, std::string* err)
     }
     gila_graph_set_stream(j->g, j->st);
     j->g->ks.scratch_cap = std::max<size_t>((size_t)64 << 20, s->budget / 8);
+    j->g->ks.keep_balls = false;  // nothing held between count and fill beyond the scratch
     int64_t nnz = 0;
     st = build_khop_count(j->g, j->prm.k, &nnz);
     if (st != GILA_OK) {
