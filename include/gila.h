@@ -143,8 +143,10 @@ gila_status gila_csr_validate(int64_t n, const int64_t* row_ptr, const int32_t* 
  * col_idx int32[row_ptr[n]] are host arrays in symmetric CSR form (each
  * undirected edge stored in both rows). flags: GILA_GRAPH_VALIDATE rejects a
  * malformed CSR with GILA_EINVAL; GILA_GRAPH_SIMPLIFY repairs it instead.
- * Without either flag the CSR is trusted. On success *out owns device
- * copies of the arrays. */
+ * Without either flag only what the kernels need to index safely is checked
+ * (row_ptr[0] = 0, non-decreasing, every id in [0, n); GILA_EINVAL
+ * otherwise); symmetry and simplicity are then the caller's to guarantee.
+ * On success *out owns device copies of the arrays. */
 gila_status gila_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
                               int32_t flags, gila_graph** out);
 
@@ -321,7 +323,8 @@ gila_status gila_server_create(size_t mem_budget_bytes, int32_t max_slots, gila_
 /* Stop the threads, fail unfinished jobs, free everything. Must not run
  * concurrently with other calls on the same server. */
 void gila_server_destroy(gila_server* s);
-/* Queue a job: graph (host CSR, as for gila_graph_create, trusted),
+/* Queue a job: graph (host CSR, as for gila_graph_create without flags:
+ * offsets and ids are checked, symmetry is the caller's), 
  * parameters (prm->iters iterations), initial placement (host double[2n]).
  * The arrays are copied before the call returns. *ticket identifies it. */
 gila_status gila_server_submit(gila_server* s, int64_t n, const int64_t* row_ptr,

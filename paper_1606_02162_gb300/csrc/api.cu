@@ -199,6 +199,22 @@ gila_status graph_create_from_device(int64_t n, const int64_t* row_dev, const in
 }
 
 
+gila_status check_csr_bounds(int64_t n, const int64_t* row_ptr, const int32_t* col_idx)
+{
+    if (row_ptr[0] != 0) return fail(GILA_EINVAL, "row_ptr[0] != 0");
+    for (int64_t u = 0; u < n; ++u)
+        if (row_ptr[u + 1] < row_ptr[u])
+            return fail(GILA_EINVAL, "row_ptr decreases at row " + std::to_string(u));
+    const int64_t nnz = row_ptr[n];
+    if (nnz > 0 && !col_idx) return fail(GILA_EINVAL, "col_idx is NULL");
+    for (int64_t e = 0; e < nnz; ++e)
+        if (col_idx[e] < 0 || col_idx[e] >= n)
+            return fail(GILA_EINVAL, "id " + std::to_string(col_idx[e]) + " out of range at entry " +
+                                         std::to_string(e));
+    return GILA_OK;
+}
+
+
 }  // namespace gila
 
 using namespace gila;
@@ -217,6 +233,7 @@ void gila_params_default(gila_params* p)
     p->q = 1;
     p->precision = GILA_FP32;
 }
+
 
 gila_status gila_csr_validate(int64_t n, const int64_t* row_ptr, const int32_t* col_idx)
 {
@@ -273,8 +290,10 @@ gila_status gila_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* 
     } else if (flags & GILA_GRAPH_VALIDATE) {
         gila_status s = gila_csr_validate(n, row_ptr, col_idx);
         if (s != GILA_OK) return s;
-    } else if (row_ptr[0] != 0 || row_ptr[n] < 0) {
-        return fail(GILA_EINVAL, "row_ptr is malformed");
+    } else {
+        // always: offsets and ids the kernels can index safely
+        gila_status s = check_csr_bounds(n, row_ptr, col_idx);
+        if (s != GILA_OK) return s;
     }
     const int64_t nnz = row_ptr[n];
     if (nnz > 0 && !col_idx) return fail(GILA_EINVAL, "col_idx is NULL");

@@ -456,6 +456,9 @@ gila_status gila_batch_create(int32_t count, const int64_t* n, const int64_t* co
         if (flags & GILA_GRAPH_VALIDATE) {
             gila_status s = gila_csr_validate(n[i], row_ptr[i], col_idx[i]);
             if (s != GILA_OK) return fail(s, "graph " + std::to_string(i) + ": " + gila_last_error());
+        } else {
+            gila_status s = check_csr_bounds(n[i], row_ptr[i], col_idx[i]);
+            if (s != GILA_OK) return fail(s, "graph " + std::to_string(i) + ": " + gila_last_error());
         }
         voff[i + 1] = voff[i] + n[i];
         eoff[i + 1] = eoff[i] + (row_ptr[i][n[i]] - row_ptr[i][0]);

@@ -194,6 +194,9 @@ gila_status prepare_iteration(gila_graph* g, const gila_params* prm);
 gila_status blocked_tile_wait_failed(cudaStream_t st);
 gila_status convert_positions(gila_graph* g, int precision, const double* src, void* dst,
                               bool to_device_type);
+// Offsets non-decreasing from 0 and every id in [0, n): what the kernels need
+// to index safely (GILA_EINVAL otherwise). Host arrays.
+gila_status check_csr_bounds(int64_t n, const int64_t* row_ptr, const int32_t* col_idx);
 // Repulsion weights from host or device doubles (null clears); synchronises.
 gila_status set_repulsion_weights(gila_graph* g, const double* w, bool w_on_device);
 // Upload a graph from device CSR arrays (copied; ids trusted).

@@ -477,6 +477,10 @@ gila_status gila_server_submit(gila_server* s, int64_t n, const int64_t* row_ptr
     j->row.assign(row_ptr, row_ptr + n + 1);
     for (auto& r : j->row) r -= row_ptr[0];
     j->col.assign(col_idx + row_ptr[0], col_idx + row_ptr[0] + nnz);
+    {
+        gila_status bs = check_csr_bounds(n, j->row.data(), j->col.data());
+        if (bs != GILA_OK) return bs;
+    }
     if (n > 0) j->pos_in.assign(pos_in, pos_in + 2 * n);
     j->prm = *prm;
     j->t_submit = Clock::now();

@@ -109,3 +109,34 @@ def test_product_package_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cpp", ".h", ".cuh")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert not bad.search(src), f"{f} reaches into the oracle"
+
+
+@pytest.mark.parametrize("row,col,needle", [
+    ([0, 1, 2], [1, 2], "out of range"),
+    ([0, 2, 1], [1, 0], "decreases"),
+    ([1, 2, 3], [1, 0], "row_ptr[0]"),
+    ([0, 1, 2], [1, -1], "out of range"),
+])
+def test_graph_create_rejects_unsafe_csr_without_gpu(row, col, needle):
+    """Offsets and ids are checked before any device work, flags or not, so a
+    malformed CSR can never reach a kernel."""
+    from paper_1606_02162_gb300 import gila as G
+    with pytest.raises(G.GilaError) as err:
+        G.gila_graph_create(2, np.array(row, dtype=np.int64), np.array(col, dtype=np.int32))
+    assert err.value.status == G.GILA_EINVAL and needle in str(err.value)
+
+
+def test_batch_create_rejects_unsafe_csr_without_gpu():
+    from paper_1606_02162_gb300 import gila as G
+    good = I.path(4)
+    bad = I.path(3)
+    bad_col = bad.col_idx.copy()
+    bad_col[0] = 7
+    import ctypes
+    lib = G.load()
+    ns = (ctypes.c_int64 * 2)(good.n, bad.n)
+    rows = (ctypes.c_void_p * 2)(good.row_ptr.ctypes.data, bad.row_ptr.ctypes.data)
+    cols = (ctypes.c_void_p * 2)(good.col_idx.ctypes.data, bad_col.ctypes.data)
+    out = ctypes.c_void_p()
+    st = lib.gila_batch_create(2, ns, rows, cols, 0, ctypes.byref(out))
+    assert st == G.GILA_EINVAL and b"graph 1" in lib.gila_last_error()
