@@ -50,6 +50,12 @@ WORKLOADS = {
                            oracle_sample=2048,
                            desc="Chung-Lu gamma=2.3, n=250000, E=1000000, k=3, 300 iterations, "
                                 "FP32 compensated"),
+    "ba1m_k2": dict(graph="ba1m", k=2, iters=500, precision="fp32", oracle_sample=4096,
+                    desc="Barabasi-Albert n=333,334 m=3 (999,996 edges), k=2, 500 iterations, "
+                         "linear cooling from 0.1*sqrt(n), d=1, FP32"),
+    "ba1m_k3": dict(graph="ba1m", k=3, iters=500, precision="fp32", oracle_sample=2048,
+                    desc="Barabasi-Albert n=333,334 m=3 (999,996 edges), k=3, 500 iterations, "
+                         "linear cooling from 0.1*sqrt(n), d=1, FP32"),
     "batch4096": dict(k=2, iters=200, precision="fp32",
                       desc="4096 graphs, n log-uniform in [50, 5000] (random trees, near-square "
                            "grids, G(n, 4/(n-1))), k=2, 200 iterations each, one persistent launch"),
@@ -300,8 +306,14 @@ def cpu_baseline(wl, g, pos, budget_s=20.0):
             t_it += force_pass()
             done += 1
         t_layout = t_build + t_it / done * iters
-        return {"value": pairs * iters / t_layout, "unit": "pairs/s", "cores": O.threads(),
-                "kind": "oracle",
+        cores = O.threads()
+        O.set_threads(1)
+        try:
+            t_one = force_pass()
+        finally:
+            O.set_threads(cores)
+        return {"value": pairs * iters / t_layout, "unit": "pairs/s", "cores": cores,
+                "kind": "oracle", "single_thread_pairs_per_s": pairs / t_one,
                 "sample": f"FP64 C oracle on a systematic sample of {S} of {g.n} vertices: "
                           f"their k-hop rows ({t_build:.2f} s) + {done} force passes over them "
                           f"({t_it:.2f} s), scaled to one whole layout of the sample"}
@@ -319,10 +331,21 @@ def cpu_baseline(wl, g, pos, budget_s=20.0):
         t_it += time.perf_counter() - t
         done += 1
     t_layout = t_build + t_it / done * iters
-    return {"value": P * iters / t_layout, "unit": "pairs/s", "cores": O.threads(),
+    cores = O.threads()
+    # the same iteration on one thread (one step, for the per-core figure)
+    O.set_threads(1)
+    try:
+        t = time.perf_counter()
+        O.step(g.n, g.row_ptr, g.col_idx, krow, kcol, cur, O.temperature(0, t0, done, iters))
+        t_one = time.perf_counter() - t
+    finally:
+        O.set_threads(cores)
+    return {"value": P * iters / t_layout, "unit": "pairs/s", "cores": cores,
             "kind": "oracle",
+            "single_thread_pairs_per_s": P / t_one,
             "sample": f"FP64 C oracle: k-hop build ({t_build:.2f} s) + {done} of {iters} "
-                      f"iterations ({t_it:.2f} s), scaled to one whole layout"}
+                      f"iterations ({t_it:.2f} s), scaled to one whole layout; one more "
+                      f"iteration on 1 thread ({t_one:.2f} s) for the per-core figure"}
 
 
 def _timed_region(torch, stream, fn, steps):

@@ -393,6 +393,7 @@ def workload(name: str) -> tuple[Graph, np.ndarray]:
     ba100k      : Barabasi-Albert n=100,000, m=3, seed 2, U[0, sqrt n]^2
     chunglu250k : Chung-Lu gamma=2.3, n=250,000, E=1,000,000, seed 3
     mesh1000    : 1000x1000 triangulated mesh, seed 3
+    ba1m        : Barabasi-Albert n=333,334, m=3 (999,996 edges), seed 12, U[0, sqrt n]^2
     """
     if name == "grid32":
         g = grid(32, 32)
@@ -406,4 +407,7 @@ def workload(name: str) -> tuple[Graph, np.ndarray]:
     if name == "mesh1000":
         g = tri_mesh(1000, 1000)
         return g, uniform_positions(g.n, 3)
+    if name == "ba1m":
+        g = barabasi_albert(333_334, 3, 12)
+        return g, uniform_positions(g.n, 12)
     raise KeyError(name)
