@@ -140,3 +140,30 @@ def test_batch_create_rejects_unsafe_csr_without_gpu():
     out = ctypes.c_void_p()
     st = lib.gila_batch_create(2, ns, rows, cols, 0, ctypes.byref(out))
     assert st == G.GILA_EINVAL and b"graph 1" in lib.gila_last_error()
+
+
+def _declared_arity():
+    """Parameter count of every function declared in include/gila.h."""
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "include", "gila.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(gila_\w+)\s*\(([^;{]*?)\)\s*;", src):
+        name, params = m.group(1), m.group(2).strip()
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every entry point the binding declares has the header's parameter count."""
+    from paper_1606_02162_gb300 import gila as G
+    arity = _declared_arity()
+    sigs = list(G.SIGNATURES)
+    for extra in ("SERVER_SIGNATURES",):
+        sigs += list(getattr(G, extra, []))
+    assert sigs
+    for name, _res, args in sigs:
+        assert name in arity, name
+        assert len(args) == arity[name], (name, len(args), arity[name])
+    # and every declared entry point has a binding
+    assert set(arity) == {n for n, _, _ in sigs}
