@@ -73,11 +73,11 @@ KERNEL_SOURCES = ("paper_1606_02162_gb300/csrc/blocked.cu",
                   "paper_1606_02162_gb300/csrc/force.cuh",
                   "paper_1606_02162_gb300/csrc/device_util.cuh")
 NCU_TRAFFIC = {
-    "ba100k_k3": {"bytes": 965340928 + 8196352 + 10422272,
+    "ba100k_k3": {"bytes": 965216512 + 8248576 + 10422272,
                   "kernels": "blocked_kernel + combine_kernel (one iteration)",
                   "profile": "profiles/blocked_kernel_ba100k_k3.md, "
                              "profiles/combine_kernel_ba100k_k3.md",
-                  "sources_sha256": "f2c654ed673537a880db6ab43b4adf9fe049d88b3497e77765199d62ead738c7"},
+                  "sources_sha256": "dd6ebb8a3b6cb2464cd3e50359178b82b1f07c226d93eb22612f92a97fa75d02"},
 }
 
 
