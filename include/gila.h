@@ -123,6 +123,11 @@ typedef struct gila_tuning {
     int32_t chunk;         /* entries per chunk of a chunked row (32768) */
     int32_t ctas_per_sm;   /* blocked path: row ranges per tile chosen so that the grid holds
                               about this many CTAs per SM (4; 8 from 2e9 k-hop entries) */
+    int32_t bank_spread;   /* blocked path: 0 or 1 (default on) orders each row's entries of
+                              a tile so that the lanes of one shared-memory gather read
+                              distinct banks where the entries allow; -1 keeps ascending
+                              id order. The plan then needs a temporary copy of the k-hop
+                              lists (ascending order if it cannot be allocated) */
 } gila_tuning;
 
 typedef struct gila_graph gila_graph;

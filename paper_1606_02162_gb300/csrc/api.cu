@@ -372,6 +372,8 @@ gila_status gila_graph_tune(gila_graph* g, const gila_tuning* t)
     if (t->tile_vertices < 0 || t->min_segment < 0 || t->small_max < 0 || t->warp_max < 0 ||
         t->block_max < 0 || t->chunk < 0 || t->ctas_per_sm < 0)
         return fail(GILA_EINVAL, "tuning values must be >= 0");
+    if (t->bank_spread < -1 || t->bank_spread > 1)
+        return fail(GILA_EINVAL, "bank_spread must be -1, 0 or 1");
     BinConfig c;  // defaults
     if (t->small_max) c.small_max = t->small_max;
     if (t->warp_max) c.warp_max = t->warp_max;
@@ -397,6 +399,7 @@ gila_status gila_graph_get_tuning(const gila_graph* g, gila_tuning* out)
     out->min_segment = g->tune.min_segment > 0 ? g->tune.min_segment : 48;
     out->ctas_per_sm = g->tune.ctas_per_sm > 0 ? g->tune.ctas_per_sm
                                                : (g->nnz_khop >= 2000000000LL ? 8 : 4);
+    out->bank_spread = g->tune.bank_spread >= 0 ? 1 : -1;
     out->small_max = g->bins.cfg.small_max;
     out->warp_max = g->bins.cfg.warp_max;
     out->block_max = g->bins.cfg.block_max;

@@ -558,6 +558,127 @@ __global__ void block_copy_kernel(int64_t n, const int64_t* __restrict__ krow,
     for (int64_t e = lo + lane; e < hi; e += 32) dst[e - lo] = kcol[e];
 }
 
+// The same copy, with each segment's ids ordered for blocked_kernel's
+// shared-memory gathers. One gather of a warp is served in groups of G
+// lanes (G = 128 bytes / position size: 16 for float2, 8 for double2), one
+// wavefront per group when the group's tile offsets are distinct modulo G
+// (distinct banks), one more per repeat otherwise; in ascending id order
+// the residues fall at random and a 16-lane group takes about three. A
+// row's sum does not depend on the order of its entries (up to rounding),
+// so every group of slots that one gather reads (the positions p of a
+// stripe step with equal p mod 4, in one half of the step for float2, one
+// quarter for double2) takes one id of each residue while all G residues
+// have ids left, otherwise ids of distinct residues, those with most ids
+// left first. Each gather reads one segment only (a step that holds
+// several rows gathers once per row), so segments are ordered
+// independently. One warp per segment: count residues, scatter the ids by
+// residue into scratch (stable), deal them to the slots.
+template <int G>
+__global__ void __launch_bounds__(256) block_spread_kernel(
+    int64_t n, const int64_t* __restrict__ krow, const uint32_t* __restrict__ kcol, int nt,
+    int tv, const int64_t* __restrict__ toff, const int64_t* __restrict__ blk,
+    const int32_t* __restrict__ range_start, int nr, uint32_t* __restrict__ scratch,
+    uint32_t* __restrict__ tk)
+{
+    __shared__ int s_run[8][G];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n * nt) return;  // warp-uniform
+    const int j = (int)(i / n);
+    const int64_t u = i % n;
+    int64_t lo, hi;
+    seg_bounds(krow, kcol, u, j, nt, tv, &lo, &hi);
+    if (hi == lo) return;
+    const uint32_t tb = (uint32_t)j * (uint32_t)tv;
+    // the block (j, r) that holds the segment, and the segment's place in it
+    int ra = 0, rb = nr - 1;
+    while (ra < rb) {
+        const int mid = (ra + rb + 1) >> 1;
+        if (range_start[mid] <= u) ra = mid; else rb = mid - 1;
+    }
+    const int64_t bs = blk[2 * ((int64_t)j * nr + ra)];
+    const int64_t L = blk[2 * ((int64_t)j * nr + ra) + 1];
+    const int64_t S0 = toff[i] - bs, S1 = S0 + (hi - lo);
+    uint32_t* dst = tk + toff[i];
+    uint32_t* scr = scratch + toff[i];
+
+    // residue counts and their exclusive prefix (lane c holds residue c)
+    if (lane < G) s_run[wl][lane] = 0;
+    __syncwarp();
+    for (int64_t e = lo + lane; e < hi; e += 32) atomicAdd(&s_run[wl][(kcol[e] - tb) % G], 1);
+    __syncwarp();
+    const int cnt = (lane < G) ? s_run[wl][lane] : 0;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int cstart = incl - cnt;
+    __syncwarp();
+    if (lane < G) s_run[wl][lane] = cstart;
+    __syncwarp();
+    // stable scatter by residue
+    for (int64_t base = lo; base < hi; base += 32) {
+        const int64_t e = base + lane;
+        const bool act = e < hi;
+        const uint32_t id = act ? kcol[e] : 0u;
+        const int c = act ? (int)((id - tb) % G) : G + lane;
+        const unsigned m = __match_any_sync(0xffffffffu, c);
+        const int o = act ? s_run[wl][c] + __popc(m & ((1u << lane) - 1u)) : 0;
+        __syncwarp();
+        if (act && lane == 31 - __clz(m)) s_run[wl][c] += __popc(m);
+        __syncwarp();
+        if (act) scr[o] = id;
+    }
+    __syncwarp();  // orders the scratch writes before the other lanes read them
+
+    int rem = cnt, used = 0;
+    auto deal = [&](int64_t pf, int g) {
+        // g slots at pf, pf + 4, ...: distinct residues, most ids left first
+        for (int filled = 0; filled < g;) {
+            const bool avail = lane < G && rem > 0;
+            const int nz = __popc(__ballot_sync(0xffffffffu, avail));
+            if (nz == 0) break;  // cannot happen: the slots left equal the ids left
+            const int take = (nz < g - filled) ? nz : g - filled;
+            int rank = lane;  // all G residues give one id: any order
+            if (take < G) {
+                rank = 0;
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    const int rk = __shfl_sync(0xffffffffu, rem, k);
+                    rank += (rk > rem || (rk == rem && k < lane)) ? 1 : 0;
+                }
+            }
+            if (avail && rank < take) {
+                dst[pf - S0 + 4 * (filled + rank)] = scr[cstart + used];
+                ++used;
+                --rem;
+            }
+            filled += take;
+        }
+    };
+    // the stripes blocked_kernel cuts the block into
+    auto stripe_a = [&](int w) -> int64_t {
+        return (w >= kBWarps) ? L : ((L * w / kBWarps) & ~int64_t(3));
+    };
+    constexpr int kSpan = 4 * G;  // positions one G-lane group reads in one step
+    int w = (int)(S0 * kBWarps / L);  // S0 < L
+    for (int64_t cur = S0; cur < S1;) {
+        while (w > 0 && stripe_a(w) > cur) --w;
+        while (w < kBWarps - 1 && stripe_a(w + 1) <= cur) ++w;
+        const int64_t aw = stripe_a(w), bw = stripe_a(w + 1);
+        int64_t he = aw + (cur - aw) / kSpan * kSpan + kSpan;
+        if (he > bw) he = bw;
+        if (he > S1) he = S1;
+        for (int q = 0; q < 4; ++q) {
+            const int64_t pf = cur + ((q - (int)(cur & 3)) & 3);
+            if (pf < he) deal(pf, (int)((he - pf + 3) >> 2));
+        }
+        cur = he;
+    }
+}
+
 template <class T, int MODEL, bool COMP, int G>
 cudaError_t launch_window_g(const WindowArgs& W, int grid, size_t smem, cudaStream_t st,
                             int device)
@@ -878,13 +999,37 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
                               cudaMemcpyHostToDevice, g->stream));
     GILA_CUDA(cudaMemcpyAsync(P.range_start, rs.data(), sizeof(int32_t) * rs.size(),
                               cudaMemcpyHostToDevice, g->stream));
-    block_copy_kernel<<<(unsigned)((cells * 32 + 255) / 256), 256, 0, g->stream>>>(
-        n, g->krow, g->kcol, (int)nt, (int)tv, P.toff, P.tk);
+    // ids ordered for conflict-free gathers where scratch for the scatter
+    // can be had; in ascending order otherwise
+    void* scratch = nullptr;
+    if (g->tune.bank_spread >= 0 && cudaMalloc(&scratch, sizeof(uint32_t) * (size_t)tk_len) !=
+                                        cudaSuccess) {
+        cudaGetLastError();  // clear the failed allocation
+        scratch = nullptr;
+    }
+    const unsigned copy_blocks = (unsigned)((cells * 32 + 255) / 256);
+    if (scratch && esz == 8)
+        block_spread_kernel<16><<<copy_blocks, 256, 0, g->stream>>>(
+            n, g->krow, g->kcol, (int)nt, (int)tv, P.toff, P.blk, P.range_start, (int)nr,
+            (uint32_t*)scratch, P.tk);
+    else if (scratch)
+        block_spread_kernel<8><<<copy_blocks, 256, 0, g->stream>>>(
+            n, g->krow, g->kcol, (int)nt, (int)tv, P.toff, P.blk, P.range_start, (int)nr,
+            (uint32_t*)scratch, P.tk);
+    else
+        block_copy_kernel<<<copy_blocks, 256, 0, g->stream>>>(n, g->krow, g->kcol, (int)nt,
+                                                              (int)tv, P.toff, P.tk);
     count_launch();
-    GILA_CUDA(cudaGetLastError());
+    cudaError_t ce = cudaGetLastError();
     // hubs of the adjacency for the combine kernel; synchronises, so the
     // host vectors above stay valid until their copies are done
-    if ((s = plan_hubs(g, P)) != GILA_OK) return s;
+    if (ce == cudaSuccess) s = plan_hubs(g, P);
+    if (scratch) {
+        cudaStreamSynchronize(g->stream);
+        cudaFree(scratch);
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "block copy");
+    if (s != GILA_OK) return s;
     P.nt = (int32_t)nt;
     P.tv = (int32_t)tv;
     P.nr = (int32_t)nr;

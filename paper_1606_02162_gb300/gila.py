@@ -58,7 +58,8 @@ class gila_tuning(ctypes.Structure):
     _fields_ = [("tiled", ctypes.c_int32), ("tile_vertices", ctypes.c_int32),
                 ("min_segment", ctypes.c_int32), ("small_max", ctypes.c_int32),
                 ("warp_max", ctypes.c_int32), ("block_max", ctypes.c_int32),
-                ("chunk", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("chunk", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("bank_spread", ctypes.c_int32)]
 
 
 class gila_batch_tuning(ctypes.Structure):
@@ -246,9 +247,10 @@ def gila_graph_info(g) -> dict:
 
 
 def gila_graph_tune(g, tiled=-1, tile_vertices=0, min_segment=0, small_max=0, warp_max=0,
-                    block_max=0, chunk=0, ctas_per_sm=0) -> None:
+                    block_max=0, chunk=0, ctas_per_sm=0, bank_spread=0) -> None:
     t = gila_tuning(int(tiled), int(tile_vertices), int(min_segment), int(small_max),
-                    int(warp_max), int(block_max), int(chunk), int(ctas_per_sm))
+                    int(warp_max), int(block_max), int(chunk), int(ctas_per_sm),
+                    int(bank_spread))
     _check(load().gila_graph_tune(g, ctypes.byref(t)))
 
 

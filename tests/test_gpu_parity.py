@@ -141,6 +141,7 @@ TUNINGS = [
     ("untiled", dict(tiled=0)),
     ("tiled", dict(tiled=1)),
     ("tiled_small_tiles", dict(tiled=1, tile_vertices=1000)),
+    ("tiled_small_tiles_ascending", dict(tiled=1, tile_vertices=1000, bank_spread=-1)),
     ("untiled_small_classes", dict(tiled=0, small_max=4, warp_max=64, block_max=512, chunk=300)),
 ]
 
@@ -207,6 +208,34 @@ def test_step_parity_window_mode(k, prec, tune):
         _, odisp = O.step(g.n, g.row_ptr, g.col_idx, okrow, okcol, base, t)
         assert np.abs(got - odisp).max() <= TOL[prec] * np.abs(odisp).max()
         assert (got[g.n - 37:] == 0).all()  # isolated vertices do not move
+
+
+@pytest.mark.parametrize("prec,tol", [(G.GILA_FP32, 2e-5), (G.GILA_FP64, 1e-13)],
+                         ids=["fp32", "fp64"])
+@pytest.mark.parametrize("tv", [0, 1200, 960], ids=["tv_default", "tv1200", "tv960"])
+def test_bank_spread_only_reorders(prec, tol, tv):
+    """The blocked path with each segment's ids ordered for distinct banks
+    and with them in ascending order sums the same terms: displacements
+    agree to rounding (a lost or repeated id would move them by a whole
+    term). n = 30,000 gives tiles of 15,000 (FP32) or about 10,000 (FP64)
+    positions by default, 1,200 (tile starts at multiples of the bank
+    period) and 938 (starts off it)."""
+    torch = _torch()
+    g = I.barabasi_albert(30000, 3, 17)
+    pos = I.uniform_positions(g.n, 18)
+    t = 1e30  # uncapped: the displacement is the force
+    out = []
+    for spread in (0, -1):
+        with G.Graph.from_inputs(g) as h:
+            G.gila_graph_tune(h.handle, tiled=1, tile_vertices=tv, bank_spread=spread)
+            assert G.gila_graph_get_tuning(h.handle)["bank_spread"] == (1 if spread == 0 else -1)
+            p_in = torch.tensor(pos, dtype=_dt(prec), device="cuda")
+            p_out, disp = torch.empty_like(p_in), torch.empty_like(p_in)
+            G.gila_layout_step(h.handle, G.params(k=3, precision=prec), t, p_in, p_out, disp)
+            torch.cuda.synchronize()
+            out.append(disp.double().cpu().numpy())
+    scale = np.abs(out[1]).max()
+    assert np.abs(out[0] - out[1]).max() <= tol * scale
 
 
 @pytest.mark.parametrize("tiled", [0, 1], ids=["plain", "blocked"])
