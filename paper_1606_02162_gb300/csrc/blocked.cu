@@ -3,8 +3,10 @@
 //
 // Tiles: tile j holds the positions of ids [j tv, (j+1) tv). Ranges: rows are
 // cut into contiguous ranges of about equal total list length. Block (j, r)
-// holds, for every row u of range r in order, the entries of u's sorted
-// k-hop row that fall in tile j; block starts are 16-byte aligned. One CTA
+// holds, for every row u of range r in order, the entries of u's k-hop row
+// that fall in tile j, in an order chosen so that the lanes of one gather
+// read distinct shared-memory banks (block_spread_kernel); block starts are
+// 16-byte aligned. One CTA
 // per block loads tile j and the block's row directory into shared memory;
 // each warp streams an equal, aligned stripe of the block with 16-byte id
 // loads and gathers positions from the tile. A row is summed in stripe

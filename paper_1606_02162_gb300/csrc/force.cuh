@@ -128,6 +128,14 @@ __device__ __forceinline__ float rsqrt_fast(float x)
     return r;
 }
 
+// Reciprocal, one approximate MUFU operation (denormals flushed; +inf at 0).
+__device__ __forceinline__ float rcp_fast(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Position of id v for a kernel reading from `SRC`.
 template <class T, int SRC>
 struct PosSource {
@@ -153,8 +161,8 @@ struct PosSource {
 
 // Repulsion of one k-hop entry v on u (Section 3.1 with the repelling set
 // of Section 4.5): adds c (x_u - x_v) with c = d^2 / delta^(q+1). For
-// Fruchterman-Reingold (q = 1) in FP32 that is d^2 * rsqrt(r^2)^2: one MUFU
-// and two multiplies, no divide. A pair at distance 0 adds nothing. With
+// Fruchterman-Reingold (q = 1) in FP32 that is d^2 * rcp(r^2): one MUFU
+// and a multiply, no divide. A pair at distance 0 adds nothing. With
 // UNSCALED the factor d^2 is left out (the caller multiplies the row's sum
 // by it once). With WEIGHTED the term is multiplied by wt[v], the repulsion
 // weight of the repelling vertex (Section 4.6).
@@ -172,11 +180,11 @@ struct Rep {
     {
         const P2 pv = src(v);
         const T dx = xu - pv.x, dy = yu - pv.y;
-        const T r2 = dx * dx + dy * dy;
         T c;
         if (MODEL == kFR) {
-            c = UNSCALED ? rep_fr1(r2) : rep_fr(d2, r2);
+            c = UNSCALED ? rep_fr1(dx, dy) : rep_fr(d2, dx * dx + dy * dy);
         } else {
+            const T r2 = dx * dx + dy * dy;
             c = T(0);
             if (r2 > T(0)) {
                 const T dl = sqrt(r2);
@@ -189,22 +197,25 @@ struct Rep {
 
     __device__ __forceinline__ static float rep_fr(float d2, float r2)
     {
-        const float r = rsqrt_fast(r2);
-        return r2 > 0.0f ? d2 * (r * r) : 0.0f;
+        return r2 > 0.0f ? d2 * rcp_fast(r2) : 0.0f;
     }
     __device__ __forceinline__ static double rep_fr(double d2, double r2)
     {
         return r2 > 0.0 ? d2 * rcp_newton(r2) : 0.0;
     }
-    // 1 / r^2. At r^2 = 0 the approximate rsqrt gives +inf; the clamp turns
-    // that into a finite factor, which then multiplies dx = dy = 0 exactly.
-    __device__ __forceinline__ static float rep_fr1(float r2)
+    // 1 / r^2 in FP32: one approximate reciprocal of r^2 + 2^-100. The added
+    // 2^-100 is less than half an ulp of any r^2 >= 2^-75 (far below any
+    // distance of a placement), so it changes such an r^2 by at most its
+    // rounding; at r^2 = 0
+    // (coincident vertices) it keeps the factor finite (2^100), and the
+    // factor then multiplies dx = dy = 0 exactly: the pair adds nothing.
+    __device__ __forceinline__ static float rep_fr1(float dx, float dy)
     {
-        const float r = rsqrt_fast(r2);
-        return fminf(r * r, 3.0e38f);
+        return rcp_fast(fmaf(dx, dx, fmaf(dy, dy, 0x1p-100f)));
     }
-    __device__ __forceinline__ static double rep_fr1(double r2)
+    __device__ __forceinline__ static double rep_fr1(double dx, double dy)
     {
+        const double r2 = dx * dx + dy * dy;
         return r2 > 0.0 ? rcp_newton(r2) : 0.0;
     }
 };
