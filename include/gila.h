@@ -126,8 +126,7 @@ typedef struct gila_tuning {
     int32_t bank_spread;   /* blocked path: 0 or 1 (default on) orders each row's entries of
                               a tile so that the lanes of one shared-memory gather read
                               distinct banks where the entries allow; -1 keeps ascending
-                              id order. The plan then needs a temporary copy of the k-hop
-                              lists (ascending order if it cannot be allocated) */
+                              id order */
 } gila_tuning;
 
 typedef struct gila_graph gila_graph;

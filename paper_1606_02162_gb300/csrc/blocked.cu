@@ -5,16 +5,18 @@
 // cut into contiguous ranges of about equal total list length. Block (j, r)
 // holds, for every row u of range r in order, the entries of u's k-hop row
 // that fall in tile j, in an order chosen so that the lanes of one gather
-// read distinct shared-memory banks (block_spread_kernel); block starts are
-// 16-byte aligned. One CTA
-// per block loads tile j and the block's row directory into shared memory;
-// each warp streams an equal, aligned stripe of the block with 16-byte id
-// loads and gathers positions from the tile. A row is summed in stripe
-// order by the warps that hold it (the usual case: one warp), combined in
-// warp order, and stored as the row's partial for tile j. A second kernel
-// adds each row's tile partials in tile order, adds its attraction terms
-// and applies the capped move. Every partial has a fixed place in a fixed
-// order, so results do not depend on scheduling.
+// read distinct shared-memory banks; block starts are 16-byte aligned. One
+// CTA per block loads tile j and the block's row directory into shared
+// memory; each thread takes an equal, 4-aligned share of the block's
+// entries (stored so that a warp's 16-byte id loads of one step are
+// contiguous), gathers positions from the tile and sums them row by row on
+// its own. A row wholly inside a share is stored by its thread; the parts of
+// rows cut by share bounds are added by a segmented scan across the warp,
+// and rows cut by warp bounds in warp order, then stored as the row's
+// partial for tile j. A second kernel adds each row's tile partials in tile
+// order, adds its attraction terms and applies the capped move. Every
+// partial has a fixed place and a fixed order of additions, so results do
+// not depend on scheduling.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -43,9 +45,9 @@ constexpr uint64_t kTestWaitNs = 1000000ull;   // the bound while the wait test 
 __device__ int g_tile_wait_failed = 0;
 
 struct BlockedArgs {
-    const uint32_t* tk;        // ids in block order
-    const int64_t* toff;       // nt n: start of (tile j, row u) in tk
-    const int64_t* blk;        // 2 nt nr: start and length of block (j, r)
+    const uint32_t* tk;        // ids, block by block, each block in share storage order
+    const int64_t* toff;       // nt n: start of segment (tile j, row u) within its block
+    const int64_t* blk;        // 2 nt nr: first slot in tk and entry count of block (j, r)
     const int32_t* range_start;
     int64_t n;
     int32_t nt, tv, nr;
@@ -86,6 +88,22 @@ __device__ __forceinline__ void store_cell(typename V2<T>::type* c, const Acc<T,
     }
 }
 
+// Entries of block (j, r) per thread: thread t takes [lane_start(L, t),
+// lane_start(L, t + 1)), 4-aligned; in storage every thread has lane_len(L)
+// slots (a multiple of 4, at least its share), laid out per warp step-major:
+// the k-th group of four slots of lane l of warp w is at
+// (w 32 lane_len + 128 k + 4 l) from the block's start, so that a warp's
+// 16-byte loads of one step are one contiguous 512-byte run.
+__host__ __device__ __forceinline__ int32_t lane_start(int32_t L, int t)
+{
+    return (t >= kBThreads) ? L : (int32_t)(((int64_t)L * t / kBThreads) & ~int64_t(3));
+}
+__host__ __device__ __forceinline__ int32_t lane_len(int32_t L)
+{
+    // a share is at most L / kBThreads + 4 entries (4-aligned cuts)
+    return (L == 0) ? 0 : ((L / kBThreads + 7) & ~3);
+}
+
 template <class T, int MODEL, bool COMP>
 __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs A)
 {
@@ -100,7 +118,7 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
     const int j = blockIdx.x / A.nr, r = blockIdx.x % A.nr;
     const int64_t u0 = A.range_start[r], u1 = A.range_start[r + 1];
     const int nrows = (int)(u1 - u0);
-    const int64_t bs = A.blk[2 * (int64_t)blockIdx.x];
+    const int64_t bsp = A.blk[2 * (int64_t)blockIdx.x];  // the block's first slot in tk
     // a block holds at most kMaxRows segments of at most tv entries: < 2^31
     const int32_t L = (int32_t)A.blk[2 * (int64_t)blockIdx.x + 1];
     const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos);
@@ -118,10 +136,10 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                      &tile_bar);
         if ((size_t)tn * sizeof(P2) != bytes) tile[tn - 1] = pos[tb + tn - 1];
     }
-    // meanwhile: the row directory and zero partials for rows with no
-    // entries in this tile
+    // meanwhile: the row directory (segment starts within the block) and
+    // zero partials for rows with no entries in this tile
     for (int i = threadIdx.x; i < nrows; i += kBThreads) {
-        D[i] = (int32_t)(A.toff[(int64_t)j * A.n + u0 + i] - bs);
+        D[i] = (int32_t)A.toff[(int64_t)j * A.n + u0 + i];
         P2* c = cell_ptr<T>(A.part, A.n, j, u0 + i);
         P2 z;
         z.x = T(0);
@@ -146,134 +164,200 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
     if (!tile_ok) return;  // uniform across the CTA
     mbar_wait(&tile_bar, 0, A.wait_ns);  // completed: acquires the tile for this thread
 
-    Rep<T, MODEL, COMP, kSrcShared, true> f;  // d^2 is applied when the partials are added
-    f.src.set_shared(tile, (uint32_t)tb);
-    f.d2 = T(1);
-    f.q = A.q;
-    // this warp's stripe [a, b) of the block, 4-entry aligned
-    const int32_t a = (int32_t)(((int64_t)L * warp / kBWarps) & ~int64_t(3));
-    const int32_t b =
-        (warp == kBWarps - 1) ? L : (int32_t)(((int64_t)L * (warp + 1) / kBWarps) & ~int64_t(3));
-    if (a < b) {
-        // first row: the last i with D[i] <= a
+    if (L > 0) {
+        Rep<T, MODEL, COMP, kSrcShared, true> f;  // d^2 is applied when the partials are added
+        f.src.set_shared(tile, (uint32_t)tb);
+        f.d2 = T(1);
+        f.q = A.q;
+        // this thread's entries [a, b) (a < L), their storage, and the row of a
+        const int32_t a = lane_start(L, threadIdx.x), b = lane_start(L, threadIdx.x + 1);
+        const int32_t m4 = lane_len(L);
+        const uint4* ids4 =
+            reinterpret_cast<const uint4*>(A.tk + bsp + (int64_t)warp * 32 * m4) + lane;
         int lo = 0, hi = nrows;
-        while (lo < hi) {
+        while (lo < hi) {  // the last i with D[i] <= a
             const int mid = (lo + hi + 1) >> 1;
             if (D[mid] <= a) lo = mid; else hi = mid - 1;
         }
         int ri = lo;
-        while (ri < nrows && D[ri + 1] <= a) ++ri;  // skip empty rows at a
-        int32_t rs = D[ri], re = D[ri + 1];
+        while (D[ri + 1] <= a) ++ri;  // skip empty rows at a (a < L = D[nrows])
+        const int ra = ri;  // the first row
+        // it continues the previous share's last row (that share holds its
+        // earlier entries, or is empty and ends in the row that holds a)
+        const bool open_left =
+            D[ra] < a || (threadIdx.x > 0 && lane_start(L, threadIdx.x - 1) == a);
+        int32_t re = D[ri + 1];
+        // the next nonempty row and its own position, fetched one row ahead
+        auto next_row = [&](int i) {
+            int x = i + 1;
+            while (x < nrows && D[x + 1] == D[x]) ++x;
+            return x < nrows ? x : i;
+        };
+        int nx = next_row(ri);
         P2 xr = pos[u0 + ri];
-        // the next row's own position is fetched one row ahead
-        P2 xn = pos[u0 + (ri + 1 < nrows ? ri + 1 : ri)];
-        Acc<T, COMP> acc;
-        const uint4* ids4 = reinterpret_cast<const uint4*>(A.tk + bs);
-        auto finalize = [&](bool started_before, int row) {
-            acc.group_reduce(32);
-            if (lane == 0) {
-                if (started_before) {
-                    head[warp].row = row;
-                    head[warp].v[0] = acc.sx;
-                    head[warp].v[1] = acc.sy;
-                    head[warp].v[2] = acc.cx;
-                    head[warp].v[3] = acc.cy;
-                } else {
-                    store_cell<T, COMP>(cell_ptr<T>(A.part, A.n, j, u0 + row), acc);
-                }
+        P2 xn = pos[u0 + nx];
+        f.xu = xr.x;
+        f.yu = xr.y;
+        Acc<T, COMP> acc, first;
+        bool in_first = true;
+        // the current row is complete: the first row's sum is kept for the
+        // warp's scan; a later row lies wholly in [a, b) and is stored
+        auto close_row = [&]() {
+            if (in_first) {
+                first = acc;
+                in_first = false;
+            } else {
+                store_cell<T, COMP>(cell_ptr<T>(A.part, A.n, j, u0 + ri), acc);
             }
             acc = Acc<T, COMP>();
+            ri = nx;
+            re = D[ri + 1];
+            xr = xn;
+            f.xu = xr.x;
+            f.yu = xr.y;
+            nx = next_row(ri);
+            xn = pos[u0 + nx];
         };
-        bool done = false;
-        f.xu = xr.x;  // the row's own position, set again only when the row changes
-        f.yu = xr.y;
+        int32_t lim = (re < b) ? re : b;
         // 16-byte id loads run kRing steps ahead (four, three with the
-        // compensated sums, which need the registers): each of the kRing
-        // unrolled steps below consumes its own ring register and refills
-        // it, so the ring needs no register moves
+        // compensated sums, which need the registers); each unrolled step
+        // consumes its own ring register and refills it: no register moves
         constexpr int kRing = COMP ? 3 : 4;
-        auto load_step = [&](int32_t base) {
-            const int32_t p0 = base + 4 * lane;
-            return (p0 < b) ? ld_ids4(ids4 + (p0 >> 2)) : make_uint4(0, 0, 0, 0);
-        };
+        const int nsteps = m4 >> 2;  // the same for every thread of the block
         uint4 ring[kRing];
 #pragma unroll
-        for (int st = 0; st < kRing; ++st) ring[st] = load_step(a + 128 * st);
-        for (int32_t base = a; base < b && !done; base += 128 * kRing) {
+        for (int st = 0; st < kRing; ++st)
+            ring[st] = (st < nsteps) ? ld_ids4(ids4 + 32 * st) : make_uint4(0, 0, 0, 0);
+        int32_t p = a;
+        for (int k0 = 0; k0 < nsteps; k0 += kRing) {
 #pragma unroll
             for (int st = 0; st < kRing; ++st) {
-                const int32_t sb = base + 128 * st;
-                if (sb >= b || done) break;  // warp-uniform
+                const int k = k0 + st;
+                if (k >= nsteps) break;  // uniform
                 const uint4 c = ring[st];
-                ring[st] = load_step(sb + 128 * kRing);
+                ring[st] = (k + kRing < nsteps) ? ld_ids4(ids4 + 32 * (k + kRing))
+                                                : make_uint4(0, 0, 0, 0);
                 const uint32_t ids[4] = {c.x, c.y, c.z, c.w};
-                const int32_t p0 = sb + 4 * lane;
-                const int32_t lim = (sb + 128 < b) ? sb + 128 : b;
-                if (re > lim) {  // the whole step lies in row ri (warp-uniform)
-                    if (sb + 128 <= b) {
-                        if (COMP) {
-                            // compensated mode: the step's four terms summed
-                            // plainly, the partial added with its error term
-                            Acc<T, false> s4;
-                            f(ids[0], s4);
-                            f(ids[1], s4);
-                            f(ids[2], s4);
-                            f(ids[3], s4);
-                            acc.merge(s4.sx, s4.sy, T(0), T(0));
-                        } else {
-                            f(ids[0], acc);
-                            f(ids[1], acc);
-                            f(ids[2], acc);
-                            f(ids[3], acc);
-                        }
+                if (p + 4 <= lim) {  // all four in the current row
+                    if (COMP) {
+                        // compensated mode: the step's four terms summed
+                        // plainly, the partial added with its error term
+                        Acc<T, false> s4;
+                        f(ids[0], s4);
+                        f(ids[1], s4);
+                        f(ids[2], s4);
+                        f(ids[3], s4);
+                        acc.merge(s4.sx, s4.sy, T(0), T(0));
                     } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            if (p0 + q < b) f(ids[q], acc);
+                        f(ids[0], acc);
+                        f(ids[1], acc);
+                        f(ids[2], acc);
+                        f(ids[3], acc);
                     }
-                    continue;
-                }
-                // rows ri, ri + 1, ... end inside this step
-                for (;;) {
+                } else if (p < b) {  // a row ends in this step, or the share does
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int32_t p = p0 + q;
-                        if (p >= rs && p < re && p < b) f(ids[q], acc);
+                        const int32_t pq = p + q;
+                        if (pq >= b) break;
+                        while (pq >= re) close_row();
+                        f(ids[q], acc);
                     }
-                    if (re > lim) break;  // this row goes on in the next step
-                    finalize(rs < a, ri);
-                    const int prev = ri;
-                    ++ri;
-                    while (ri < nrows && D[ri + 1] == D[ri]) ++ri;  // empty rows stay zero
-                    if (ri >= nrows || D[ri] >= b) {
-                        done = true;
-                        break;
-                    }
-                    rs = D[ri];
-                    re = D[ri + 1];
-                    xr = (ri == prev + 1) ? xn : pos[u0 + ri];
-                    xn = pos[u0 + (ri + 1 < nrows ? ri + 1 : ri)];
-                    f.xu = xr.x;
-                    f.yu = xr.y;
+                    lim = (re < b) ? re : b;
                 }
+                p += 4;
             }
         }
-        if (!done && ri < nrows && re > b) {
-            // the stripe ends inside row ri: its part goes to a slot
-            acc.group_reduce(32);
-            if (lane == 0) {
-                Slot<T, COMP>& sl = (rs < a) ? head[warp] : tail[warp];
-                sl.row = ri;
-                sl.v[0] = acc.sx;
-                sl.v[1] = acc.sy;
-                sl.v[2] = acc.cx;
-                sl.v[3] = acc.cy;
+        const bool has_b = !in_first;  // the share ends in a later row than it began
+        if (in_first) first = acc;
+        const int orow = has_b ? ri : ra;  // the row the share ends in
+        const bool open_right = re > b;
+
+        // Rows cut by share bounds, in lane order: element A (row ra, sum
+        // first) and, with has_b, element B (row ri, sum acc). A segmented
+        // scan of the warp's elements (A continues the previous lane's last
+        // row, B always starts a run) gives each run's sum where it ends.
+        Acc<T, COMP> x = has_b ? acc : first;
+        const int prev_orow = __shfl_up_sync(kFull, orow, 1);
+        const bool cont = lane > 0 && prev_orow == ra;
+        const bool start = has_b || !cont;
+        const unsigned starts = __ballot_sync(kFull, start);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            // the run of lane - o reaches this lane when no run starts in
+            // lanes (lane - o, lane]
+            const unsigned span = (lane >= o) ? (((1u << o) - 1u) << (lane - o + 1)) : 0u;
+            const T sx = __shfl_up_sync(kFull, x.sx, o);
+            const T sy = __shfl_up_sync(kFull, x.sy, o);
+            const T cx = COMP ? __shfl_up_sync(kFull, x.cx, o) : T(0);
+            const T cy = COMP ? __shfl_up_sync(kFull, x.cy, o) : T(0);
+            if (lane >= o && (starts & span) == 0) {
+                Acc<T, COMP> y;
+                y.sx = sx;
+                y.sy = sy;
+                y.cx = cx;
+                y.cy = cy;
+                y.merge(x.sx, x.sy, x.cx, x.cy);
+                x = y;
             }
+        }
+        // the sum of the run that reaches into A of a lane with B
+        Acc<T, COMP> carry;
+        {
+            const T sx = __shfl_up_sync(kFull, x.sx, 1);
+            const T sy = __shfl_up_sync(kFull, x.sy, 1);
+            const T cx = COMP ? __shfl_up_sync(kFull, x.cx, 1) : T(0);
+            const T cy = COMP ? __shfl_up_sync(kFull, x.cy, 1) : T(0);
+            if (cont) {
+                carry.sx = sx;
+                carry.sy = sy;
+                carry.cx = cx;
+                carry.cy = cy;
+            }
+        }
+        // runs that include lane 0's A belong to a row begun before the
+        // warp's entries when lane 0's first row is open on the left; such a
+        // run, and one running past the warp's last entry, goes to the
+        // warp's slots, every other run to its cell
+        const bool lane0_open = __shfl_sync(kFull, open_left, 0);
+        const bool lane0_has_b = __shfl_sync(kFull, has_b, 0);
+        const bool last_open = __shfl_sync(kFull, open_right, 31);
+        const unsigned below = starts & ((2u << lane) - 1u) & ~1u;  // starts in lanes 1..lane
+        auto put = [&](int row, const Acc<T, COMP>& v, bool from_lane0, bool past_end) {
+            if (from_lane0 && lane0_open) {
+                Slot<T, COMP>& sl = head[warp];
+                sl.row = row;
+                sl.v[0] = v.sx;
+                sl.v[1] = v.sy;
+                sl.v[2] = v.cx;
+                sl.v[3] = v.cy;
+            } else if (past_end) {
+                Slot<T, COMP>& sl = tail[warp];
+                sl.row = row;
+                sl.v[0] = v.sx;
+                sl.v[1] = v.sy;
+                sl.v[2] = v.cx;
+                sl.v[3] = v.cy;
+            } else {
+                store_cell<T, COMP>(cell_ptr<T>(A.part, A.n, j, u0 + row), v);
+            }
+        };
+        if (has_b) {
+            // A's run ends here: the carry plus this lane's first row
+            carry.merge(first.sx, first.sy, first.cx, first.cy);
+            const bool a_from0 =
+                (lane == 0) || (cont && !lane0_has_b && (below & ~(1u << lane)) == 0);
+            put(ra, carry, a_from0, false);
+        }
+        const int next_ra = __shfl_down_sync(kFull, ra, 1);
+        const bool ends_here = (lane == 31) || next_ra != orow;
+        if (ends_here) {
+            const bool o_from0 = !has_b && !lane0_has_b && below == 0;
+            put(orow, x, o_from0, lane == 31 && last_open);
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        // rows cut by stripe bounds: add their slots in warp order
+        // rows cut by warp bounds: add their slots in warp order
         int cur = -1;
         Acc<T, COMP> sum;
         auto flush = [&]() {
@@ -545,44 +629,37 @@ __global__ void seglen_kernel(int64_t n, const int64_t* __restrict__ krow,
     len[i] = hi - lo;
 }
 
-// Copy every (tile, row) segment to its place in the block layout; one warp
-// per segment.
-__global__ void block_copy_kernel(int64_t n, const int64_t* __restrict__ krow,
-                                  const uint32_t* __restrict__ kcol, int nt, int tv,
-                                  const int64_t* __restrict__ toff, uint32_t* __restrict__ tk)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= n * nt) return;
-    int64_t lo, hi;
-    seg_bounds(krow, kcol, i % n, (int)(i / n), nt, tv, &lo, &hi);
-    uint32_t* dst = tk + toff[i];
-    for (int64_t e = lo + lane; e < hi; e += 32) dst[e - lo] = kcol[e];
-}
-
-// The same copy, with each segment's ids ordered for blocked_kernel's
-// shared-memory gathers. One gather of a warp is served in groups of G
-// lanes (G = 128 bytes / position size: 16 for float2, 8 for double2), one
+// Copy every (tile, row) segment into its block's share storage: entry p of
+// the block, held by the share of thread t (s = p - lane_start(L, t)), goes
+// to slot (t / 32) 32 lane_len(L) + 128 (s / 4) + 4 (t % 32) + s % 4.
+//
+// With SPREAD each segment's ids are also ordered for blocked_kernel's
+// shared-memory gathers. A warp's gather is served in groups of G lanes
+// (G = 128 bytes / position size: 16 for float2, 8 for double2), one
 // wavefront per group when the group's tile offsets are distinct modulo G
-// (distinct banks), one more per repeat otherwise; in ascending id order
-// the residues fall at random and a 16-lane group takes about three. A
-// row's sum does not depend on the order of its entries (up to rounding),
-// so every group of slots that one gather reads (the positions p of a
-// stripe step with equal p mod 4, in one half of the step for float2, one
-// quarter for double2) takes one id of each residue while all G residues
-// have ids left, otherwise ids of distinct residues, those with most ids
-// left first. Each gather reads one segment only (a step that holds
-// several rows gathers once per row), so segments are ordered
-// independently. One warp per segment: count residues, scatter the ids by
-// residue into scratch (stable), deal them to the slots.
-template <int G>
-__global__ void __launch_bounds__(256) block_spread_kernel(
+// (distinct banks), one more per repeat; in ascending id order the residues
+// fall at random and a 16-lane group takes about three. In one gather the
+// lanes of a group read entry s of their own shares, so entry s of thread t
+// aims at residue (t + s) mod G, distinct across the group for every s. A
+// row's sum does not depend on the order of its entries (up to rounding)
+// and a segment is one row, so its ids are dealt to its entries: each entry
+// takes an id of its target residue while one is left (lanes in order),
+// else one of the nearest residue above it (cyclically) that has ids left.
+// One warp per segment, through shared memory by chunks of at most
+// kSpreadChunk entries: count the chunk's residues, group its ids by residue
+// (stable), deal them 32 entries at a time.
+constexpr int kSpreadWarps = 4;
+constexpr int kSpreadChunk = 1024;
+
+template <int G, bool SPREAD>
+__global__ void __launch_bounds__(kSpreadWarps * 32) block_layout_kernel(
     int64_t n, const int64_t* __restrict__ krow, const uint32_t* __restrict__ kcol, int nt,
     int tv, const int64_t* __restrict__ toff, const int64_t* __restrict__ blk,
-    const int32_t* __restrict__ range_start, int nr, uint32_t* __restrict__ scratch,
-    uint32_t* __restrict__ tk)
+    const int32_t* __restrict__ range_start, int nr, uint32_t* __restrict__ tk)
 {
-    __shared__ int s_run[8][G];
+    __shared__ uint32_t s_in[kSpreadWarps][kSpreadChunk];  // the chunk's ids by residue
+    __shared__ int s_run[kSpreadWarps][G];
+    __shared__ int s_ask[kSpreadWarps][G];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n * nt) return;  // warp-uniform
@@ -592,92 +669,115 @@ __global__ void __launch_bounds__(256) block_spread_kernel(
     seg_bounds(krow, kcol, u, j, nt, tv, &lo, &hi);
     if (hi == lo) return;
     const uint32_t tb = (uint32_t)j * (uint32_t)tv;
-    // the block (j, r) that holds the segment, and the segment's place in it
+    // the block (j, r) that holds the segment
     int ra = 0, rb = nr - 1;
     while (ra < rb) {
         const int mid = (ra + rb + 1) >> 1;
         if (range_start[mid] <= u) ra = mid; else rb = mid - 1;
     }
-    const int64_t bs = blk[2 * ((int64_t)j * nr + ra)];
-    const int64_t L = blk[2 * ((int64_t)j * nr + ra) + 1];
-    const int64_t S0 = toff[i] - bs, S1 = S0 + (hi - lo);
-    uint32_t* dst = tk + toff[i];
-    uint32_t* scr = scratch + toff[i];
-
-    // residue counts and their exclusive prefix (lane c holds residue c)
-    if (lane < G) s_run[wl][lane] = 0;
-    __syncwarp();
-    for (int64_t e = lo + lane; e < hi; e += 32) atomicAdd(&s_run[wl][(kcol[e] - tb) % G], 1);
-    __syncwarp();
-    const int cnt = (lane < G) ? s_run[wl][lane] : 0;
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
+    const int64_t bsp = blk[2 * ((int64_t)j * nr + ra)];
+    const int32_t L = (int32_t)blk[2 * ((int64_t)j * nr + ra) + 1];
+    const int32_t m4 = lane_len(L);
+    const int32_t S0 = (int32_t)toff[i], S1 = S0 + (int32_t)(hi - lo);
+    // the share holding entry p (t follows p, which only grows) and the slot
+    int t = (int)((int64_t)S0 * kBThreads / L);
+    auto place = [&](int32_t p, int32_t* s) -> int64_t {
+        while (t > 0 && lane_start(L, t) > p) --t;
+        while (t < kBThreads - 1 && lane_start(L, t + 1) <= p) ++t;
+        *s = p - lane_start(L, t);
+        return bsp + (int64_t)(t >> 5) * 32 * m4 + 128 * (*s >> 2) + 4 * (t & 31) + (*s & 3);
+    };
+    if (!SPREAD) {
+        for (int32_t p = S0 + lane; p < S1; p += 32) {
+            int32_t sidx;
+            const int64_t d = place(p, &sidx);
+            tk[d] = kcol[lo + (p - S0)];
+        }
+        return;
     }
-    const int cstart = incl - cnt;
-    __syncwarp();
-    if (lane < G) s_run[wl][lane] = cstart;
-    __syncwarp();
-    // stable scatter by residue
-    for (int64_t base = lo; base < hi; base += 32) {
-        const int64_t e = base + lane;
-        const bool act = e < hi;
-        const uint32_t id = act ? kcol[e] : 0u;
-        const int c = act ? (int)((id - tb) % G) : G + lane;
-        const unsigned m = __match_any_sync(0xffffffffu, c);
-        const int o = act ? s_run[wl][c] + __popc(m & ((1u << lane) - 1u)) : 0;
+    uint32_t* in = s_in[wl];
+    int* run = s_run[wl];
+    int* ask = s_ask[wl];
+    for (int32_t c0 = S0; c0 < S1; c0 += kSpreadChunk) {
+        const int len = (S1 - c0 < kSpreadChunk) ? S1 - c0 : kSpreadChunk;
+        const uint32_t* src = kcol + lo + (c0 - S0);
+        // residue counts of the chunk and their exclusive prefix (lane c: residue c)
+        if (lane < G) run[lane] = 0;
         __syncwarp();
-        if (act && lane == 31 - __clz(m)) s_run[wl][c] += __popc(m);
+        for (int e = lane; e < len; e += 32) atomicAdd(&run[(src[e] - tb) % G], 1);
         __syncwarp();
-        if (act) scr[o] = id;
-    }
-    __syncwarp();  // orders the scratch writes before the other lanes read them
-
-    int rem = cnt, used = 0;
-    auto deal = [&](int64_t pf, int g) {
-        // g slots at pf, pf + 4, ...: distinct residues, most ids left first
-        for (int filled = 0; filled < g;) {
-            const bool avail = lane < G && rem > 0;
-            const int nz = __popc(__ballot_sync(0xffffffffu, avail));
-            if (nz == 0) break;  // cannot happen: the slots left equal the ids left
-            const int take = (nz < g - filled) ? nz : g - filled;
-            int rank = lane;  // all G residues give one id: any order
-            if (take < G) {
-                rank = 0;
+        const int cnt = (lane < G) ? run[lane] : 0;
+        int incl = cnt;
 #pragma unroll
-                for (int k = 0; k < G; ++k) {
-                    const int rk = __shfl_sync(0xffffffffu, rem, k);
-                    rank += (rk > rem || (rk == rem && k < lane)) ? 1 : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int cstart = incl - cnt;
+        __syncwarp();
+        if (lane < G) run[lane] = cstart;
+        __syncwarp();
+        // stable grouping by residue
+        for (int e0 = 0; e0 < len; e0 += 32) {
+            const int e = e0 + lane;
+            const bool act = e < len;
+            const uint32_t id = act ? src[e] : 0u;
+            const int c = act ? (int)((id - tb) % G) : G + lane;
+            const unsigned m = __match_any_sync(kFull, c);
+            const int o = act ? run[c] + __popc(m & ((1u << lane) - 1u)) : 0;
+            __syncwarp();
+            if (act && lane == 31 - __clz(m)) run[c] += __popc(m);
+            __syncwarp();
+            if (act) in[o] = id;
+        }
+        __syncwarp();  // the grouped ids are visible to the whole warp
+
+        // deal: lane c < G keeps residue c's ids left and taken
+        int rem = cnt, used = 0;
+        for (int e0 = 0; e0 < len; e0 += 32) {
+            const int e = e0 + lane;
+            const bool act = e < len;
+            int32_t sidx = 0;
+            const int64_t d = act ? place(c0 + e, &sidx) : 0;
+            const int want = act ? (int)(((t % G) + sidx) % G) : 0;
+            // the target residue for as many lanes as it has ids left, in lane order
+            const unsigned m = __match_any_sync(kFull, act ? want : G + lane);
+            const int rank = __popc(m & ((1u << lane) - 1u));
+            const int left = __shfl_sync(kFull, rem, want);
+            const int base = __shfl_sync(kFull, cstart + used, want);
+            const bool got = act && rank < left;
+            uint32_t id = got ? in[base + rank] : 0u;
+            // residue c's lane takes off the lanes that asked for c (at most rem)
+            if (lane < G) ask[lane] = 0;
+            __syncwarp();
+            if (act && rank == 0) ask[want] = __popc(m);
+            __syncwarp();
+            if (lane < G) {
+                const int give = (ask[lane] < rem) ? ask[lane] : rem;
+                rem -= give;
+                used += give;
+            }
+            // the others in lane order: the nearest residue at or above the
+            // target (cyclically) that has ids left
+            unsigned pend = __ballot_sync(kFull, act && !got);
+            while (pend) {
+                const int l = __ffs(pend) - 1;
+                const int wt = __shfl_sync(kFull, want, l);
+                const unsigned av = __ballot_sync(kFull, lane < G && rem > 0) & ((1u << G) - 1u);
+                if (av == 0) break;  // cannot happen: ids left equal entries left
+                const unsigned rot = ((av >> wt) | (av << (G - wt))) & ((1u << G) - 1u);
+                const int c = (wt + __ffs(rot) - 1) % G;
+                const int at = __shfl_sync(kFull, cstart + used, c);
+                if (lane == c) {
+                    --rem;
+                    ++used;
                 }
+                if (lane == l) id = in[at];
+                pend &= pend - 1;
             }
-            if (avail && rank < take) {
-                dst[pf - S0 + 4 * (filled + rank)] = scr[cstart + used];
-                ++used;
-                --rem;
-            }
-            filled += take;
+            if (act) tk[d] = id;
         }
-    };
-    // the stripes blocked_kernel cuts the block into
-    auto stripe_a = [&](int w) -> int64_t {
-        return (w >= kBWarps) ? L : ((L * w / kBWarps) & ~int64_t(3));
-    };
-    constexpr int kSpan = 4 * G;  // positions one G-lane group reads in one step
-    int w = (int)(S0 * kBWarps / L);  // S0 < L
-    for (int64_t cur = S0; cur < S1;) {
-        while (w > 0 && stripe_a(w) > cur) --w;
-        while (w < kBWarps - 1 && stripe_a(w + 1) <= cur) ++w;
-        const int64_t aw = stripe_a(w), bw = stripe_a(w + 1);
-        int64_t he = aw + (cur - aw) / kSpan * kSpan + kSpan;
-        if (he > bw) he = bw;
-        if (he > S1) he = S1;
-        for (int q = 0; q < 4; ++q) {
-            const int64_t pf = cur + ((q - (int)(cur & 3)) & 3);
-            if (pf < he) deal(pf, (int)((he - pf + 3) >> 2));
-        }
-        cur = he;
+        __syncwarp();  // the next chunk reuses the buffers
     }
 }
 
@@ -972,21 +1072,23 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
     }
     const std::vector<int32_t> rs = partition_rows(cost, total, ranges_target(g, nt));
     const int64_t nr = (int64_t)rs.size() - 1;
-    // block layout: (j, r) blocks in that order, starts aligned to 4 entries
+    // block layout: (j, r) blocks in that order, each in share storage
+    // (lane_len(L) slots per thread; block starts are multiples of 4 slots);
+    // segment starts within their block
     std::vector<int64_t> toff((size_t)cells), blk((size_t)(2 * nt * nr));
-    int64_t off = 0;
+    int64_t slots = 0;
     for (int64_t j = 0; j < nt; ++j)
         for (int64_t r = 0; r < nr; ++r) {
-            off = (off + 3) & ~int64_t(3);
-            const int64_t start = off;
+            int64_t off = 0;
             for (int64_t u = rs[(size_t)r]; u < rs[(size_t)r + 1]; ++u) {
                 toff[(size_t)(j * n + u)] = off;
                 off += len[(size_t)(j * n + u)];
             }
-            blk[(size_t)(2 * (j * nr + r))] = start;
-            blk[(size_t)(2 * (j * nr + r) + 1)] = off - start;
+            blk[(size_t)(2 * (j * nr + r))] = slots;
+            blk[(size_t)(2 * (j * nr + r) + 1)] = off;
+            slots += (int64_t)kBThreads * lane_len((int32_t)off);
         }
-    const int64_t tk_len = off + 4;
+    const int64_t tk_len = slots + 4;
     if ((s = ensure((void**)&P.toff, &P.toff_cap, sizeof(int64_t) * (size_t)cells)) != GILA_OK)
         return s;
     if ((s = ensure((void**)&P.blk, &P.blk_cap, sizeof(int64_t) * blk.size())) != GILA_OK) return s;
@@ -1001,37 +1103,24 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
                               cudaMemcpyHostToDevice, g->stream));
     GILA_CUDA(cudaMemcpyAsync(P.range_start, rs.data(), sizeof(int32_t) * rs.size(),
                               cudaMemcpyHostToDevice, g->stream));
-    // ids ordered for conflict-free gathers where scratch for the scatter
-    // can be had; in ascending order otherwise
-    void* scratch = nullptr;
-    if (g->tune.bank_spread >= 0 && cudaMalloc(&scratch, sizeof(uint32_t) * (size_t)tk_len) !=
-                                        cudaSuccess) {
-        cudaGetLastError();  // clear the failed allocation
-        scratch = nullptr;
-    }
-    const unsigned copy_blocks = (unsigned)((cells * 32 + 255) / 256);
-    if (scratch && esz == 8)
-        block_spread_kernel<16><<<copy_blocks, 256, 0, g->stream>>>(
-            n, g->krow, g->kcol, (int)nt, (int)tv, P.toff, P.blk, P.range_start, (int)nr,
-            (uint32_t*)scratch, P.tk);
-    else if (scratch)
-        block_spread_kernel<8><<<copy_blocks, 256, 0, g->stream>>>(
-            n, g->krow, g->kcol, (int)nt, (int)tv, P.toff, P.blk, P.range_start, (int)nr,
-            (uint32_t*)scratch, P.tk);
+    // ids ordered for conflict-free gathers, or in ascending order; the
+    // slots past each share's end stay zero
+    GILA_CUDA(cudaMemsetAsync(P.tk, 0, sizeof(uint32_t) * (size_t)tk_len, g->stream));
+    const unsigned lay_blocks = (unsigned)((cells + kSpreadWarps - 1) / kSpreadWarps);
+    if (g->tune.bank_spread >= 0 && esz == 8)
+        block_layout_kernel<16, true><<<lay_blocks, kSpreadWarps * 32, 0, g->stream>>>(
+            n, g->krow, g->kcol, (int)nt, (int)tv, P.toff, P.blk, P.range_start, (int)nr, P.tk);
+    else if (g->tune.bank_spread >= 0)
+        block_layout_kernel<8, true><<<lay_blocks, kSpreadWarps * 32, 0, g->stream>>>(
+            n, g->krow, g->kcol, (int)nt, (int)tv, P.toff, P.blk, P.range_start, (int)nr, P.tk);
     else
-        block_copy_kernel<<<copy_blocks, 256, 0, g->stream>>>(n, g->krow, g->kcol, (int)nt,
-                                                              (int)tv, P.toff, P.tk);
+        block_layout_kernel<16, false><<<lay_blocks, kSpreadWarps * 32, 0, g->stream>>>(
+            n, g->krow, g->kcol, (int)nt, (int)tv, P.toff, P.blk, P.range_start, (int)nr, P.tk);
     count_launch();
-    cudaError_t ce = cudaGetLastError();
+    GILA_CUDA(cudaGetLastError());
     // hubs of the adjacency for the combine kernel; synchronises, so the
     // host vectors above stay valid until their copies are done
-    if (ce == cudaSuccess) s = plan_hubs(g, P);
-    if (scratch) {
-        cudaStreamSynchronize(g->stream);
-        cudaFree(scratch);
-    }
-    if (ce != cudaSuccess) return cuda_fail(ce, "block copy");
-    if (s != GILA_OK) return s;
+    if ((s = plan_hubs(g, P)) != GILA_OK) return s;
     P.nt = (int32_t)nt;
     P.tv = (int32_t)tv;
     P.nr = (int32_t)nr;
