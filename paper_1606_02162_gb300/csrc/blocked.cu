@@ -39,6 +39,8 @@ constexpr uint32_t kBulkChunk = 32768;      // bytes per bulk copy instruction
 constexpr int64_t kBlockedMinNnz = 100000000;  // automatic mode: k-hop entries needed (tiles)
 constexpr uint64_t kWaitNs = 1000000000ull;  // bound on a tile wait (1 s, far above any copy)
 constexpr uint64_t kTestWaitNs = 1000000ull;   // the bound while the wait test hook is on
+constexpr int kPrefetch = 4;  // steps between an L2 prefetch of ids and their ring load (4, 12, 24
+                               // measured: 4 best; longer distances crowd L2)
 
 // Set when a CTA gave up waiting for its tile copy (the launch's partials
 // are then incomplete); read and cleared by blocked_tile_wait_failed().
@@ -228,8 +230,19 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
 #pragma unroll
         for (int st = 0; st < kRing; ++st)
             ring[st] = (st < nsteps) ? ld_ids4(ids4 + 32 * st) : make_uint4(0, 0, 0, 0);
+        // the warp's ids kPrefetch steps ahead of the ring are pulled into L2
+        // by one lane, kRing steps (kRing x 512 bytes) at a time
+        const uint4* warp_ids = ids4 - lane;
+        if (lane == 0)
+            for (int k = kRing; k < kPrefetch + kRing && k < nsteps; k += kRing)
+                bulk_prefetch_l2(warp_ids + 32 * k,
+                                 (uint32_t)(512 * ((nsteps - k < kRing) ? nsteps - k : kRing)));
         int32_t p = a;
         for (int k0 = 0; k0 < nsteps; k0 += kRing) {
+            const int kp = k0 + kPrefetch + kRing;
+            if (lane == 0 && kp < nsteps)
+                bulk_prefetch_l2(warp_ids + 32 * kp,
+                                 (uint32_t)(512 * ((nsteps - kp < kRing) ? nsteps - kp : kRing)));
 #pragma unroll
             for (int st = 0; st < kRing; ++st) {
                 const int k = k0 + st;
