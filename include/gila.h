@@ -114,9 +114,8 @@ typedef struct gila_tuning {
                               1, graphs whose row ranges touch narrow id windows get one
                               window per range, read in place) */
     int32_t tile_vertices; /* positions per tile; 0 = as many as fit in 200 KiB */
-    int32_t min_segment;   /* automatic mode tiles FP32 placements with at least 10^8 k-hop
-                              entries when nnz_khop / (n * tiles) >= this (48); FP64 only
-                              when tiled = 1 */
+    int32_t min_segment;   /* automatic mode tiles placements with at least 10^8 k-hop
+                              entries when nnz_khop / (n * tiles) >= this (48) */
     int32_t small_max;     /* untiled kernel: rows of length <= this use 8-lane groups (64) */
     int32_t warp_max;      /* ... rows <= this use one warp (8192) */
     int32_t block_max;     /* ... rows <= this use one block (65536); longer rows are chunked */

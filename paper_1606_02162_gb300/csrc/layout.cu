@@ -6,8 +6,8 @@
 //        + sum over edges (u,v)  of delta^p/d along (x_v - x_u)/delta
 //   x_u <- x_u + F(u) min(1, t/|F(u)|), all vertices at once.
 // Per entry of a k-hop row the kernels compute Delta = x_u - x_v and add
-// d^2/delta^(q+1) Delta (for q = 1 in FP32: d^2 rsqrt(r^2)^2 Delta, one MUFU
-// and no divide); a short second pass over u's adjacency row adds the
+// d^2/delta^(q+1) Delta (for q = 1 in FP32: d^2 rcp(r^2) Delta, one MUFU and
+// no divide); a short second pass over u's adjacency row adds the
 // attraction -delta^(p-1)/d Delta. The k-hop stream is the only large read.
 //
 // Work is split by row length into four classes, each a range of blocks
