@@ -39,6 +39,16 @@ constexpr uint32_t kBulkChunk = 32768;      // bytes per bulk copy instruction
 constexpr int64_t kBlockedMinNnz = 100000000;  // automatic mode: k-hop entries needed (tiles)
 constexpr uint64_t kWaitNs = 1000000000ull;  // bound on a tile wait (1 s, far above any copy)
 constexpr uint64_t kTestWaitNs = 1000000ull;   // the bound while the wait test hook is on
+// Every (tile j, row) segment is padded to a multiple of 4 entries with the
+// id j tv + tv, whose tile slot (one past the tile) holds a position so far
+// away that its term is exactly zero: in FP32 the factor rcp(r^2 + 2^-100)
+// of r^2 = 2e38 is below the smallest normal and flushes to 0; in FP64 r^2
+// = 1.48e308 flushes rcp to 0 the same way; the generic model cuts terms
+// beyond r^2 = 1e38 (FP32) or 1e300 (FP64). 0 * Delta then adds nothing.
+template <class T> struct FarSlot;
+template <> struct FarSlot<float> { static constexpr float v = 1.0e19f; };
+template <> struct FarSlot<double> { static constexpr double v = 8.6e153; };
+
 constexpr int kPrefetch = 4;  // steps between an L2 prefetch of ids and their ring load (4, 12, 24
                                // measured: 4 best; longer distances crowd L2)
 
@@ -112,7 +122,7 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
     using P2 = typename V2<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     P2* tile = reinterpret_cast<P2*>(smem_raw);
-    int32_t* D = reinterpret_cast<int32_t*>(smem_raw + (size_t)A.tv * sizeof(P2));
+    int32_t* D = reinterpret_cast<int32_t*>(smem_raw + (size_t)(A.tv + 1) * sizeof(P2));
     __shared__ Slot<T, COMP> head[kBWarps], tail[kBWarps];
     __shared__ __align__(8) uint64_t tile_bar;
     __shared__ int tile_ok;
@@ -137,6 +147,10 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
             bulk_g2s(smem_raw + o, src + o, (bytes - o < kBulkChunk) ? bytes - o : kBulkChunk,
                      &tile_bar);
         if ((size_t)tn * sizeof(P2) != bytes) tile[tn - 1] = pos[tb + tn - 1];
+        P2 far;  // the padding's slot, outside the copied range
+        far.x = FarSlot<T>::v;
+        far.y = FarSlot<T>::v;
+        tile[A.tv] = far;
     }
     // meanwhile: the row directory (segment starts within the block) and
     // zero partials for rows with no entries in this tile
@@ -220,7 +234,6 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
             nx = next_row(ri);
             xn = pos[u0 + nx];
         };
-        int32_t lim = (re < b) ? re : b;
         // 16-byte id loads run kRing steps ahead (four, three with the
         // compensated sums, which need the registers); each unrolled step
         // consumes its own ring register and refills it: no register moves
@@ -237,7 +250,29 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
             for (int k = kRing; k < kPrefetch + kRing && k < nsteps; k += kRing)
                 bulk_prefetch_l2(warp_ids + 32 * k,
                                  (uint32_t)(512 * ((nsteps - k < kRing) ? nsteps - k : kRing)));
+        // segments and shares are multiples of 4 entries: every step lies in
+        // one row, and rows change only between steps. A step before the
+        // current row's end (and the share's) goes straight to its four
+        // terms; a step where a row begins first closes the rows before it
+        int32_t lim = (re < b) ? re : b;
         int32_t p = a;
+        auto four = [&](const uint4 c) {
+            if (COMP) {
+                // compensated mode: the step's four terms summed plainly,
+                // the partial added with its error term
+                Acc<T, false> s4;
+                f(c.x, s4);
+                f(c.y, s4);
+                f(c.z, s4);
+                f(c.w, s4);
+                acc.merge(s4.sx, s4.sy, T(0), T(0));
+            } else {
+                f(c.x, acc);
+                f(c.y, acc);
+                f(c.z, acc);
+                f(c.w, acc);
+            }
+        };
         for (int k0 = 0; k0 < nsteps; k0 += kRing) {
             const int kp = k0 + kPrefetch + kRing;
             if (lane == 0 && kp < nsteps)
@@ -250,52 +285,20 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                 const uint4 c = ring[st];
                 ring[st] = (k + kRing < nsteps) ? ld_ids4(ids4 + 32 * (k + kRing))
                                                 : make_uint4(0, 0, 0, 0);
-                const uint32_t ids[4] = {c.x, c.y, c.z, c.w};
-                // FP64 (costly terms): the warp takes a step on the fast path
-                // only when every lane can, and the other steps together, so
-                // no term is issued twice (BA k = 3: 7.07 -> 5.14 ms); FP32:
-                // each lane decides (the checks per entry cost more than the
-                // divergence saves: 0.247 vs 0.258 ms)
-                constexpr bool kUniform = sizeof(T) == 8;
-                const bool fast = p + 4 <= lim;
-                if (kUniform ? __all_sync(kFull, fast) : fast) {  // all four in the current row
-                    if (COMP) {
-                        // compensated mode: the step's four terms summed
-                        // plainly, the partial added with its error term
-                        Acc<T, false> s4;
-                        f(ids[0], s4);
-                        f(ids[1], s4);
-                        f(ids[2], s4);
-                        f(ids[3], s4);
-                        acc.merge(s4.sx, s4.sy, T(0), T(0));
-                    } else {
-                        f(ids[0], acc);
-                        f(ids[1], acc);
-                        f(ids[2], acc);
-                        f(ids[3], acc);
+                if (sizeof(T) == 8) {
+                    // FP64 (costly terms): the warp takes every step together
+                    // and only the closing of rows diverges, so no term is
+                    // issued twice (BA k = 3: 5.15 ms; 7.08 ms as for FP32)
+                    if (p < b) {
+                        while (p >= re) close_row();
+                        four(c);
                     }
-                } else if (kUniform) {
-                    // a row or a share ends in this step for some lane: the
-                    // warp takes the four entries together, each lane closing
-                    // its rows where they end (the only divergent part)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int32_t pq = p + q;
-                        if (pq < b) {
-                            while (pq >= re) close_row();
-                            f(ids[q], acc);
-                        }
-                    }
+                } else if (p < lim) {
+                    four(c);
+                } else if (p < b) {
+                    while (p >= re) close_row();
                     lim = (re < b) ? re : b;
-                } else if (p < b) {  // a row ends in this step, or the share does
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int32_t pq = p + q;
-                        if (pq >= b) break;
-                        while (pq >= re) close_row();
-                        f(ids[q], acc);
-                    }
-                    lim = (re < b) ? re : b;
+                    four(c);
                 }
                 p += 4;
             }
@@ -712,20 +715,19 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) block_layout_kernel(
     const int32_t L = (int32_t)blk[2 * ((int64_t)j * nr + ra) + 1];
     const int32_t m4 = lane_len(L);
     const int32_t S0 = (int32_t)toff[i], S1 = S0 + (int32_t)(hi - lo);
+    const int32_t S4 = S0 + (int32_t)((hi - lo + 3) & ~int64_t(3));  // padded end
+    const uint32_t pad = tb + (uint32_t)tv;  // the id of the tile's far slot
     // the share holding entry p (t follows p, which only grows) and the slot
     int t = (int)((int64_t)S0 * kBThreads / L);
-    auto place = [&](int32_t p, int32_t* s) -> int64_t {
+    int32_t sidx = 0;  // p's index in its share, set by place
+    auto place = [&](int32_t p) -> int64_t {
         while (t > 0 && lane_start(L, t) > p) --t;
         while (t < kBThreads - 1 && lane_start(L, t + 1) <= p) ++t;
-        *s = p - lane_start(L, t);
-        return bsp + (int64_t)(t >> 5) * 32 * m4 + 128 * (*s >> 2) + 4 * (t & 31) + (*s & 3);
+        sidx = p - lane_start(L, t);
+        return bsp + (int64_t)(t >> 5) * 32 * m4 + 128 * (sidx >> 2) + 4 * (t & 31) + (sidx & 3);
     };
     if (!SPREAD) {
-        for (int32_t p = S0 + lane; p < S1; p += 32) {
-            int32_t sidx;
-            const int64_t d = place(p, &sidx);
-            tk[d] = kcol[lo + (p - S0)];
-        }
+        for (int32_t p = S0 + lane; p < S4; p += 32) tk[place(p)] = (p < S1) ? kcol[lo + (p - S0)] : pad;
         return;
     }
     uint32_t* in = s_in[wl];
@@ -770,8 +772,7 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) block_layout_kernel(
         for (int e0 = 0; e0 < len; e0 += 32) {
             const int e = e0 + lane;
             const bool act = e < len;
-            int32_t sidx = 0;
-            const int64_t d = act ? place(c0 + e, &sidx) : 0;
+            const int64_t d = act ? place(c0 + e) : 0;
             const int want = act ? (int)(((t % G) + sidx) % G) : 0;
             // the target residue for as many lanes as it has ids left, in lane order
             const unsigned m = __match_any_sync(kFull, act ? want : G + lane);
@@ -812,6 +813,8 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) block_layout_kernel(
         }
         __syncwarp();  // the next chunk reuses the buffers
     }
+    // the padding (at most 3 entries, lanes 0-2)
+    if (S1 + lane < S4) tk[place(S1 + lane)] = pad;
 }
 
 template <class T, int MODEL, bool COMP, int G>
@@ -1062,7 +1065,7 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
     P.window = false;
     const int64_t n = g->n;
     if (n == 0 || g->nnz_khop == 0 || g->tune.tiled == 0) return GILA_OK;
-    int64_t tv_max = kTileBudget / (int64_t)esz;
+    int64_t tv_max = kTileBudget / (int64_t)esz - 1;  // one slot for the padding's position
     if (g->tune.tile_vertices > 0) tv_max = std::min<int64_t>(tv_max, g->tune.tile_vertices);
     tv_max = std::max<int64_t>(2, tv_max & ~int64_t(1));
     const int64_t nt = (n + tv_max - 1) / tv_max;
@@ -1106,7 +1109,8 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
     const int64_t nr = (int64_t)rs.size() - 1;
     // block layout: (j, r) blocks in that order, each in share storage
     // (lane_len(L) slots per thread; block starts are multiples of 4 slots);
-    // segment starts within their block
+    // segments padded to multiples of 4 entries; segment starts within
+    // their block
     std::vector<int64_t> toff((size_t)cells), blk((size_t)(2 * nt * nr));
     int64_t slots = 0;
     for (int64_t j = 0; j < nt; ++j)
@@ -1114,7 +1118,7 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
             int64_t off = 0;
             for (int64_t u = rs[(size_t)r]; u < rs[(size_t)r + 1]; ++u) {
                 toff[(size_t)(j * n + u)] = off;
-                off += len[(size_t)(j * n + u)];
+                off += (len[(size_t)(j * n + u)] + 3) & ~int64_t(3);  // padded to 4 entries
             }
             blk[(size_t)(2 * (j * nr + r))] = slots;
             blk[(size_t)(2 * (j * nr + r) + 1)] = off;
@@ -1164,7 +1168,7 @@ bool blocked_auto_applies(int64_t n, int64_t nnz_khop, size_t esz, const gila_tu
 {
     if (n == 0 || nnz_khop == 0 || tune.tiled == 0) return tune.tiled == 1 && n > 0;
     if (tune.tiled == 1) return true;
-    int64_t tv_max = kTileBudget / (int64_t)esz;
+    int64_t tv_max = kTileBudget / (int64_t)esz - 1;  // one slot for the padding's position
     if (tune.tile_vertices > 0) tv_max = std::min<int64_t>(tv_max, tune.tile_vertices);
     tv_max = std::max<int64_t>(2, tv_max & ~int64_t(1));
     const int64_t nt = (n + tv_max - 1) / tv_max;
@@ -1264,7 +1268,7 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
     C.nhub = P.nhub;
     C.nreg = (int32_t)((g->n * kCombineLanes + kCombineThreads - 1) / kCombineThreads);
     const int grid = P.nt * P.nr;
-    const size_t smem = (size_t)P.tv * esz + (size_t)(kMaxRows + 1) * 4;
+    const size_t smem = (size_t)(P.tv + 1) * esz + (size_t)(kMaxRows + 1) * 4;
     const bool fr = (prm->p == 2 && prm->q == 1);
     cudaError_t e;
     switch (prm->precision) {

@@ -128,6 +128,11 @@ __device__ __forceinline__ float rsqrt_fast(float x)
     return r;
 }
 
+// Squared distance beyond which the generic force model takes a term as zero.
+template <class T> __device__ __forceinline__ T far_r2();
+template <> __device__ __forceinline__ float far_r2<float>() { return 1.0e38f; }
+template <> __device__ __forceinline__ double far_r2<double>() { return 1.0e300; }
+
 // Reciprocal, one approximate MUFU operation (denormals flushed; +inf at 0).
 __device__ __forceinline__ float rcp_fast(float x)
 {
@@ -186,7 +191,9 @@ struct Rep {
         } else {
             const T r2 = dx * dx + dy * dy;
             c = T(0);
-            if (r2 > T(0)) {
+            // beyond r^2 = 1e38 (FP32) or 1e300 (FP64) the term is taken as
+            // zero (padding entries of the blocked layout lie there)
+            if (r2 > T(0) && r2 < far_r2<T>()) {
                 const T dl = sqrt(r2);
                 c = (UNSCALED ? T(1) : d2) / (ipow_(dl, q) * dl);
             }

@@ -48,9 +48,11 @@ def gpu_khop(g, k):
     return krow, kcol
 
 
-def gpu_step(g, k, pos, t, prec, d=1.0, p=2, q=1):
+def gpu_step(g, k, pos, t, prec, d=1.0, p=2, q=1, tune=None):
     torch = _torch()
     with G.Graph.from_inputs(g) as h:
+        if tune:
+            G.gila_graph_tune(h.handle, **tune)
         p_in = torch.tensor(pos, dtype=_dt(prec), device="cuda")
         p_out = torch.empty_like(p_in)
         disp = torch.empty_like(p_in)
@@ -275,6 +277,25 @@ def test_step_parity_generic_exponents(p, q, prec):
     okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, k)
     t = 1e30
     base, _, disp = gpu_step(g, k, pos, t, prec, d=d, p=p, q=q)
+    _, odisp = O.step(g.n, g.row_ptr, g.col_idx, okrow, okcol, base, t, d=d, p=p, q=q)
+    assert np.abs(disp - odisp).max() <= TOL[prec] * np.abs(odisp).max()
+
+
+@pytest.mark.parametrize("p,q", [(3, 2), (0, 1), (1, 0), (2, 3)])
+@pytest.mark.parametrize("prec", [G.GILA_FP32, G.GILA_FP32_COMPENSATED, G.GILA_FP64],
+                         ids=["fp32", "fp32c", "fp64"])
+def test_step_parity_generic_exponents_blocked(p, q, prec):
+    """The generic force model on the blocked path (tiles of 998 positions,
+    so segments of every length and their padding to 4 entries occur): q = 0
+    and q = 1 are where a padding entry's far position would add a visible
+    term if the model did not cut it."""
+    g = I.barabasi_albert(6000, 3, 19)
+    k, d = 3, 1.3
+    pos = I.uniform_positions(g.n, 23)
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, k)
+    t = 1e30
+    base, _, disp = gpu_step(g, k, pos, t, prec, d=d, p=p, q=q,
+                             tune=dict(tiled=1, tile_vertices=998))
     _, odisp = O.step(g.n, g.row_ptr, g.col_idx, okrow, okcol, base, t, d=d, p=p, q=q)
     assert np.abs(disp - odisp).max() <= TOL[prec] * np.abs(odisp).max()
 
