@@ -73,11 +73,11 @@ KERNEL_SOURCES = ("paper_1606_02162_gb300/csrc/blocked.cu",
                   "paper_1606_02162_gb300/csrc/force.cuh",
                   "paper_1606_02162_gb300/csrc/device_util.cuh")
 NCU_TRAFFIC = {
-    "ba100k_k3": {"bytes": 965216512 + 8248576 + 10422272,
+    "ba100k_k3": {"bytes": 978219264 + 7552000 + 10422272,
                   "kernels": "blocked_kernel + combine_kernel (one iteration)",
                   "profile": "profiles/blocked_kernel_ba100k_k3.md, "
                              "profiles/combine_kernel_ba100k_k3.md",
-                  "sources_sha256": "dd6ebb8a3b6cb2464cd3e50359178b82b1f07c226d93eb22612f92a97fa75d02"},
+                  "sources_sha256": "e81b21c6068c2752cf450f67a196abcc01fe412af0bd11c57fd931560bca3109"},
 }
 
 
@@ -662,10 +662,11 @@ def main():
                 "compulsory_gbs": comp_bytes / (iter_ms / 1e3) / 1e9,
                 "compulsory_frac": comp_bytes / (iter_ms / 1e3) / 1e9 / hbm,
                 "traffic_source": tr["profile"] if tr else None,
-                "limiter": ("shared-memory gathers of the tiled positions (ncu on "
-                            "blocked_kernel: L1/shared 76% of peak, DRAM 37%); the 12 B/pair "
-                            "gather model counts position bytes that never reach HBM, so "
-                            "frac can exceed 1; compulsory_frac is the DRAM-side figure")
+                "limiter": ("instruction issue of blocked_kernel (ncu: issue active 73% at "
+                            "46% warp occupancy, L1/shared 65%, DRAM 58%); the 12 B/pair "
+                            "gather model counts position bytes that are read from shared "
+                            "memory, never HBM, so frac can exceed 1; compulsory_frac is the "
+                            "DRAM-side figure")
                            if achieved > hbm else None}
 
     # ------------------------------------------------ end to end (host buffers)
