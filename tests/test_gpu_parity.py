@@ -240,6 +240,23 @@ def test_bank_spread_only_reorders(prec, tol, tv):
     assert np.abs(out[0] - out[1]).max() <= tol * scale
 
 
+@pytest.mark.parametrize("prec", [G.GILA_FP32, G.GILA_FP32_COMPENSATED, G.GILA_FP64],
+                         ids=["fp32", "fp32c", "fp64"])
+@pytest.mark.parametrize("spread", [0, -1], ids=["spread", "ascending"])
+def test_step_parity_blocks_smaller_than_a_cta(prec, spread):
+    """Tiles of 48 positions on a 2,000-vertex graph: blocks of a few
+    hundred entries for 1024 threads, so most shares are empty or a single
+    step, and rows are cut by many share and warp bounds."""
+    g = I.barabasi_albert(2000, 3, 29)
+    pos = I.uniform_positions(g.n, 31)
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, 2)
+    t = 1e30
+    base, _, disp = gpu_step(g, 2, pos, t, prec,
+                             tune=dict(tiled=1, tile_vertices=48, bank_spread=spread))
+    _, odisp = O.step(g.n, g.row_ptr, g.col_idx, okrow, okcol, base, t)
+    assert np.abs(disp - odisp).max() <= TOL[prec] * np.abs(odisp).max()
+
+
 @pytest.mark.parametrize("tiled", [0, 1], ids=["plain", "blocked"])
 def test_fp64_two_vertex_force_across_scales(tiled):
     """FP64 repulsion uses a Newton-Raphson reciprocal: the force of a single
