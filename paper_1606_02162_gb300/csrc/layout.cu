@@ -289,7 +289,7 @@ cudaError_t launch_typed(const IterArgs& A, unsigned grid, cudaStream_t st)
 
 // ------------------------------------------------------------- metrics
 
-constexpr int kRedBlocks = 512;
+constexpr int kRedBlocks = 1216;  // a full wave of 256-thread blocks on 152 SMs
 constexpr int kRedThreads = 256;
 
 template <class T>
@@ -341,17 +341,18 @@ metrics_kernel(int pass, int64_t n, const int64_t* __restrict__ row,
         if (pass == 0 && sizeof(T) == 4) {
             // FP32 placements: each pair's term d^2 / delta^q in FP32 (one
             // approximate reciprocal square root, relative error below 1e-6),
-            // four terms per lane summed in FP32, then added in FP64. FP64
-            // sqrt and divide per pair would make this pass ALU-bound on
-            // GB300's low FP64 rate.
+            // eight terms per lane summed in FP32 (all positive), then added
+            // in FP64. FP64 sqrt and divide per pair would make this pass
+            // ALU-bound on GB300's low FP64 rate; eight independent loads per
+            // lane halve the rounds a warp walks a hub's row in
             const float2* pf = reinterpret_cast<const float2*>(pos);
             const float2 qu = pf[u];
             const float d2f = (float)(d * d);
             const int64_t e1 = krow[u + 1];
-            for (int64_t e0 = krow[u]; e0 < e1; e0 += 128) {
+            for (int64_t e0 = krow[u]; e0 < e1; e0 += 256) {
                 float s = 0.f;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < 8; ++j) {
                     const int64_t e = e0 + j * 32 + lane;
                     if (e >= e1) continue;
                     const int64_t v = kcol[e];
