@@ -8,12 +8,20 @@ reductions of the result. `value` is pair interactions per second over the
 timed steps, P = nnz(N(k)) + nnz(A) directed pairs per iteration (each
 k-hop pair gives a repulsion, each edge also an attraction).
 
-Default workload: Barabasi-Albert graph, n = 100,000, m = 3 (299,994 edges),
-k = 3, 500 iterations, linear cooling from 0.1 sqrt(n), d = 1, FP32,
-placement uniform in [0, sqrt n]^2 (seed 2). The k-hop lists (about 0.96 GB)
-are larger than L2, so no explicit flush is needed between steps.
+Default workload: the 1M-edge power-law graph, Chung-Lu gamma = 2.3,
+n = 250,000, E = 1,000,000 (seed 3), k = 3, 300 iterations, linear cooling
+from 0.1 sqrt(n), d = 1, FP32 with compensated sums, placement uniform in
+[0, sqrt n]^2. The k-hop lists (about 45 GB) are far larger than L2, so no
+explicit flush is needed between steps.
+
+On one GPU the same line also carries secondary figures: the triangulated
+1000 x 1000 mesh (k = 3), the Barabasi-Albert graphs of 1M edges (k = 2)
+and 300k edges (k = 3, k = 2), the batch of 4096 small graphs in one
+persistent launch against one-at-a-time launches (FP32 and FP64), and a
+short Poisson serving stream against a FIFO one-at-a-time server.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gila|reference]
+                       [--workload NAME] [--no-secondary]
 Under torchrun each rank lays out its own copy of the workload (replicas).
 """
 from __future__ import annotations
@@ -360,19 +368,18 @@ def _timed_region(torch, stream, fn, steps):
     return e0.elapsed_time(e1)
 
 
-def run_batch(args, wl, ws, rank, local):
-    """Config of many small graphs: all 4096 layouts per step in one
-    persistent, graph-captured launch (plus the one k-hop build of the
-    union), against laying the same graphs out one at a time."""
+def bench_batch(steps, warmup, ws, local, dist, count=4096, plain_every=16):
+    """Many small graphs: all `count` layouts per step in one persistent,
+    graph-captured launch (plus the one k-hop build of the union), FP32 and
+    FP64, against laying every `plain_every`-th graph out one at a time with
+    the single-graph kernels. Returns the figures (rank-local layouts/s
+    scaled by ws)."""
     import torch
 
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_1606_02162_gb300 import gila as G
     from paper_1606_02162_gb300 import inputs as I
-    torch.cuda.set_device(local)
-    dist = init_dist(ws, local)
-    graphs = I.batch_mix(4096, 50, 5000, 4)
+    wl = WORKLOADS["batch4096"]
+    graphs = I.batch_mix(count, 50, 5000, 4)
     pos = [I.uniform_positions(g.n, 400000 + i) for i, g in enumerate(graphs)]
     k, iters = wl["k"], wl["iters"]
     out = {}
@@ -394,14 +401,14 @@ def run_batch(args, wl, ws, rank, local):
             x.copy_(x0)
             G.gila_layout_batch_device(b.handle, prm, x)
 
-        for _ in range(max(args.warmup, 1)):
+        for _ in range(max(warmup, 1)):
             step()
         clocks = ClockSampler(local)
         clocks.start()
         l0 = G.gila_kernel_launches()
         if dist is not None:
             dist.barrier()
-        ms = _timed_region(torch, stream, step, args.steps)
+        ms = _timed_region(torch, stream, step, steps)
         if dist is not None:
             dist.barrier()
         ms = max_over_ranks(ms, dist, "cuda")
@@ -410,66 +417,80 @@ def run_batch(args, wl, ws, rank, local):
         nnz = G.gila_batch_info(b.handle)["nnz_khop"]
         P = nnz + sum(g.nnz for g in graphs)
         b.close()
-        out[name] = {"layouts_per_s": ws * len(graphs) * args.steps / (ms / 1e3),
-                     "ms_per_step": ms / args.steps,
-                     "pairs_per_s": ws * P * iters * args.steps / (ms / 1e3),
+        out[name] = {"layouts_per_s": ws * len(graphs) * steps / (ms / 1e3),
+                     "ms_per_step": ms / steps,
+                     "pairs_per_s": ws * P * iters * steps / (ms / 1e3),
                      "gpu_launches": launches, "clocks": clk,
                      "tuning": tuning, "autotune_s": round(t_tune, 3)}
     # one graph at a time (same kernels of the single-graph path), on a
-    # systematic sample of every 16th graph
-    sample = graphs[::16]
-    spos = pos[::16]
-    prm = G.params(k=k, iters=iters, precision=G.GILA_FP32)
-    hs = [G.Graph.from_inputs(g) for g in sample]
-    xs0 = [torch.tensor(p, dtype=torch.float32, device="cuda") for p in spos]
-    xs = [torch.empty_like(t) for t in xs0]
+    # systematic sample of every plain_every-th graph
+    sample = graphs[::plain_every]
+    spos = pos[::plain_every]
+    plain = {}
+    for name, prec, dt in (("fp32", G.GILA_FP32, torch.float32), ("fp64", G.GILA_FP64, torch.float64)):
+        prm = G.params(k=k, iters=iters, precision=prec)
+        hs = [G.Graph.from_inputs(g) for g in sample]
+        xs0 = [torch.tensor(p, dtype=dt, device="cuda") for p in spos]
+        xs = [torch.empty_like(t) for t in xs0]
 
-    def plain():
-        for h, a0, a in zip(hs, xs0, xs):
-            G.gila_khop_reset(h.handle)
-            G.gila_build_khop(h.handle, k)
-            a.copy_(a0)
-            G.gila_layout_run_device(h.handle, prm, a)
+        def one_at_a_time():
+            for h, a0, a in zip(hs, xs0, xs):
+                G.gila_khop_reset(h.handle)
+                G.gila_build_khop(h.handle, k)
+                a.copy_(a0)
+                G.gila_layout_run_device(h.handle, prm, a)
 
-    plain()
-    pms = _timed_region(torch, stream, plain, 1)
-    for h in hs:
-        h.close()
-    plain_lps = len(sample) / (pms / 1e3)
+        one_at_a_time()
+        pms = _timed_region(torch, stream, one_at_a_time, 1)
+        for h in hs:
+            h.close()
+        plain[name] = ws * len(sample) / (pms / 1e3)
+    return {"workload": wl["desc"], "graphs": len(graphs),
+            "vertices": int(sum(g.n for g in graphs)),
+            "fp32": out["fp32"], "fp64": out["fp64"],
+            "plain_one_at_a_time": {"fp32_layouts_per_s": plain["fp32"],
+                                    "fp64_layouts_per_s": plain["fp64"],
+                                    "sample": f"every {plain_every}th graph ({len(sample)})"},
+            "speedup_vs_plain": {"fp32": out["fp32"]["layouts_per_s"] / plain["fp32"],
+                                 "fp64": out["fp64"]["layouts_per_s"] / plain["fp64"]}}
+
+
+def run_batch(args, wl, ws, rank, local):
+    """The batch workload as its own JSON line."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dist = init_dist(ws, local)
+    res = bench_batch(args.steps, args.warmup, ws, local, dist)
     if dist is not None:
         dist.destroy_process_group()
     if rank != 0:
         return 0
     line = {
-        "metric": "layouts/s", "value": out["fp32"]["layouts_per_s"], "unit": "layouts/s",
+        "metric": "layouts/s", "value": res["fp32"]["layouts_per_s"], "unit": "layouts/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": out["fp32"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": res["fp32"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl["desc"], "graphs": len(graphs),
-                   "vertices": int(sum(g.n for g in graphs)),
-                   "fp32": out["fp32"], "fp64": out["fp64"],
-                   "plain_one_at_a_time": {"layouts_per_s": plain_lps,
-                                           "sample": f"every 16th graph ({len(sample)})"},
-                   "speedup_vs_plain": out["fp32"]["layouts_per_s"] / plain_lps},
-        "gpu_launches": out["fp32"]["gpu_launches"], "clocks": out["fp32"]["clocks"],
+        "config": res,
+        "gpu_launches": res["fp32"]["gpu_launches"], "clocks": res["fp32"]["clocks"],
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serve(args, wl, ws, rank, local, count=48, emax=1e6):
+def bench_serve(ws, local, dist, count=48, emax=1e6, mults=(0.9, 2.0, 4.0), seed=5):
     """Serving stream: layout requests arriving as a Poisson process, served
     by the continuous-batching server, against one-at-a-time service of the
-    same requests (a FIFO single server fed by the same arrivals)."""
+    same requests (a FIFO single server fed by the same arrivals, with each
+    request's measured service time). Returns the figures per arrival rate."""
     import torch
 
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_1606_02162_gb300 import gila as G
     from paper_1606_02162_gb300 import inputs as I
-    torch.cuda.set_device(local)
-    dist = init_dist(ws, local)
-    reqs = I.serving_requests(count, 5, emax=emax)
+    wl = WORKLOADS["serve"]
+    reqs = I.serving_requests(count, seed, emax=emax)
     graphs = [I.barabasi_albert_fast(r["n"], 3, r["seed"]) for r in reqs]
     pos = [I.uniform_positions(g.n, r["seed"]) for g, r in zip(graphs, reqs)]
     prms = [G.params(k=r["k"], iters=wl["iters"], precision=G.GILA_FP32) for r in reqs]
@@ -488,7 +509,7 @@ def run_serve(args, wl, ws, rank, local, count=48, emax=1e6):
     free_b, _ = torch.cuda.mem_get_info()
     budget = int(free_b * 0.6)
     runs = []
-    for mult in (0.9, 2.0, 4.0):
+    for mult in mults:
         rate = mult * capacity
         arrivals = I.poisson_arrivals(count, rate, 55)
         # FIFO single server with the measured service times
@@ -529,59 +550,91 @@ def run_serve(args, wl, ws, rank, local, count=48, emax=1e6):
                      "plain_one_at_a_time": {"layouts_per_s": ws * count / done,
                                              "p50_ms": float(np.percentile(plain_lat, 50) * 1e3),
                                              "p99_ms": float(np.percentile(plain_lat, 99) * 1e3)}})
+    return {"workload": "Poisson stream of Barabasi-Albert layout requests, E log-uniform in "
+                        "[1e3, %.0f], k in {2, 3}, 300 iterations, FP32" % emax,
+            "requests": count,
+            "budget": budget, "plain_capacity_layouts_per_s": capacity,
+            "mean_service_ms": float(service.mean() * 1e3), "runs": runs}
+
+
+def run_serve(args, wl, ws, rank, local, count=48, emax=1e6):
+    """The serving workload as its own JSON line."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dist = init_dist(ws, local)
+    res = bench_serve(ws, local, dist, count=count, emax=emax)
     if dist is not None:
         dist.destroy_process_group()
     if rank != 0:
         return 0
-    top = runs[-1]
+    top = res["runs"][-1]
     line = {
         "metric": "layouts/s", "value": top["server"]["layouts_per_s"], "unit": "layouts/s",
         "n_gpus": ws, "steps": 1, "warmup": 2,
         "ms_per_step": ws * count / top["server"]["layouts_per_s"] * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": wl["desc"], "requests": count, "budget": budget,
-                   "plain_capacity_layouts_per_s": capacity,
-                   "mean_service_ms": float(service.mean() * 1e3), "runs": runs},
+        "data": "synthetic", "config": res,
         "gpu_launches": top["gpu_launches"], "clocks": top["clocks"],
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="gila", choices=["gila", "reference"])
-    ap.add_argument("--workload", default="ba100k_k3", choices=sorted(WORKLOADS))
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
-    ws, rank, local = dist_env()
+def roofline_of(g, P, nnzk, elem, iter_ms, kern, hbm, peak_kind, tr):
+    """Roofline record of one FR iteration. The bound is HBM: the only
+    compulsory DRAM traffic of an iteration is the id stream of the k-hop
+    lists as the kernel reads them (2 B per entry on the blocked path, whose
+    ids are 16-bit and relative to a position tile; 4 B on the plain path),
+    the adjacency ids of the attraction pass (4 B per directed edge), and per
+    vertex the row offset (8 B) and the own position read and written
+    (2 x elem); the gathered positions are served on chip (shared-memory
+    tiles on the blocked path, L2 otherwise). `frac` is that compulsory
+    traffic over the measured iteration time against the measured HBM copy
+    bandwidth. The 12 B/pair gather model (a 4 B id and a float2 position per
+    pair, every gather counted as HBM traffic) is kept as a second figure;
+    it exceeds 1 wherever positions come from shared memory."""
+    blocked = bool(kern) and kern.get("name") == "blocked_kernel"
+    id_bytes = 2 if blocked else 4
+    nnza = P - nnzk
+    comp = id_bytes * nnzk + 4 * nnza + 8 * (g.n + 1) + 2 * elem * g.n
+    gather = (4 + elem) * P + 8 * (g.n + 1) + 2 * elem * g.n
+    achieved = comp / (iter_ms / 1e3) / 1e9
+    rec = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+           "frac": achieved / hbm, "traffic": tr["bytes"] if tr else None,
+           "kernel": "one FR iteration (all kernels of an iteration; dominant below)",
+           "bytes_model": "compulsory: %d B per k-hop entry (ids as stored) + 4 B per adjacency "
+                          "entry + 8 B offset + 2 x %d B position per vertex" % (id_bytes, elem),
+           "alg_bytes_per_launch": comp, "iter_ms": iter_ms,
+           "peak_source": peak_kind,
+           "traffic_source": tr["profile"] if tr else None,
+           "gather_model": {"bytes_per_iter": gather,
+                            "gbs": gather / (iter_ms / 1e3) / 1e9,
+                            "frac": gather / (iter_ms / 1e3) / 1e9 / hbm}}
+    if kern and kern["launches"] > 0:
+        kms = kern["ms"] / kern["launches"]
+        # the repulsion kernel streams the k-hop ids once
+        kb = id_bytes * nnzk
+        rec["dominant_kernel"] = {"name": kern["name"], "ms_per_launch": kms,
+                                  "share_of_iteration": kms / iter_ms,
+                                  "compulsory_bytes": kb,
+                                  "gbs": kb / (kms / 1e3) / 1e9,
+                                  "frac": kb / (kms / 1e3) / 1e9 / hbm}
+    return rec
 
-    if args.impl == "reference":
-        if args.workload in ("batch4096", "serve"):
-            print(json.dumps({"impl": "reference", "unavailable":
-                              "the CPU oracle arm is defined for the single-graph workloads"}))
-            return 0
-        return reference_arm(args, wl, ws, rank)
-    if args.workload == "batch4096":
-        return run_batch(args, wl, ws, rank, local)
-    if args.workload == "serve":
-        return run_serve(args, wl, ws, rank, local)
 
+def run_graph(args, name, steps, warmup, with_e2e, with_cpu, ws, rank, dist, local):
+    """One single-graph workload: `steps` whole layouts timed with CUDA
+    events on the launching stream after `warmup` untimed ones; per-iteration
+    and repulsion-kernel times from the library's own events on the same
+    stream. Returns a dict of figures."""
     import torch
 
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_1606_02162_gb300 import gila as G
     from paper_1606_02162_gb300 import inputs as I
-
-    torch.cuda.set_device(local)
-    dist = init_dist(ws, local)
+    wl = WORKLOADS[name]
 
     def barrier():
         if dist is not None:
@@ -606,11 +659,12 @@ def main():
         G.gila_layout_run_device(h.handle, prm, pos)
         return G.gila_layout_metrics(h.handle, prm, pos)
 
-    for _ in range(max(args.warmup, 0)):
+    for _ in range(max(warmup, 0)):
         step()
     torch.cuda.synchronize()
     G.gila_profile_read(h.handle)  # clear
-    G.gila_profile_enable(h.handle, True)
+    G.gila_profile_read_kernel(h.handle)
+    G.gila_profile_enable(h.handle, 2)
     clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
@@ -618,64 +672,45 @@ def main():
     launches0 = G.gila_kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     ev0.record(stream)
     marks[0].record(stream)
     last = None
-    for i in range(args.steps):
+    for i in range(steps):
         last = step()
         marks[i + 1].record(stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    step_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps)]
+    step_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(steps)]
     nnzk = G.gila_graph_info(h.handle)["nnz_khop"]
     P = nnzk + g.nnz
     launches = G.gila_kernel_launches() - launches0
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     prof = G.gila_profile_read(h.handle)
+    kern = G.gila_profile_read_kernel(h.handle)
     G.gila_profile_enable(h.handle, False)
     ms = max_over_ranks(ms, dist, "cuda")
-    ms_step = ms / args.steps
-    value = P * iters * args.steps * ws / (ms / 1e3)
+    value = P * iters * steps * ws / (ms / 1e3)
     iter_ms = prof["iter_ms"] / max(prof["iter_launches"], 1)
     build_ms = prof["build_ms"] / max(prof["builds"], 1)
     h.close()
+    del pos, pos_init
+    torch.cuda.empty_cache()
 
-    # roofline of the iteration kernel: 12 B per directed pair (4 B id +
-    # 8 B float2 position) plus 8 B row offset, 8 B own position read and
-    # 8 B position write per vertex
     elem = 16 if prec == G.GILA_FP64 else 8
-    alg_bytes = (4 + elem) * P + 8 * (g.n + 1) + 2 * elem * g.n
-    # compulsory DRAM bytes: the ids once, row offsets, own position in and out
-    # (the gathered positions stay on chip)
-    comp_bytes = 4 * P + 8 * (g.n + 1) + 2 * elem * g.n
     hbm, peak_kind = peaks()
-    achieved = alg_bytes / (iter_ms / 1e3) / 1e9
-    tr = measured_traffic(args.workload)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": tr["bytes"] if tr else None,
-                "kernel": tr["kernels"] if tr else "iteration (all kernels of one iteration)",
-                "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
-                "compulsory_bytes_per_launch": comp_bytes,
-                "compulsory_gbs": comp_bytes / (iter_ms / 1e3) / 1e9,
-                "compulsory_frac": comp_bytes / (iter_ms / 1e3) / 1e9 / hbm,
-                "traffic_source": tr["profile"] if tr else None,
-                "limiter": ("instruction issue of blocked_kernel (ncu: issue active 73% at "
-                            "46% warp occupancy, L1/shared 65%, DRAM 58%); the 12 B/pair "
-                            "gather model counts position bytes that are read from shared "
-                            "memory, never HBM, so frac can exceed 1; compulsory_frac is the "
-                            "DRAM-side figure")
-                           if achieved > hbm else None}
+    roof = roofline_of(g, P, nnzk, elem, iter_ms, kern, hbm, peak_kind, measured_traffic(name))
 
     # ------------------------------------------------ end to end (host buffers)
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         row = torch.from_numpy(g.row_ptr).pin_memory().numpy()
         col = torch.from_numpy(g.col_idx).pin_memory().numpy()
         pin_in = torch.from_numpy(np.ascontiguousarray(pos0)).pin_memory().numpy()
         pin_out = torch.empty(pin_in.shape, dtype=torch.float64).pin_memory().numpy()
+        e2e_steps = min(steps, 10)
 
         def e2e_step():
             # CSR and placement uploads, k-hop build, iterations, FP64
@@ -690,40 +725,112 @@ def main():
         e2e_step()
         barrier()
         t = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             e2e_step()
         torch.cuda.synchronize()
         barrier()
         e2e_s = max_over_ranks(time.perf_counter() - t, dist, "cuda")
-        e2e = {"value": P * iters * args.steps * ws / e2e_s, "unit": "pairs/s",
+        e2e = {"value": P * iters * e2e_steps * ws / e2e_s, "unit": "pairs/s",
                "h2d_bytes_per_step": int(row.nbytes + col.nbytes + pin_in.nbytes),
                "d2h_bytes_per_step": int(pin_out.nbytes) + 2 * 32,
-               "ms_per_step": e2e_s / args.steps * 1e3}
+               "ms_per_step": e2e_s / e2e_steps * 1e3, "steps": e2e_steps}
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if with_cpu and rank == 0 and ws == 1:
         cpu = cpu_baseline(wl, g, pos0)
+    return {"name": name, "wl": wl, "g": g, "value": value, "ms": ms, "steps": steps,
+            "ms_per_step": ms / steps, "step_ms": step_ms, "nnzk": nnzk, "P": P,
+            "iter_ms": iter_ms, "build_ms": build_ms, "launches": launches, "clocks": clk,
+            "roofline": roof, "e2e": e2e, "cpu": cpu, "last": last}
+
+
+def secondary_record(r):
+    """Short summary of a secondary workload for the main line."""
+    roof = r["roofline"]
+    rec = {"workload": r["wl"]["desc"], "pairs_per_iter": r["P"], "ms_per_iter": r["iter_ms"],
+           "pairs_per_s": r["value"], "khop_build_and_plan_ms": r["build_ms"],
+           "compulsory_frac": roof["frac"], "gather_model_frac": roof["gather_model"]["frac"],
+           "steps": r["steps"]}
+    dk = roof.get("dominant_kernel")
+    if dk:
+        rec["dominant_kernel"] = {"name": dk["name"], "ms_per_launch": dk["ms_per_launch"],
+                                  "frac": dk["frac"]}
+    return rec
+
+
+SECONDARY = ("mesh1000_k3", "ba1m_k2", "ba100k_k3", "ba100k_k2")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gila", choices=["gila", "reference"])
+    ap.add_argument("--workload", default="chunglu250k_k3", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the secondary graphs, the batch and the serving figures")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        if args.workload in ("batch4096", "serve"):
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the CPU oracle arm is defined for the single-graph workloads"}))
+            return 0
+        return reference_arm(args, wl, ws, rank)
+    if args.workload == "batch4096":
+        return run_batch(args, wl, ws, rank, local)
+    if args.workload == "serve":
+        return run_serve(args, wl, ws, rank, local)
+
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+
+    torch.cuda.set_device(local)
+    dist = init_dist(ws, local)
+    r = run_graph(args, args.workload, args.steps, args.warmup, not args.no_e2e,
+                  not args.no_cpu_baseline, ws, rank, dist, local)
+    # secondary figures, one GPU only: the short-row graphs (mesh, k = 2),
+    # the default-sized BA graph, the batch and a short serving stream
+    secondary = None
+    if ws == 1 and not args.no_secondary:
+        secondary = {}
+        for name in SECONDARY:
+            if name == args.workload:
+                continue
+            s = run_graph(args, name, 3, 1, False, False, ws, rank, dist, local)
+            secondary[name] = secondary_record(s)
+        secondary["batch4096"] = bench_batch(1, 1, ws, local, dist)
+        secondary["serve"] = bench_serve(ws, local, dist, count=24, emax=1e6, mults=(2.0, 4.0))
 
     if dist is not None:
         dist.destroy_process_group()
     if rank != 0:
         return 0
+    g, last = r["g"], r["last"]
     line = {
-        "metric": "pair-interactions/s", "value": value, "unit": "pairs/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "metric": "pair-interactions/s", "value": r["value"], "unit": "pairs/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE_NAME[wl["precision"]], "data": "synthetic",
-        "config": {"workload": wl["desc"], "n": g.n, "edges": g.num_edges, "k": k,
-                   "iters": iters, "nnz_khop": nnzk, "pairs_per_iter": P,
-                   "ms_per_iter": iter_ms, "khop_build_ms": build_ms,
-                   "step_ms": [round(x, 3) for x in step_ms],
-                   "layouts_per_s": ws * args.steps / (ms / 1e3),
-                   "l2": "inputs larger than L2 (k-hop lists %.2f GB)" % (4 * nnzk / 1e9),
+        "config": {"workload": wl["desc"], "n": g.n, "edges": g.num_edges, "k": wl["k"],
+                   "iters": wl["iters"], "nnz_khop": r["nnzk"], "pairs_per_iter": r["P"],
+                   "ms_per_iter": r["iter_ms"], "khop_build_and_plan_ms": r["build_ms"],
+                   "step_ms": [round(x, 3) for x in r["step_ms"]],
+                   "layouts_per_s": ws * args.steps / (r["ms"] / 1e3),
+                   "l2": "inputs larger than L2 (k-hop lists %.2f GB)" % (4 * r["nnzk"] / 1e9),
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "quality_last": {"edge_cv": last["edge_cv"],
-                                    "rep_att_ratio": last["rep_att_ratio"]} if last else None},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches, "clocks": clk,
+                                    "rep_att_ratio": last["rep_att_ratio"]} if last else None,
+                   "secondary": secondary},
+        "roofline": r["roofline"], "cpu_baseline": r["cpu"], "e2e": r["e2e"],
+        "gpu_launches": r["launches"], "clocks": r["clocks"],
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -268,6 +268,13 @@ gila_status gila_batch_info(const gila_batch* b, int32_t* count, int64_t* total_
  * cached per k like gila_build_khop. gila_batch_khop_reset drops them. */
 gila_status gila_batch_build_khop(gila_batch* b, int32_t k, int64_t* nnz_out);
 gila_status gila_batch_khop_reset(gila_batch* b);
+/* Copy the built k-hop lists N_v(k) of the whole batch (Section 4.5) to
+ * host memory, as for gila_khop_export: krow_host int64[total_n + 1],
+ * kcol_host int32[nnz_khop], rows sorted ascending. Vertex v of graph i is
+ * row voff_i + v, where voff_i is the vertex count of graphs 0..i-1, and
+ * its entries are numbered the same way (a graph's lists stay inside its
+ * own id range). GILA_ESTATE when no lists are built. */
+gila_status gila_batch_khop_export(const gila_batch* b, int64_t* krow_host, int32_t* kcol_host);
 /* Set (or read back, defaults filled in for a precision) the launch shape
  * and lanes-per-vertex thresholds of the batched kernel. */
 gila_status gila_batch_tune(gila_batch* b, const gila_batch_tuning* t);
@@ -450,13 +457,27 @@ gila_status gila_graph_set_wait_test(gila_graph* g, int32_t on);
 double gila_temperature(const gila_params* prm, double t0, int32_t i);
 
 /* Per-graph timing by CUDA events recorded on the graph's stream while
- * enabled (on = 1): k-hop builds (count, ms) and iteration kernels
+ * enabled (on = 1 or 2; 0 turns it off; other values give GILA_EINVAL):
+ * k-hop builds (count, ms; the one-time blocked-path plan of the lists is
+ * added to build_ms, not counted as a build) and iteration sequences
  * (launches, ms of the launch sequence). gila_profile_read returns the
  * totals since the previous read, then clears them; it waits for the last
  * recorded event. */
 gila_status gila_profile_enable(gila_graph* g, int32_t on);
 gila_status gila_profile_read(gila_graph* g, int64_t* builds, double* build_ms,
                               int64_t* iter_launches, double* iter_ms);
+
+/* With on = 2 each iteration's repulsion kernel (the one that streams the
+ * k-hop lists of Section 4.5: blocked_kernel, window_kernel,
+ * iteration_kernel or ordered_kernel) is also timed on its own, between
+ * events recorded directly before and after its launch. Returns the number
+ * of such launches since the previous call and their total ms, and copies
+ * the name of the last kernel timed into name (NUL-terminated, at most
+ * name_cap - 1 characters; name may be NULL); then clears those totals.
+ * Waits for the recorded events. Call gila_profile_read first when both are
+ * wanted (it folds pending records of every kind). */
+gila_status gila_profile_read_kernel(gila_graph* g, int64_t* launches, double* ms, char* name,
+                                     int32_t name_cap);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* gila_last_error(void);

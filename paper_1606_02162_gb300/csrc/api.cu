@@ -17,6 +17,32 @@ static std::atomic<int64_t> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+cudaEvent_t prof_kernel_begin(gila_graph* g)
+{
+    if (g->prof_on < 2) return nullptr;
+    cudaEvent_t a = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaEventRecord(a, g->stream);
+    return a;
+}
+
+void prof_kernel_end(gila_graph* g, cudaEvent_t a, const char* name)
+{
+    if (!a) return;
+    cudaEvent_t b = nullptr;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaGetLastError();
+        cudaEventDestroy(a);
+        return;
+    }
+    cudaEventRecord(b, g->stream);
+    g->prof.push_back(ProfileRec{a, b, 2, 1});
+    g->prof_kernel_name = name;
+}
+
 void set_error(const std::string& msg) { t_err = msg; }
 
 gila_status fail(gila_status s, const std::string& msg)
@@ -94,6 +120,27 @@ gila_status ensure_khop(gila_graph* g, int k)
     return s;
 }
 
+// prepare_iteration (the blocked-path plan, once per k-hop build) inside a
+// build-kind profile record, so that iteration timings hold iterations only.
+gila_status timed_prepare(gila_graph* g, const gila_params* prm)
+{
+    const int w = is_f64(prm->precision) ? 1 : 0;
+    if (prm->precision == GILA_FP64_ORDERED || g->n == 0 || g->tplan[w].ready)
+        return GILA_OK;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (g->prof_on) {
+        GILA_CUDA(cudaEventCreate(&a));
+        GILA_CUDA(cudaEventCreate(&b));
+        GILA_CUDA(cudaEventRecord(a, g->stream));
+    }
+    gila_status s = prepare_iteration(g, prm);
+    if (a) {
+        cudaEventRecord(b, g->stream);
+        g->prof.push_back(ProfileRec{a, b, 0, 0});
+    }
+    return s;
+}
+
 // Temperature of iteration i (0-based) of prm->iters.
 double temperature(const gila_params* prm, double t0, int i)
 {
@@ -123,6 +170,9 @@ gila_status run_loop(gila_graph* g, const gila_params* prm, void* pos, void* tmp
     double t0 = 0.0;
     gila_status s = resolve_t0(g, prm, pos, &t0);
     if (s != GILA_OK) return s;
+    // the one-time blocked-path plan of the current k-hop lists, timed with
+    // the build when profiling
+    if ((s = timed_prepare(g, prm)) != GILA_OK) return s;
     cudaEvent_t a = nullptr, b = nullptr;
     if (g->prof_on && prm->iters > 0) {
         GILA_CUDA(cudaEventCreate(&a));
@@ -498,6 +548,7 @@ gila_status gila_layout_step(gila_graph* g, const gila_params* prm, double t,
         return fail(GILA_EINVAL, "pos_in_dev and pos_out_dev must not overlap");
     if ((s = use_device(g)) != GILA_OK) return s;
     if ((s = ensure_khop(g, prm->k)) != GILA_OK) return s;
+    if ((s = timed_prepare(g, prm)) != GILA_OK) return s;
     cudaEvent_t a = nullptr, b = nullptr;
     if (g->prof_on) {
         GILA_CUDA(cudaEventCreate(&a));
@@ -589,7 +640,8 @@ double gila_temperature(const gila_params* prm, double t0, int32_t i)
 gila_status gila_profile_enable(gila_graph* g, int32_t on)
 {
     if (!g) return fail(GILA_EINVAL, "graph is NULL");
-    g->prof_on = on != 0;
+    if (on < 0 || on > 2) return fail(GILA_EINVAL, "on must be 0, 1 or 2");
+    g->prof_on = on;
     return GILA_OK;
 }
 
@@ -606,6 +658,9 @@ gila_status gila_profile_read(gila_graph* g, int64_t* builds, double* build_ms,
         if (r.kind == 0) {
             g->prof_builds += r.launches;
             g->prof_build_ms += ms;
+        } else if (r.kind == 2) {
+            g->prof_kernel_launches += r.launches;
+            g->prof_kernel_ms += ms;
         } else {
             g->prof_launches += r.launches;
             g->prof_iter_ms += ms;
@@ -622,6 +677,49 @@ gila_status gila_profile_read(gila_graph* g, int64_t* builds, double* build_ms,
     g->prof_launches = 0;
     g->prof_build_ms = 0.0;
     g->prof_iter_ms = 0.0;
+    return GILA_OK;
+}
+
+gila_status gila_profile_read_kernel(gila_graph* g, int64_t* launches, double* ms, char* name,
+                                     int32_t name_cap)
+{
+    if (!g) return fail(GILA_EINVAL, "graph is NULL");
+    // folds the pending repulsion-kernel records into the totals; records of
+    // the other kinds stay for gila_profile_read
+    int64_t kl = 0;
+    double kms = 0.0;
+    {
+        gila_status s = use_device(g);
+        if (s != GILA_OK) return s;
+        for (auto& r : g->prof) {
+            if (r.kind != 2) continue;
+            float m = 0.0f;
+            GILA_CUDA(cudaEventSynchronize(r.b));
+            GILA_CUDA(cudaEventElapsedTime(&m, r.a, r.b));
+            kl += r.launches;
+            kms += m;
+        }
+        std::vector<ProfileRec> rest;
+        for (auto& r : g->prof) {
+            if (r.kind == 2) {
+                cudaEventDestroy(r.a);
+                cudaEventDestroy(r.b);
+            } else {
+                rest.push_back(r);
+            }
+        }
+        g->prof.swap(rest);
+    }
+    kl += g->prof_kernel_launches;
+    kms += g->prof_kernel_ms;
+    g->prof_kernel_launches = 0;
+    g->prof_kernel_ms = 0.0;
+    if (launches) *launches = kl;
+    if (ms) *ms = kms;
+    if (name && name_cap > 0) {
+        std::strncpy(name, g->prof_kernel_name, (size_t)name_cap - 1);
+        name[name_cap - 1] = '\0';
+    }
     return GILA_OK;
 }
 

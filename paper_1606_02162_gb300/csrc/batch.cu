@@ -542,6 +542,12 @@ gila_status gila_batch_khop_reset(gila_batch* b)
     return gila_khop_reset(b->g);
 }
 
+gila_status gila_batch_khop_export(const gila_batch* b, int64_t* krow_host, int32_t* kcol_host)
+{
+    if (!b) return fail(GILA_EINVAL, "batch is NULL");
+    return gila_khop_export(b->g, krow_host, kcol_host);
+}
+
 gila_status gila_batch_tune(gila_batch* b, const gila_batch_tuning* t)
 {
     if (!b || !t) return fail(GILA_EINVAL, "batch or tuning is NULL");

@@ -5,12 +5,15 @@
 // cut into contiguous ranges of about equal total list length. Block (j, r)
 // holds, for every row u of range r in order, the entries of u's k-hop row
 // that fall in tile j, in an order chosen so that the lanes of one gather
-// read distinct shared-memory banks; block starts are 16-byte aligned. One
+// read distinct shared-memory banks; block starts are 16-byte aligned. An
+// entry is stored as a 16-bit id relative to the tile's first id (a tile
+// holds at most 32,767 positions), so the id stream, the only compulsory
+// DRAM traffic of an iteration, is 2 bytes per entry instead of 4. One
 // CTA per block loads tile j and the block's row directory into shared
-// memory; each thread takes an equal, 4-aligned share of the block's
-// entries (stored so that a warp's 16-byte id loads of one step are
-// contiguous), gathers positions from the tile and sums them row by row on
-// its own. A row wholly inside a share is stored by its thread; the parts of
+// memory; each thread takes an equal, 8-aligned share of the block's
+// entries (stored so that a warp's 16-byte id loads of one step, eight ids
+// per lane, are contiguous), gathers positions from the tile and sums them
+// row by row on its own. A row wholly inside a share is stored by its thread; the parts of
 // rows cut by share bounds are added by a segmented scan across the warp,
 // and rows cut by warp bounds in warp order, then stored as the row's
 // partial for tile j. A second kernel adds each row's tile partials in tile
@@ -35,12 +38,13 @@ constexpr int kBWarps = kBThreads / 32;
 constexpr int kSmemCap = 227 * 1024;
 constexpr int kMaxRows = 4096;  // rows per range (directory in shared memory)
 constexpr int kTileBudget = kSmemCap - (kMaxRows + 1) * 4 - 4096;
+constexpr int64_t kMaxTile = 65534;  // tile-relative ids and the far slot's id fit 16 bits
 constexpr uint32_t kBulkChunk = 32768;      // bytes per bulk copy instruction
 constexpr int64_t kBlockedMinNnz = 100000000;  // automatic mode: k-hop entries needed (tiles)
 constexpr uint64_t kWaitNs = 1000000000ull;  // bound on a tile wait (1 s, far above any copy)
 constexpr uint64_t kTestWaitNs = 1000000ull;   // the bound while the wait test hook is on
-// Every (tile j, row) segment is padded to a multiple of 4 entries with the
-// id j tv + tv, whose tile slot (one past the tile) holds a position so far
+// Every (tile j, row) segment is padded to a multiple of 8 entries with the
+// relative id tv, whose tile slot (one past the tile) holds a position so far
 // away that its term is exactly zero: in FP32 the factor rcp(r^2 + 2^-100)
 // of r^2 = 2e38 is below the smallest normal and flushes to 0; in FP64 r^2
 // = 1.48e308 flushes rcp to 0 the same way; the generic model cuts terms
@@ -57,7 +61,7 @@ constexpr int kPrefetch = 4;  // steps between an L2 prefetch of ids and their r
 __device__ int g_tile_wait_failed = 0;
 
 struct BlockedArgs {
-    const uint32_t* tk;        // ids, block by block, each block in share storage order
+    const uint16_t* tk;        // tile-relative ids, block by block, in share storage order
     const int64_t* toff;       // nt n: start of segment (tile j, row u) within its block
     const int64_t* blk;        // 2 nt nr: first slot in tk and entry count of block (j, r)
     const int32_t* range_start;
@@ -100,20 +104,23 @@ __device__ __forceinline__ void store_cell(typename V2<T>::type* c, const Acc<T,
     }
 }
 
+// Entries per step: one 16-byte load of eight 16-bit ids.
+constexpr int kStep = 8;
+
 // Entries of block (j, r) per thread: thread t takes [lane_start(L, t),
-// lane_start(L, t + 1)), 4-aligned; in storage every thread has lane_len(L)
-// slots (a multiple of 4, at least its share), laid out per warp step-major:
-// the k-th group of four slots of lane l of warp w is at
-// (w 32 lane_len + 128 k + 4 l) from the block's start, so that a warp's
+// lane_start(L, t + 1)), 8-aligned; in storage every thread has lane_len(L)
+// slots (a multiple of 8, at least its share), laid out per warp step-major:
+// the k-th group of eight slots of lane l of warp w is at
+// (w 32 lane_len + 256 k + 8 l) from the block's start, so that a warp's
 // 16-byte loads of one step are one contiguous 512-byte run.
 __host__ __device__ __forceinline__ int32_t lane_start(int32_t L, int t)
 {
-    return (t >= kBThreads) ? L : (int32_t)(((int64_t)L * t / kBThreads) & ~int64_t(3));
+    return (t >= kBThreads) ? L : (int32_t)(((int64_t)L * t / kBThreads) & ~int64_t(kStep - 1));
 }
 __host__ __device__ __forceinline__ int32_t lane_len(int32_t L)
 {
-    // a share is at most L / kBThreads + 4 entries (4-aligned cuts)
-    return (L == 0) ? 0 : ((L / kBThreads + 7) & ~3);
+    // a share is at most L / kBThreads + 8 entries (8-aligned cuts)
+    return (L == 0) ? 0 : ((L / kBThreads + 2 * kStep - 1) & ~(kStep - 1));
 }
 
 template <class T, int MODEL, bool COMP>
@@ -182,14 +189,14 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
 
     if (L > 0) {
         Rep<T, MODEL, COMP, kSrcShared, true> f;  // d^2 is applied when the partials are added
-        f.src.set_shared(tile, (uint32_t)tb);
+        f.src.set_shared(tile, 0u);  // ids are relative to the tile
         f.d2 = T(1);
         f.q = A.q;
         // this thread's entries [a, b) (a < L), their storage, and the row of a
         const int32_t a = lane_start(L, threadIdx.x), b = lane_start(L, threadIdx.x + 1);
-        const int32_t m4 = lane_len(L);
+        const int32_t m8 = lane_len(L);
         const uint4* ids4 =
-            reinterpret_cast<const uint4*>(A.tk + bsp + (int64_t)warp * 32 * m4) + lane;
+            reinterpret_cast<const uint4*>(A.tk + bsp + (int64_t)warp * 32 * m8) + lane;
         int lo = 0, hi = nrows;
         while (lo < hi) {  // the last i with D[i] <= a
             const int mid = (lo + hi + 1) >> 1;
@@ -238,7 +245,7 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
         // compensated sums, which need the registers); each unrolled step
         // consumes its own ring register and refills it: no register moves
         constexpr int kRing = COMP ? 3 : 4;
-        const int nsteps = m4 >> 2;  // the same for every thread of the block
+        const int nsteps = m8 / kStep;  // the same for every thread of the block
         uint4 ring[kRing];
 #pragma unroll
         for (int st = 0; st < kRing; ++st)
@@ -250,27 +257,35 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
             for (int k = kRing; k < kPrefetch + kRing && k < nsteps; k += kRing)
                 bulk_prefetch_l2(warp_ids + 32 * k,
                                  (uint32_t)(512 * ((nsteps - k < kRing) ? nsteps - k : kRing)));
-        // segments and shares are multiples of 4 entries: every step lies in
+        // segments and shares are multiples of 8 entries: every step lies in
         // one row, and rows change only between steps. A step before the
-        // current row's end (and the share's) goes straight to its four
+        // current row's end (and the share's) goes straight to its eight
         // terms; a step where a row begins first closes the rows before it
         int32_t lim = (re < b) ? re : b;
         int32_t p = a;
-        auto four = [&](const uint4 c) {
+        auto eight = [&](const uint4 c) {
             if (COMP) {
-                // compensated mode: the step's four terms summed plainly,
+                // compensated mode: the step's eight terms summed plainly,
                 // the partial added with its error term
-                Acc<T, false> s4;
-                f(c.x, s4);
-                f(c.y, s4);
-                f(c.z, s4);
-                f(c.w, s4);
-                acc.merge(s4.sx, s4.sy, T(0), T(0));
+                Acc<T, false> s8;
+                f(c.x & 0xffffu, s8);
+                f(c.x >> 16, s8);
+                f(c.y & 0xffffu, s8);
+                f(c.y >> 16, s8);
+                f(c.z & 0xffffu, s8);
+                f(c.z >> 16, s8);
+                f(c.w & 0xffffu, s8);
+                f(c.w >> 16, s8);
+                acc.merge(s8.sx, s8.sy, T(0), T(0));
             } else {
-                f(c.x, acc);
-                f(c.y, acc);
-                f(c.z, acc);
-                f(c.w, acc);
+                f(c.x & 0xffffu, acc);
+                f(c.x >> 16, acc);
+                f(c.y & 0xffffu, acc);
+                f(c.y >> 16, acc);
+                f(c.z & 0xffffu, acc);
+                f(c.z >> 16, acc);
+                f(c.w & 0xffffu, acc);
+                f(c.w >> 16, acc);
             }
         };
         for (int k0 = 0; k0 < nsteps; k0 += kRing) {
@@ -291,16 +306,16 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                     // issued twice (BA k = 3: 5.15 ms; 7.08 ms as for FP32)
                     if (p < b) {
                         while (p >= re) close_row();
-                        four(c);
+                        eight(c);
                     }
                 } else if (p < lim) {
-                    four(c);
+                    eight(c);
                 } else if (p < b) {
                     while (p >= re) close_row();
                     lim = (re < b) ? re : b;
-                    four(c);
+                    eight(c);
                 }
-                p += 4;
+                p += kStep;
             }
         }
         const bool has_b = !in_first;  // the share ends in a later row than it began
@@ -665,9 +680,10 @@ __global__ void seglen_kernel(int64_t n, const int64_t* __restrict__ krow,
     len[i] = hi - lo;
 }
 
-// Copy every (tile, row) segment into its block's share storage: entry p of
-// the block, held by the share of thread t (s = p - lane_start(L, t)), goes
-// to slot (t / 32) 32 lane_len(L) + 128 (s / 4) + 4 (t % 32) + s % 4.
+// Copy every (tile, row) segment into its block's share storage as 16-bit
+// ids relative to the tile: entry p of the block, held by the share of
+// thread t (s = p - lane_start(L, t)), goes to slot
+// (t / 32) 32 lane_len(L) + 256 (s / 8) + 8 (t % 32) + s % 8.
 //
 // With SPREAD each segment's ids are also ordered for blocked_kernel's
 // shared-memory gathers. A warp's gather is served in groups of G lanes
@@ -691,7 +707,7 @@ template <int G, bool SPREAD>
 __global__ void __launch_bounds__(kSpreadWarps * 32) block_layout_kernel(
     int64_t n, const int64_t* __restrict__ krow, const uint32_t* __restrict__ kcol, int nt,
     int tv, const int64_t* __restrict__ toff, const int64_t* __restrict__ blk,
-    const int32_t* __restrict__ range_start, int nr, uint32_t* __restrict__ tk)
+    const int32_t* __restrict__ range_start, int nr, uint16_t* __restrict__ tk)
 {
     __shared__ uint32_t s_in[kSpreadWarps][kSpreadChunk];  // the chunk's ids by residue
     __shared__ int s_run[kSpreadWarps][G];
@@ -713,10 +729,10 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) block_layout_kernel(
     }
     const int64_t bsp = blk[2 * ((int64_t)j * nr + ra)];
     const int32_t L = (int32_t)blk[2 * ((int64_t)j * nr + ra) + 1];
-    const int32_t m4 = lane_len(L);
+    const int32_t m8 = lane_len(L);
     const int32_t S0 = (int32_t)toff[i], S1 = S0 + (int32_t)(hi - lo);
-    const int32_t S4 = S0 + (int32_t)((hi - lo + 3) & ~int64_t(3));  // padded end
-    const uint32_t pad = tb + (uint32_t)tv;  // the id of the tile's far slot
+    const int32_t S8 = S0 + (int32_t)((hi - lo + kStep - 1) & ~int64_t(kStep - 1));  // padded end
+    const uint16_t pad = (uint16_t)tv;  // the relative id of the tile's far slot
     // the share holding entry p (t follows p, which only grows) and the slot
     int t = (int)((int64_t)S0 * kBThreads / L);
     int32_t sidx = 0;  // p's index in its share, set by place
@@ -724,10 +740,11 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) block_layout_kernel(
         while (t > 0 && lane_start(L, t) > p) --t;
         while (t < kBThreads - 1 && lane_start(L, t + 1) <= p) ++t;
         sidx = p - lane_start(L, t);
-        return bsp + (int64_t)(t >> 5) * 32 * m4 + 128 * (sidx >> 2) + 4 * (t & 31) + (sidx & 3);
+        return bsp + (int64_t)(t >> 5) * 32 * m8 + 256 * (sidx >> 3) + 8 * (t & 31) + (sidx & 7);
     };
     if (!SPREAD) {
-        for (int32_t p = S0 + lane; p < S4; p += 32) tk[place(p)] = (p < S1) ? kcol[lo + (p - S0)] : pad;
+        for (int32_t p = S0 + lane; p < S8; p += 32)
+            tk[place(p)] = (p < S1) ? (uint16_t)(kcol[lo + (p - S0)] - tb) : pad;
         return;
     }
     uint32_t* in = s_in[wl];
@@ -809,12 +826,12 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) block_layout_kernel(
                 if (lane == l) id = in[at];
                 pend &= pend - 1;
             }
-            if (act) tk[d] = id;
+            if (act) tk[d] = (uint16_t)(id - tb);
         }
         __syncwarp();  // the next chunk reuses the buffers
     }
-    // the padding (at most 3 entries, lanes 0-2)
-    if (S1 + lane < S4) tk[place(S1 + lane)] = pad;
+    // the padding (at most 7 entries, lanes 0-6)
+    if (S1 + lane < S8) tk[place(S1 + lane)] = pad;
 }
 
 template <class T, int MODEL, bool COMP, int G>
@@ -844,8 +861,8 @@ cudaError_t launch_window(const WindowArgs& W, int grid, size_t smem, cudaStream
 }
 
 template <class T, int MODEL, bool COMP>
-cudaError_t launch_pair(const BlockedArgs& B, const CombineArgs& C, int grid, size_t smem,
-                        cudaStream_t st, int device)
+cudaError_t launch_pair(gila_graph* g, const BlockedArgs& B, const CombineArgs& C, int grid,
+                        size_t smem, cudaStream_t st, int device)
 {
     static std::atomic<uint64_t> configured{0};  // one bit per device; callers may race
     const uint64_t bit = 1ull << (device & 63);
@@ -856,9 +873,11 @@ cudaError_t launch_pair(const BlockedArgs& B, const CombineArgs& C, int grid, si
         if (e != cudaSuccess) return e;
         configured.fetch_or(bit);
     }
+    cudaEvent_t pa = prof_kernel_begin(g);
     blocked_kernel<T, MODEL, COMP><<<grid, kBThreads, smem, st>>>(B);
     count_launch();
     cudaError_t e = cudaGetLastError();
+    prof_kernel_end(g, pa, "blocked_kernel");
     if (e != cudaSuccess) return e;
     combine_kernel<T, MODEL, COMP><<<(unsigned)(C.nreg + C.nhub), kCombineThreads, 0, st>>>(C);
     count_launch();
@@ -1067,7 +1086,7 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
     if (n == 0 || g->nnz_khop == 0 || g->tune.tiled == 0) return GILA_OK;
     int64_t tv_max = kTileBudget / (int64_t)esz - 1;  // one slot for the padding's position
     if (g->tune.tile_vertices > 0) tv_max = std::min<int64_t>(tv_max, g->tune.tile_vertices);
-    tv_max = std::max<int64_t>(2, tv_max & ~int64_t(1));
+    tv_max = std::max<int64_t>(2, std::min<int64_t>(tv_max, kMaxTile) & ~int64_t(1));
     const int64_t nt = (n + tv_max - 1) / tv_max;
     const int64_t tv = std::min<int64_t>(tv_max, (((n + nt - 1) / nt) + 1) & ~int64_t(1));
     const int min_seg = g->tune.min_segment > 0 ? g->tune.min_segment : 48;
@@ -1108,9 +1127,9 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
     const std::vector<int32_t> rs = partition_rows(cost, total, ranges_target(g, nt));
     const int64_t nr = (int64_t)rs.size() - 1;
     // block layout: (j, r) blocks in that order, each in share storage
-    // (lane_len(L) slots per thread; block starts are multiples of 4 slots);
-    // segments padded to multiples of 4 entries; segment starts within
-    // their block
+    // (lane_len(L) slots per thread; block starts are multiples of 8 slots,
+    // 16 bytes); segments padded to multiples of 8 entries; segment starts
+    // within their block
     std::vector<int64_t> toff((size_t)cells), blk((size_t)(2 * nt * nr));
     int64_t slots = 0;
     for (int64_t j = 0; j < nt; ++j)
@@ -1118,19 +1137,19 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
             int64_t off = 0;
             for (int64_t u = rs[(size_t)r]; u < rs[(size_t)r + 1]; ++u) {
                 toff[(size_t)(j * n + u)] = off;
-                off += (len[(size_t)(j * n + u)] + 3) & ~int64_t(3);  // padded to 4 entries
+                off += (len[(size_t)(j * n + u)] + kStep - 1) & ~int64_t(kStep - 1);  // padded
             }
             blk[(size_t)(2 * (j * nr + r))] = slots;
             blk[(size_t)(2 * (j * nr + r) + 1)] = off;
             slots += (int64_t)kBThreads * lane_len((int32_t)off);
         }
-    const int64_t tk_len = slots + 4;
+    const int64_t tk_len = slots + kStep;
     if ((s = ensure((void**)&P.toff, &P.toff_cap, sizeof(int64_t) * (size_t)cells)) != GILA_OK)
         return s;
     if ((s = ensure((void**)&P.blk, &P.blk_cap, sizeof(int64_t) * blk.size())) != GILA_OK) return s;
     if ((s = ensure((void**)&P.range_start, &P.range_cap, sizeof(int32_t) * rs.size())) != GILA_OK)
         return s;
-    if ((s = ensure((void**)&P.tk, &P.tk_cap, sizeof(uint32_t) * (size_t)tk_len)) != GILA_OK)
+    if ((s = ensure((void**)&P.tk, &P.tk_cap, sizeof(uint16_t) * (size_t)tk_len)) != GILA_OK)
         return s;
     if ((s = ensure(&P.part, &P.part_cap, 2 * esz * (size_t)cells)) != GILA_OK) return s;
     GILA_CUDA(cudaMemcpyAsync(P.toff, toff.data(), sizeof(int64_t) * cells, cudaMemcpyHostToDevice,
@@ -1141,7 +1160,7 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
                               cudaMemcpyHostToDevice, g->stream));
     // ids ordered for conflict-free gathers, or in ascending order; the
     // slots past each share's end stay zero
-    GILA_CUDA(cudaMemsetAsync(P.tk, 0, sizeof(uint32_t) * (size_t)tk_len, g->stream));
+    GILA_CUDA(cudaMemsetAsync(P.tk, 0, sizeof(uint16_t) * (size_t)tk_len, g->stream));
     const unsigned lay_blocks = (unsigned)((cells + kSpreadWarps - 1) / kSpreadWarps);
     if (g->tune.bank_spread >= 0 && esz == 8)
         block_layout_kernel<16, true><<<lay_blocks, kSpreadWarps * 32, 0, g->stream>>>(
@@ -1170,7 +1189,7 @@ bool blocked_auto_applies(int64_t n, int64_t nnz_khop, size_t esz, const gila_tu
     if (tune.tiled == 1) return true;
     int64_t tv_max = kTileBudget / (int64_t)esz - 1;  // one slot for the padding's position
     if (tune.tile_vertices > 0) tv_max = std::min<int64_t>(tv_max, tune.tile_vertices);
-    tv_max = std::max<int64_t>(2, tv_max & ~int64_t(1));
+    tv_max = std::max<int64_t>(2, std::min<int64_t>(tv_max, kMaxTile) & ~int64_t(1));
     const int64_t nt = (n + tv_max - 1) / tv_max;
     const int min_seg = tune.min_segment > 0 ? tune.min_segment : 48;
     return nnz_khop >= kBlockedMinNnz && (double)nnz_khop / ((double)n * (double)nt) >= min_seg;
@@ -1220,6 +1239,7 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
         const bool wide = g->nnz_khop > 64 * g->n;
         const bool fr = (prm->p == 2 && prm->q == 1);
         cudaError_t e;
+        cudaEvent_t pa = prof_kernel_begin(g);
         switch (prm->precision) {
         case GILA_FP64:
             e = fr ? launch_window<double, kFR, false>(W, P.nr, wsmem, g->stream, g->device, wide)
@@ -1234,6 +1254,7 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
                    : launch_window<float, kGeneric, false>(W, P.nr, wsmem, g->stream, g->device, wide);
             break;
         }
+        prof_kernel_end(g, pa, "window_kernel");
         if (e != cudaSuccess) return cuda_fail(e, "window_kernel");
         *handled = true;
         return GILA_OK;
@@ -1273,16 +1294,16 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
     cudaError_t e;
     switch (prm->precision) {
     case GILA_FP64:
-        e = fr ? launch_pair<double, kFR, false>(B, C, grid, smem, g->stream, g->device)
-               : launch_pair<double, kGeneric, false>(B, C, grid, smem, g->stream, g->device);
+        e = fr ? launch_pair<double, kFR, false>(g, B, C, grid, smem, g->stream, g->device)
+               : launch_pair<double, kGeneric, false>(g, B, C, grid, smem, g->stream, g->device);
         break;
     case GILA_FP32_COMPENSATED:
-        e = fr ? launch_pair<float, kFR, true>(B, C, grid, smem, g->stream, g->device)
-               : launch_pair<float, kGeneric, true>(B, C, grid, smem, g->stream, g->device);
+        e = fr ? launch_pair<float, kFR, true>(g, B, C, grid, smem, g->stream, g->device)
+               : launch_pair<float, kGeneric, true>(g, B, C, grid, smem, g->stream, g->device);
         break;
     default:
-        e = fr ? launch_pair<float, kFR, false>(B, C, grid, smem, g->stream, g->device)
-               : launch_pair<float, kGeneric, false>(B, C, grid, smem, g->stream, g->device);
+        e = fr ? launch_pair<float, kFR, false>(g, B, C, grid, smem, g->stream, g->device)
+               : launch_pair<float, kGeneric, false>(g, B, C, grid, smem, g->stream, g->device);
         break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "blocked_kernel");

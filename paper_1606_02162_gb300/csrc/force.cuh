@@ -183,6 +183,24 @@ struct Rep {
     template <bool C = COMP>
     __device__ __forceinline__ void operator()(uint32_t v, Acc<T, C>& a) const
     {
+        if constexpr (sizeof(T) == 4 && MODEL == kFR && UNSCALED && !WEIGHTED && SRC == kSrcShared) {
+            // the blocked kernel's FP32 term with packed two-lane FP32
+            // arithmetic (sm_100 and later): one subtraction forms
+            // (dx, dy) and one fused multiply-add accumulates c (dx, dy)
+            const P2 pv = src(v);
+            uint64_t pu, pp, dd, cc, ac;
+            asm("mov.b64 %0, {%1, %2};" : "=l"(pu) : "f"(xu), "f"(yu));
+            asm("mov.b64 %0, {%1, %2};" : "=l"(pp) : "f"(pv.x), "f"(pv.y));
+            asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dd) : "l"(pu), "l"(pp));
+            float dx, dy;
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(dx), "=f"(dy) : "l"(dd));
+            const float c = rep_fr1(dx, dy);
+            asm("mov.b64 %0, {%1, %1};" : "=l"(cc) : "f"(c));
+            asm("mov.b64 %0, {%1, %2};" : "=l"(ac) : "f"(a.sx), "f"(a.sy));
+            asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(ac) : "l"(cc), "l"(dd));
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(a.sx), "=f"(a.sy) : "l"(ac));
+            return;
+        }
         const P2 pv = src(v);
         const T dx = xu - pv.x, dy = yu - pv.y;
         T c;

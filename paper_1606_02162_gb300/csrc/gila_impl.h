@@ -99,7 +99,7 @@ struct TilePlan {
     size_t blk_cap = 0;
     int64_t* toff = nullptr;         // nt n: start of (tile j, row u) in tk
     size_t toff_cap = 0;
-    uint32_t* tk = nullptr;          // ids in block order
+    uint16_t* tk = nullptr;          // tile-relative 16-bit ids in block order
     size_t tk_cap = 0;
     void* part = nullptr;            // nt n x 4 T partial forces
     size_t part_cap = 0;
@@ -119,7 +119,7 @@ struct TilePlan {
 
 struct ProfileRec {
     cudaEvent_t a, b;
-    int kind;  // 0 build, 1 iterations
+    int kind;  // 0 build (or blocked plan), 1 iterations, 2 one repulsion kernel
     int64_t launches;
 };
 
@@ -156,11 +156,13 @@ struct gila_graph {
     // test hook: blocked-path tiles are announced but not copied, so their
     // bounded waits run out (failure-detection test)
     int wait_test = 0;
-    // profiling
-    bool prof_on = false;
+    // profiling: 0 off, 1 builds and iteration sequences, 2 also the
+    // repulsion kernel of every iteration on its own
+    int prof_on = 0;
     std::vector<gila::ProfileRec> prof;
-    int64_t prof_builds = 0, prof_launches = 0;
-    double prof_build_ms = 0.0, prof_iter_ms = 0.0;
+    int64_t prof_builds = 0, prof_launches = 0, prof_kernel_launches = 0;
+    double prof_build_ms = 0.0, prof_iter_ms = 0.0, prof_kernel_ms = 0.0;
+    const char* prof_kernel_name = "";
 };
 
 namespace gila {
@@ -214,5 +216,11 @@ gila_status scan_exclusive_i64(const int64_t* in, int64_t n, int64_t* out, cudaS
 
 // Count one kernel launch issued by the library (all launch sites call it).
 void count_launch();
+
+// Profiling mode 2: an event recorded on g's stream before the repulsion
+// kernel of an iteration (null when the mode is off), and the matching end
+// record after it, kept with the kernel's name.
+cudaEvent_t prof_kernel_begin(gila_graph* g);
+void prof_kernel_end(gila_graph* g, cudaEvent_t a, const char* name);
 
 }  // namespace gila

@@ -307,6 +307,93 @@ __device__ __forceinline__ double dipow(double x, int e)
     return r;
 }
 
+// Double-float arithmetic: a value held as an unevaluated sum hi + lo of
+// two FP32 numbers (|lo| at most half an ulp of hi), 48 significant bits.
+// The building blocks are the exact error-free transformations of Knuth
+// (two-sum) and Dekker (two-product, here through a fused multiply-add);
+// every FP32 operation below is an explicitly rounded intrinsic, so the
+// compiler neither contracts nor reorders them.
+struct Ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ Ff ff_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, err};
+}
+
+// |a| >= |b| (or a = 0)
+__device__ __forceinline__ Ff ff_fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ Ff ff_two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ Ff ff_from_double(double x)
+{
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ Ff ff_add(Ff a, Ff b)
+{
+    const Ff s = ff_two_sum(a.hi, b.hi);
+    return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ Ff ff_mul(Ff a, Ff b)
+{
+    const Ff p = ff_two_prod(a.hi, b.hi);
+    const float c = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
+    return ff_fast_two_sum(p.hi, __fadd_rn(p.lo, c));
+}
+
+// |x_u - x_v|^2 from FP32 coordinates: the differences are exact as
+// double-floats (two-sum), their squares exact as double-floats
+// (two-product); only the square of each difference's low part (below
+// 2^-48 of the result) is left out.
+__device__ __forceinline__ Ff ff_dist2(float ax, float ay, float bx, float by)
+{
+    const Ff dx = ff_two_sum(ax, -bx);
+    const Ff dy = ff_two_sum(ay, -by);
+    const Ff px = ff_two_prod(dx.hi, dx.hi);
+    const Ff py = ff_two_prod(dy.hi, dy.hi);
+    const Ff s = ff_two_sum(px.hi, py.hi);
+    const float cross = __fmaf_rn(2.0f * dx.hi, dx.lo, __fmul_rn(2.0f * dy.hi, dy.lo));
+    const float low = __fadd_rn(__fadd_rn(s.lo, __fadd_rn(px.lo, py.lo)), cross);
+    return ff_fast_two_sum(s.hi, low);
+}
+
+// (1 / sqrt(r2))^q for r2 = hi + lo > 0 (q >= 0): the hardware's
+// approximate reciprocal square root y0 of hi (relative error below 2^-22)
+// refined by the series y = y0 (1 + e/2 + 3e^2/8) of y0 / sqrt(1 - e), with
+// e = 1 - r2 y0^2 formed exactly up to the rounding of its low parts (the
+// classical Newton step for the inverse square root carried one order
+// further); then q double-float products.
+__device__ __forceinline__ Ff ff_rsqrt_pow(Ff r2, int q)
+{
+    float y0;
+    asm("rsqrt.approx.f32 %0, %1;" : "=f"(y0) : "f"(r2.hi));
+    const Ff y2 = ff_two_prod(y0, y0);
+    const Ff t = ff_two_prod(r2.hi, y2.hi);
+    const float tl = __fadd_rn(t.lo, __fmaf_rn(r2.hi, y2.lo, __fmul_rn(r2.lo, y2.hi)));
+    const float e = __fsub_rn(__fsub_rn(1.0f, t.hi), tl);  // 1 - t.hi is exact near 1
+    const float corr = __fmul_rn(y0, __fmaf_rn(0.375f * e, e, 0.5f * e));
+    const Ff y = ff_fast_two_sum(y0, corr);
+    Ff r = {1.0f, 0.0f};
+    for (int i = 0; i < q; ++i) r = ff_mul(r, y);
+    return r;
+}
+
 // pass 0: [sum delta, count, sum delta^p/d, sum over k-hop pairs d^2/delta^q]
 // pass 1: [sum (delta - mean)^2, 0, 0, 0]
 // Each warp owns a fixed set of vertices; partial sums are combined in a
@@ -339,18 +426,19 @@ metrics_kernel(int pass, int64_t n, const int64_t* __restrict__ row,
             }
         }
         if (pass == 0 && sizeof(T) == 4) {
-            // FP32 placements: each pair's term d^2 / delta^q in FP32 (one
-            // approximate reciprocal square root, relative error below 1e-6),
-            // eight terms per lane summed in FP32 (all positive), then added
-            // in FP64. FP64 sqrt and divide per pair would make this pass
-            // ALU-bound on GB300's low FP64 rate; eight independent loads per
-            // lane halve the rounds a warp walks a hub's row in
+            // FP32 placements: each pair's term d^2 / delta^q in double-float
+            // arithmetic (pairs of FP32 numbers, relative error about 1e-14,
+            // far below FP32's 6e-8), eight terms per lane summed as a
+            // double-float, then added in FP64. The FP64 pipe of GB300 is a
+            // small fraction of its FP32 rate, and a per-pair FP64 sqrt and
+            // divide made this pass ALU-bound; the pair form keeps FP64
+            // accuracy at FP32 throughput.
             const float2* pf = reinterpret_cast<const float2*>(pos);
             const float2 qu = pf[u];
-            const float d2f = (float)(d * d);
+            const Ff d2f = ff_from_double(d * d);
             const int64_t e1 = krow[u + 1];
             for (int64_t e0 = krow[u]; e0 < e1; e0 += 256) {
-                float s = 0.f;
+                Ff s = {0.f, 0.f};
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int64_t e = e0 + j * 32 + lane;
@@ -358,18 +446,20 @@ metrics_kernel(int pass, int64_t n, const int64_t* __restrict__ row,
                     const int64_t v = kcol[e];
                     if (v <= u) continue;
                     const float2 pv = pf[v];
-                    const float dx = qu.x - pv.x, dy = qu.y - pv.y;
-                    const float r2 = dx * dx + dy * dy;
-                    if (r2 >= 1e-30f) {
-                        const float ir = rsqrt_fast(r2);
-                        float w = ir;
-                        for (int i = 1; i < q; ++i) w *= ir;
-                        s += d2f * w;
-                    } else if (r2 > 0.f) {  // tiny distances: exact FP64 term
-                        a3 += d * d / dipow(sqrt((double)r2), q);
+                    const Ff r2 = ff_dist2(qu.x, qu.y, pv.x, pv.y);
+                    if (r2.hi >= 1e-30f && r2.hi <= 1e30f) {
+                        s = ff_add(s, ff_mul(d2f, ff_rsqrt_pow(r2, q)));
+                    } else {
+                        // distances outside the pair form's safe range (or
+                        // coincident vertices): the FP64 term from the exact
+                        // FP64 differences, none at distance 0
+                        const double dx = (double)qu.x - (double)pv.x;
+                        const double dy = (double)qu.y - (double)pv.y;
+                        const double dl = sqrt(dx * dx + dy * dy);
+                        if (dl > 0.0) a3 += d * d / dipow(dl, q);
                     }
                 }
-                a3 += (double)s;
+                a3 += (double)s.hi + (double)s.lo;
             }
         } else if (pass == 0) {
             for (int64_t e = krow[u] + lane; e < krow[u + 1]; e += 32) {
@@ -478,11 +568,13 @@ gila_status launch_iteration(gila_graph* g, const gila_params* prm, double t, co
         if (g->wt64) return fail(GILA_EINVAL, "GILA_FP64_ORDERED takes no repulsion weights");
         if (g->n == 0) return GILA_OK;
         const unsigned grid = (unsigned)((g->n * 32 + kThreads - 1) / kThreads);
+        cudaEvent_t pa = prof_kernel_begin(g);
         ordered_kernel<<<grid, kThreads, 0, g->stream>>>(
             g->n, g->row, g->col, g->krow, g->kcol, prm->d, prm->p, prm->q, t,
             (const double2*)pos_in, (double2*)pos_out, (double2*)disp_out);
         count_launch();
         cudaError_t e = cudaGetLastError();
+        prof_kernel_end(g, pa, "ordered_kernel");
         if (e != cudaSuccess) return cuda_fail(e, "ordered_kernel");
         return GILA_OK;
     }
@@ -518,6 +610,7 @@ gila_status launch_iteration(gila_graph* g, const gila_params* prm, double t, co
     if (grid == 0) return GILA_OK;
     const bool fr = (prm->p == 2 && prm->q == 1);
     cudaError_t e;
+    cudaEvent_t pa = prof_kernel_begin(g);
     switch (prm->precision) {
     case GILA_FP64:
         e = fr ? launch_typed<double, kFR, false>(A, (unsigned)grid, g->stream)
@@ -532,6 +625,7 @@ gila_status launch_iteration(gila_graph* g, const gila_params* prm, double t, co
                : launch_typed<float, kGeneric, false>(A, (unsigned)grid, g->stream);
         break;
     }
+    prof_kernel_end(g, pa, "iteration_kernel");
     if (e != cudaSuccess) return cuda_fail(e, "iteration_kernel");
     return GILA_OK;
 }

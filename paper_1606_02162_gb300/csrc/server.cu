@@ -114,14 +114,15 @@ size_t job_bytes(int64_t n, int64_t nnz_adj, int64_t nnz_khop, int precision,
     b += 12 * (size_t)n;                                // row classes, spare
     b += 2 * esz * (size_t)n + 16 * (size_t)n;          // placement buffers, staging
     if (blocked_auto_applies(n, nnz_khop, esz, tune)) {
-        // blocked-path plan: the ids once more in block order (each block
-        // padded by at most 7 entries per thread of its CTA), and per row and
-        // tile an offset, a length and a partial force
+        // blocked-path plan: the ids once more in block order as 16-bit
+        // tile-relative ids (each row's segment per tile padded by at most 7
+        // entries, each block by at most 15 per thread of its CTA), and per
+        // row and tile an offset, a length and a partial force
         const int64_t tv = (200 * 1024) / (int64_t)esz;
         const int64_t nt = (n + tv - 1) / std::max<int64_t>(tv, 1);
         const int64_t nr = std::max<int64_t>(8 * 152 / nt + 1, n / 4096 + 1);
-        b += 4 * (size_t)nnz_khop + (16 + 2 * esz) * (size_t)n * (size_t)nt + (1 << 16);
-        b += 4 * 7 * 1024 * (size_t)(nt * nr);
+        b += 2 * (size_t)nnz_khop + (14 + 16 + 2 * esz) * (size_t)n * (size_t)nt + (1 << 16);
+        b += 2 * 15 * 1024 * (size_t)(nt * nr);
     }
     return b + ((size_t)1 << 20);
 }

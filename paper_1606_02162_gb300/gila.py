@@ -103,6 +103,7 @@ SIGNATURES = [
     ("gila_temperature", D, [PP, D, I32]),
     ("gila_profile_enable", ctypes.c_int, [P, I32]),
     ("gila_profile_read", ctypes.c_int, [P, P, P, P, P]),
+    ("gila_profile_read_kernel", ctypes.c_int, [P, P, P, ctypes.c_char_p, I32]),
     ("gila_last_error", ctypes.c_char_p, []),
     ("gila_kernel_launches", ctypes.c_int64, []),
     ("gila_khop_count_noalloc", ctypes.c_int, [I64, P, P, I32, P, ctypes.POINTER(I64), P]),
@@ -112,6 +113,7 @@ SIGNATURES = [
     ("gila_batch_info", ctypes.c_int, [P, P, P, P]),
     ("gila_batch_build_khop", ctypes.c_int, [P, I32, ctypes.POINTER(I64)]),
     ("gila_batch_khop_reset", ctypes.c_int, [P]),
+    ("gila_batch_khop_export", ctypes.c_int, [P, P, P]),
     ("gila_batch_tune", ctypes.c_int, [P, ctypes.POINTER(gila_batch_tuning)]),
     ("gila_batch_get_tuning", ctypes.c_int, [P, I32, ctypes.POINTER(gila_batch_tuning)]),
     ("gila_batch_autotune", ctypes.c_int, [P, PP, P, I32, ctypes.POINTER(gila_batch_tuning)]),
@@ -322,7 +324,9 @@ def gila_temperature(prm, t0, i) -> float:
 
 
 def gila_profile_enable(g, on=True) -> None:
-    _check(load().gila_profile_enable(g, 1 if on else 0))
+    """on: False/0 off, True/1 builds and iteration sequences, 2 also each
+    iteration's repulsion kernel on its own."""
+    _check(load().gila_profile_enable(g, int(on)))
 
 
 def gila_profile_read(g) -> dict:
@@ -331,6 +335,13 @@ def gila_profile_read(g) -> dict:
                                     ctypes.byref(ims)))
     return {"builds": b.value, "build_ms": bms.value, "iter_launches": it.value,
             "iter_ms": ims.value}
+
+
+def gila_profile_read_kernel(g) -> dict:
+    n, ms = I64(), D()
+    name = ctypes.create_string_buffer(64)
+    _check(load().gila_profile_read_kernel(g, ctypes.byref(n), ctypes.byref(ms), name, 64))
+    return {"launches": n.value, "ms": ms.value, "name": name.value.decode()}
 
 
 class Graph:
@@ -408,6 +419,15 @@ def gila_batch_build_khop(b, k) -> int:
 
 def gila_batch_khop_reset(b) -> None:
     _check(load().gila_batch_khop_reset(b))
+
+
+def gila_batch_khop_export(b):
+    """The whole batch's k-hop lists (union numbering): (krow, kcol)."""
+    info = gila_batch_info(b)
+    krow = np.zeros(info["total_n"] + 1, dtype=np.int64)
+    kcol = np.zeros(max(info["nnz_khop"], 1), dtype=np.int32)
+    _check(load().gila_batch_khop_export(b, _ptr(krow), _ptr(kcol)))
+    return krow, kcol[: info["nnz_khop"]]
 
 
 def gila_batch_tune(b, threads=0, ctas_per_sm=0, group4_max=0, group8_max=0,

@@ -85,9 +85,10 @@ def test_components_layout_matches_oracle_few_iterations(prec, iters):
 @pytest.mark.parametrize("schedule", [O.SCHED_LINEAR, O.SCHED_GEOM], ids=["linear", "geom"])
 def test_components_layout_whole_run_quality(schedule):
     """200 iterations in FP32: edge-length CV and repulsive/attractive ratio of
-    the packed drawing within 2% of the oracle's (both are unchanged by the
-    packing, which only translates components)."""
-    _torch()
+    the packed drawing (the library's FP64 reductions) within 2% of the
+    oracle's (both are unchanged by the packing, which only translates
+    components)."""
+    torch = _torch()
     g = _mixed_graph()
     pos = I.uniform_positions(g.n, 8)
     iters = 200
@@ -98,7 +99,9 @@ def test_components_layout_whole_run_quality(schedule):
             h.handle, G.params(k=2, iters=iters, schedule=schedule), pos)
     krow, kcol = O.khop(g.n, g.row_ptr, g.col_idx, 2)
     mo = O.metrics(g.n, g.row_ptr, g.col_idx, krow, kcol, ref)
-    mg = O.metrics(g.n, g.row_ptr, g.col_idx, krow, kcol, out)
+    with G.Graph.from_inputs(g) as h:
+        mg = G.gila_layout_metrics(h.handle, G.params(k=2, iters=iters, schedule=schedule),
+                                   torch.tensor(out, dtype=torch.float32, device="cuda"))
     for key in ("edge_cv", "rep_att_ratio"):
         assert abs(mg[key] - mo[key]) <= 0.02 * abs(mo[key]), (key, mg[key], mo[key])
 

@@ -6,12 +6,19 @@ bit-exact, one step of all vertices against the oracle, and whole 300-
 iteration layouts within 2% of the oracle's in edge-length CV and the
 repulsive/attractive ratio.
 
-Chung-Lu, gamma = 2.3, n = 250,000, 1,000,000 edges: about 1.5e10 k-hop
-entries (60 GB of ids), beyond what the oracle can build for every vertex.
+Chung-Lu, gamma = 2.3, n = 250,000, 1,000,000 edges: about 1.1e10 k-hop
+entries (45 GB of ids), beyond what the oracle can build for every vertex.
 Checked on sampled outputs the oracle computes one by one (k-hop rows of hubs,
-ordinary and isolated vertices; the resultant force of sampled vertices) and
-through properties that hold at any size (the forces sum to zero; FP32,
-compensated FP32 and FP64 layouts agree).
+ordinary and isolated vertices; the resultant force of sampled vertices; the
+capped moves of a systematic sample of 2,048 vertices and the hubs, in every
+precision, in the benchmark's launch configuration) and through properties
+that hold at any size (the forces sum to zero; FP32, compensated FP32 and
+FP64 layouts agree). The FP64 mode is validated over the first 10 iterations
+on a Chung-Lu graph of the same shape that the oracle lays out whole
+(n = 20,000, 80,000 edges, k = 3, 1.4e8 k-hop entries), with the position
+tiles of the blocked path cut to 2,000 vertices so that it runs in 10 tiles
+as the full-size graph does: each GPU step from the oracle's placement of
+that iteration within 1e-12 of the largest move.
 """
 import math
 
@@ -176,3 +183,77 @@ def test_chunglu_whole_layouts_agree_across_precisions(chunglu):
         for key in ("edge_cv", "rep_att_ratio"):
             assert abs(res[a][key] - res[b][key]) <= 0.02 * abs(res[b][key]), \
                 (a, b, key, res[a][key], res[b][key])
+
+
+@pytest.fixture(scope="module")
+def chunglu_sample(chunglu):
+    """A systematic sample of 2,048 vertices and the 16 largest hubs, with the
+    oracle's k-hop rows of exactly those vertices."""
+    g, _, _, _, _ = chunglu
+    deg = np.diff(g.row_ptr)
+    sys_sel = np.arange(0, g.n, g.n // 2048, dtype=np.int64)[:2048]
+    hubs = np.argsort(-deg, kind="stable")[:16]
+    sel = np.unique(np.concatenate([sys_sel, hubs]))
+    counts, rows = O.khop_rows(g.n, g.row_ptr, g.col_idx, 3, sel)
+    krow, kcol = _partial_khop(g, sel, counts, rows)
+    return sel, krow, kcol
+
+
+@pytest.mark.parametrize("prec,tol", [(G.GILA_FP32_COMPENSATED, 1e-4), (G.GILA_FP32, 1e-4),
+                                      (G.GILA_FP64, 1e-12)], ids=["fp32c", "fp32", "fp64"])
+def test_chunglu_capped_moves_sample(chunglu, chunglu_sample, prec, tol):
+    """One iteration at the linear schedule's first temperature (0.1 sqrt(n)
+    = 50, which caps the hubs) in the benchmark's launch configuration: the
+    capped moves of the sample against the oracle's. The oracle's step runs
+    on a k-hop CSR that holds only the sample's rows, so only those moves are
+    complete and compared."""
+    torch = _torch()
+    g, pos, h, _, _ = chunglu
+    sel, krow, kcol = chunglu_sample
+    t = 0.1 * math.sqrt(g.n)
+    dt = torch.float64 if prec == G.GILA_FP64 else torch.float32
+    x = torch.tensor(pos, dtype=dt, device="cuda")
+    y, disp = torch.empty_like(x), torch.empty_like(x)
+    G.gila_profile_enable(h.handle, 2)
+    G.gila_layout_step(h.handle, G.params(k=3, precision=prec), t, x, y, disp)
+    G.gila_profile_read(h.handle)
+    assert G.gila_profile_read_kernel(h.handle)["name"] == "blocked_kernel"
+    G.gila_profile_enable(h.handle, 0)
+    got = disp.double().cpu().numpy()[sel]
+    base = x.double().cpu().numpy()
+    _, odisp = O.step(g.n, g.row_ptr, g.col_idx, krow, kcol, base, t)
+    odisp = odisp[sel]
+    assert np.abs(got - odisp).max() <= tol * np.abs(odisp).max()
+    # the hubs are capped: their move has length t
+    capped = np.linalg.norm(odisp, axis=1) > 0.999 * t
+    assert capped.sum() >= 8
+
+
+def test_chunglu_shape_fp64_first_ten_iterations():
+    """FP64 mode over the first 10 iterations of a 300-iteration linear
+    schedule on a Chung-Lu graph of the configuration's shape, blocked path
+    in 10 tiles: every GPU step from the oracle's placement of that
+    iteration within 1e-12 of the largest move."""
+    torch = _torch()
+    __graft_entry__.build()
+    g = I.chung_lu(20000, 2.3, 8.0, 80000, 31)
+    pos = I.uniform_positions(g.n, 32)
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, 3)
+    prm = G.params(k=3, iters=300, precision=G.GILA_FP64)
+    t0 = 0.1 * math.sqrt(g.n)
+    with G.Graph.from_inputs(g) as h:
+        G.gila_graph_tune(h.handle, tiled=1, tile_vertices=2000)
+        G.gila_profile_enable(h.handle, 2)
+        x = pos.copy()
+        for i in range(10):
+            t = O.temperature(O.SCHED_LINEAR, t0, i, 300)
+            assert t == pytest.approx(G.gila_temperature(prm, t0, i), rel=1e-15)
+            xin = torch.tensor(x, dtype=torch.float64, device="cuda")
+            y, disp = torch.empty_like(xin), torch.empty_like(xin)
+            G.gila_layout_step(h.handle, prm, t, xin, y, disp)
+            xnext, odisp = O.step(g.n, g.row_ptr, g.col_idx, okrow, okcol, x, t)
+            got = disp.cpu().numpy()
+            assert np.abs(got - odisp).max() <= 1e-12 * np.abs(odisp).max(), i
+            x = xnext
+        G.gila_profile_read(h.handle)
+        assert G.gila_profile_read_kernel(h.handle)["name"] == "blocked_kernel"

@@ -182,7 +182,10 @@ def test_pipeline_whole_run_quality(prec):
         got = G.gila_layout_pruned_run(p.handle, prm, pos0)
     krow, kcol = O.khop(g.n, g.row_ptr, g.col_idx, k)
     mo = O.metrics(g.n, g.row_ptr, g.col_idx, krow, kcol, ref)
-    mg = O.metrics(g.n, g.row_ptr, g.col_idx, krow, kcol, got)
+    torch = _torch()
+    dt = torch.float64 if prec == G.GILA_FP64 else torch.float32
+    with G.Graph.from_inputs(g) as h:
+        mg = G.gila_layout_metrics(h.handle, prm, torch.tensor(got, dtype=dt, device="cuda"))
     for key in ("edge_cv", "rep_att_ratio"):
         assert abs(mg[key] - mo[key]) <= 0.02 * abs(mo[key]), (key, mg[key], mo[key])
 
