@@ -596,7 +596,7 @@ def roofline_of(g, P, nnzk, elem, iter_ms, kern, hbm, peak_kind, tr):
     bandwidth. The 12 B/pair gather model (a 4 B id and a float2 position per
     pair, every gather counted as HBM traffic) is kept as a second figure;
     it exceeds 1 wherever positions come from shared memory."""
-    blocked = bool(kern) and kern.get("name") == "blocked_kernel"
+    blocked = bool(kern) and kern.get("name", "").startswith("blocked_kernel")
     id_bytes = 2 if blocked else 4
     nnza = P - nnzk
     comp = id_bytes * nnzk + 4 * nnza + 8 * (g.n + 1) + 2 * elem * g.n

@@ -110,18 +110,22 @@ typedef struct gila_metrics {
  * FP32 sums (different summation trees). Zero fields keep the defaults. */
 typedef struct gila_tuning {
     int32_t tiled;         /* -1 automatic (default), 0 never, 1 always: stage positions in
-                              shared-memory tiles instead of gathering them through L2 (with
-                              1, graphs whose row ranges touch narrow id windows get one
-                              window per range, read in place) */
+                              shared memory instead of gathering them through L2. Graphs
+                              whose row ranges touch narrow id windows get one window per
+                              range, and each range's CTA finishes its rows (automatic mode:
+                              where the windows' positions stay below the id stream's
+                              bytes); other graphs get tiles of positions and a second
+                              kernel that adds each row's tile partials */
     int32_t tile_vertices; /* positions per tile; 0 = as many as fit in 200 KiB */
-    int32_t min_segment;   /* automatic mode tiles placements with at least 10^8 k-hop
-                              entries when nnz_khop / (n * tiles) >= this (48) */
+    int32_t min_segment;   /* automatic mode tiles placements with at least 4 10^6 k-hop
+                              entries when nnz_khop / (n * tiles) >= this (0: always) */
     int32_t small_max;     /* untiled kernel: rows of length <= this use 8-lane groups (64) */
     int32_t warp_max;      /* ... rows <= this use one warp (8192) */
     int32_t block_max;     /* ... rows <= this use one block (65536); longer rows are chunked */
     int32_t chunk;         /* entries per chunk of a chunked row (32768) */
     int32_t ctas_per_sm;   /* blocked path: row ranges per tile chosen so that the grid holds
-                              about this many CTAs per SM (4; 8 from 2e9 k-hop entries) */
+                              about this many CTAs per SM (tiles: 1 below 10^8 k-hop
+                              entries, 4 below 2e9, 8 beyond; windows: 2) */
     int32_t bank_spread;   /* blocked path: 0 or 1 (default on) orders each row's entries of
                               a tile so that the lanes of one shared-memory gather read
                               distinct banks where the entries allow; -1 keeps ascending
@@ -502,15 +506,21 @@ int64_t gila_kernel_launches(void);
  * their sum. Work runs on cuda_stream (NULL = legacy default stream) and the
  * call returns after it has finished.
  *
- * Scratch lives in one fixed device array inside the library (about 5.1 MiB,
- * present on every device that loads the library until the process exits),
+ * Scratch lives in one fixed device array inside the library (about 5.1 MiB)
  * which bounds n to at most 262,144 vertices: larger n returns GILA_EINVAL
  * with a message. The call makes no cudaMalloc or cudaFree call and uses no
- * allocating library routine. The first call on a device looks up the
- * scratch address for that device (cudaGetSymbolAddress with the device
- * current); make that first call before any stream capture. Every call
- * reuses the same scratch: calls that overlap on the GPU (other threads,
- * other streams) race and must be serialised by the caller. */
+ * allocating library routine. The array is reserved when the library's
+ * k-hop module is loaded on a device: with CUDA's default lazy module
+ * loading that happens at the first k-hop call on that device (this one or
+ * gila_build_khop), and it then stays until the process exits. A caller
+ * whose memory manager reserves most of the device should therefore make
+ * one call at startup, before it reserves memory; that first call also
+ * looks up the array's address for the device (cudaGetSymbolAddress with
+ * the device current). Every call synchronises cuda_stream and copies the
+ * total to the host, so it cannot be recorded into a CUDA graph (calling it
+ * while the stream is being captured is an error). Every call reuses the
+ * same scratch: calls that overlap on the GPU (other threads, other
+ * streams) race and must be serialised by the caller. */
 gila_status gila_khop_count_noalloc(int64_t n, const int64_t* row_ptr_dev,
                                     const int32_t* col_idx_dev, int32_t k, int64_t* counts_dev,
                                     int64_t* total_host, void* cuda_stream);

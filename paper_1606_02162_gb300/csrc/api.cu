@@ -446,9 +446,10 @@ gila_status gila_graph_get_tuning(const gila_graph* g, gila_tuning* out)
 {
     if (!g || !out) return fail(GILA_EINVAL, "graph or out is NULL");
     *out = g->tune;
-    out->min_segment = g->tune.min_segment > 0 ? g->tune.min_segment : 48;
-    out->ctas_per_sm = g->tune.ctas_per_sm > 0 ? g->tune.ctas_per_sm
-                                               : (g->nnz_khop >= 2000000000LL ? 8 : 4);
+    out->min_segment = g->tune.min_segment;
+    out->ctas_per_sm = g->tune.ctas_per_sm > 0
+                           ? g->tune.ctas_per_sm
+                           : (int32_t)default_ctas_per_sm(g->nnz_khop, g->tplan[0].window);
     out->bank_spread = g->tune.bank_spread >= 0 ? 1 : -1;
     out->small_max = g->bins.cfg.small_max;
     out->warp_max = g->bins.cfg.warp_max;

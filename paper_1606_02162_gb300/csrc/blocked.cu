@@ -39,8 +39,10 @@ constexpr int kSmemCap = 227 * 1024;
 constexpr int kMaxRows = 4096;  // rows per range (directory in shared memory)
 constexpr int kTileBudget = kSmemCap - (kMaxRows + 1) * 4 - 4096;
 constexpr int64_t kMaxTile = 65534;  // tile-relative ids and the far slot's id fit 16 bits
+constexpr int64_t kConvergeSeg = 2048;  // mean entries per (tile, row) below which FP32 steps
+                                        // are taken warp-uniformly
 constexpr uint32_t kBulkChunk = 32768;      // bytes per bulk copy instruction
-constexpr int64_t kBlockedMinNnz = 100000000;  // automatic mode: k-hop entries needed (tiles)
+constexpr int64_t kBlockedMinNnz = 4000000;  // automatic mode: k-hop entries needed (tiles)
 constexpr uint64_t kWaitNs = 1000000000ull;  // bound on a tile wait (1 s, far above any copy)
 constexpr uint64_t kTestWaitNs = 1000000ull;   // the bound while the wait test hook is on
 // Every (tile j, row) segment is padded to a multiple of 8 entries with the
@@ -72,6 +74,18 @@ struct BlockedArgs {
     void* part;                // nt n cells of 4 T: (sx, sy, cx, cy) without the factor d^2
     uint64_t wait_ns;          // bound on the tile wait
     int skip_copy;             // test hook: announce the tile but copy nothing
+    // window mode (one window of positions per row range, rows finished in
+    // the CTA): first id and length of range r's window, the largest window
+    // and range, and what the finish needs
+    const int64_t* wbase;      // 2 nr
+    int32_t wmax, rmax;
+    const int64_t* row;
+    const int32_t* col;
+    double d, t;
+    int p;
+    void* pos_out;
+    void* disp_out;
+    int converge;              // FP32 steps taken warp-uniformly (short segments)
 };
 
 template <class T, bool COMP>
@@ -123,26 +137,78 @@ __host__ __device__ __forceinline__ int32_t lane_len(int32_t L)
     return (L == 0) ? 0 : ((L / kBThreads + 2 * kStep - 1) & ~(kStep - 1));
 }
 
+// acc += (x, y) with a two-sum error term per component; in FP32 both
+// components go through packed two-lane operations (six instead of twelve).
+template <class T, bool COMP>
+__device__ __forceinline__ void add_compensated(Acc<T, COMP>& acc, T x, T y)
+{
+    if constexpr (sizeof(T) == 4 && COMP) {
+        uint64_t s, c, v, t, bp, e1, e2;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(s) : "f"(acc.sx), "f"(acc.sy));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(c) : "f"(acc.cx), "f"(acc.cy));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(x), "f"(y));
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(s), "l"(v));    // t = s + v
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(bp) : "l"(t), "l"(s));   // bp = t - s
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(e1) : "l"(t), "l"(bp));  // t - bp
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(e1) : "l"(s), "l"(e1));  // s - (t - bp)
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(e2) : "l"(v), "l"(bp));  // v - bp
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(e1) : "l"(e1), "l"(e2));
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(c) : "l"(c), "l"(e1));
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(acc.sx), "=f"(acc.sy) : "l"(t));
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(acc.cx), "=f"(acc.cy) : "l"(c));
+    } else {
+        acc.merge(x, y, T(0), T(0));
+    }
+}
+
+// Window mode's finish of the rows [u0, u0 + nrows) of a range, after their
+// cells (sum of the unscaled repulsion terms, with compensation) are
+// complete in shared memory: F = d^2 cell + attraction, then the capped move.
+// Rows with at most kFinishDeg neighbours take one thread each; longer ones
+// are listed in row order (a block scan, so the list does not depend on
+// timing) and taken by whole warps, lanes striding the adjacency row. Every
+// row's order of additions is fixed.
 template <class T, int MODEL, bool COMP>
+__device__ __forceinline__ void window_finish(const struct BlockedArgs& A,
+                                              const typename V2<T>::type* tile, int64_t tb,
+                                              const typename V2<T>::type* cells, int64_t u0,
+                                              int nrows);
+
+// Window mode's finish: rows whose adjacency row is longer than this are
+// finished by a whole warp (a few per range), the others by one thread.
+constexpr int kFinishDeg = 32;
+
+template <class T, int MODEL, bool COMP, bool WIN>
 __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs A)
 {
     using P2 = typename V2<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    // shared memory: the tile (or the range's window) with one more slot for
+    // the padding's far position, the row directory, and in window mode the
+    // rows' force cells
+    const int tcap = WIN ? A.wmax : A.tv;
     P2* tile = reinterpret_cast<P2*>(smem_raw);
-    int32_t* D = reinterpret_cast<int32_t*>(smem_raw + (size_t)(A.tv + 1) * sizeof(P2));
+    int32_t* D = reinterpret_cast<int32_t*>(smem_raw + (size_t)(tcap + 1) * sizeof(P2));
+    P2* cells = reinterpret_cast<P2*>(
+        smem_raw + (((size_t)(tcap + 1) * sizeof(P2) + (size_t)(A.rmax + 1) * 4 + 15) & ~size_t(15)));
     __shared__ Slot<T, COMP> head[kBWarps], tail[kBWarps];
     __shared__ __align__(8) uint64_t tile_bar;
     __shared__ int tile_ok;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int j = blockIdx.x / A.nr, r = blockIdx.x % A.nr;
+    const int j = WIN ? 0 : blockIdx.x / A.nr, r = WIN ? blockIdx.x : blockIdx.x % A.nr;
     const int64_t u0 = A.range_start[r], u1 = A.range_start[r + 1];
     const int nrows = (int)(u1 - u0);
     const int64_t bsp = A.blk[2 * (int64_t)blockIdx.x];  // the block's first slot in tk
     // a block holds at most kMaxRows segments of at most tv entries: < 2^31
     const int32_t L = (int32_t)A.blk[2 * (int64_t)blockIdx.x + 1];
     const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos);
-    const int64_t tb = (int64_t)j * A.tv;
-    const int64_t tn = (A.n - tb < A.tv) ? A.n - tb : (int64_t)A.tv;
+    const int64_t tb = WIN ? A.wbase[2 * r] : (int64_t)j * A.tv;
+    const int64_t tn = WIN ? A.wbase[2 * r + 1] : ((A.n - tb < A.tv) ? A.n - tb : (int64_t)A.tv);
+    // the cell of row i of the range: in shared memory (window mode) or the
+    // global partial of (tile j, row u0 + i)
+    auto cellp = [&](int64_t i) -> P2* {
+        return WIN ? cells + 2 * i : cell_ptr<T>(A.part, A.n, j, u0 + i);
+    };
     if (threadIdx.x == 0) {
         // tile j by the bulk-copy engine (tv is even and the placement is
         // 16-byte aligned, so the source is too); an odd float2 tail by hand
@@ -157,13 +223,13 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
         P2 far;  // the padding's slot, outside the copied range
         far.x = FarSlot<T>::v;
         far.y = FarSlot<T>::v;
-        tile[A.tv] = far;
+        tile[WIN ? tn : (int64_t)A.tv] = far;
     }
     // meanwhile: the row directory (segment starts within the block) and
     // zero partials for rows with no entries in this tile
     for (int i = threadIdx.x; i < nrows; i += kBThreads) {
         D[i] = (int32_t)A.toff[(int64_t)j * A.n + u0 + i];
-        P2* c = cell_ptr<T>(A.part, A.n, j, u0 + i);
+        P2* c = cellp(i);
         P2 z;
         z.x = T(0);
         z.y = T(0);
@@ -230,7 +296,7 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                 first = acc;
                 in_first = false;
             } else {
-                store_cell<T, COMP>(cell_ptr<T>(A.part, A.n, j, u0 + ri), acc);
+                store_cell<T, COMP>(cellp(ri), acc);
             }
             acc = Acc<T, COMP>();
             ri = nx;
@@ -276,7 +342,7 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                 f(c.z >> 16, s8);
                 f(c.w & 0xffffu, s8);
                 f(c.w >> 16, s8);
-                acc.merge(s8.sx, s8.sy, T(0), T(0));
+                add_compensated(acc, s8.sx, s8.sy);
             } else {
                 f(c.x & 0xffffu, acc);
                 f(c.x >> 16, acc);
@@ -308,6 +374,14 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                         while (p >= re) close_row();
                         eight(c);
                     }
+                } else if (A.converge) {
+                    // short segments (rows change often): only the closing of
+                    // rows diverges, the terms are issued once for the warp
+                    if (p >= lim && p < b) {
+                        while (p >= re) close_row();
+                        lim = (re < b) ? re : b;
+                    }
+                    if (p < b) eight(c);
                 } else if (p < lim) {
                     eight(c);
                 } else if (p < b) {
@@ -389,7 +463,7 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                 sl.v[2] = v.cx;
                 sl.v[3] = v.cy;
             } else {
-                store_cell<T, COMP>(cell_ptr<T>(A.part, A.n, j, u0 + row), v);
+                store_cell<T, COMP>(cellp(row), v);
             }
         };
         if (has_b) {
@@ -412,7 +486,7 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
         int cur = -1;
         Acc<T, COMP> sum;
         auto flush = [&]() {
-            if (cur >= 0) store_cell<T, COMP>(cell_ptr<T>(A.part, A.n, j, u0 + cur), sum);
+            if (cur >= 0) store_cell<T, COMP>(cellp(cur), sum);
         };
         for (int w = 0; w < kBWarps; ++w) {
             const Slot<T, COMP>* sl[2] = {&head[w], &tail[w]};
@@ -427,6 +501,93 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
             }
         }
         flush();
+    }
+    if constexpr (WIN) {
+        // every row of the range is complete here: F = d^2 (its cell) + the
+        // attraction over its adjacency row (whose neighbours lie in the
+        // window, as A is part of N(k)), then the capped move
+        __syncthreads();
+        window_finish<T, MODEL, COMP>(A, tile, tb, cells, u0, nrows);
+    }
+}
+
+constexpr int kFinishHubs = 256;  // rows per range finished by warps (more: by threads)
+
+template <class T, int MODEL, bool COMP>
+__device__ __forceinline__ void finish_row(const BlockedArgs& A, const Att<T, MODEL, COMP, kSrcShared>& att0,
+                                           const typename V2<T>::type* cells, int64_t u0, int i,
+                                           const Acc<T, COMP>& at)
+{
+    using P2 = typename V2<T>::type;
+    const P2 pu = reinterpret_cast<const P2*>(A.pos)[u0 + i];
+    const T d2 = (T)(A.d * A.d);
+    Acc<T, COMP> rep;
+    const P2 c0 = cells[2 * i];
+    rep.sx = c0.x * d2;
+    rep.sy = c0.y * d2;
+    if (COMP) {
+        const P2 c1 = cells[2 * i + 1];
+        rep.cx = c1.x * d2;
+        rep.cy = c1.y * d2;
+    }
+    rep.merge(at.sx, at.sy, at.cx, at.cy);
+    apply_move<T>(A.t, A.pos_out, A.disp_out, u0 + i, pu.x, pu.y, rep.fx(), rep.fy());
+}
+
+template <class T, int MODEL, bool COMP>
+__device__ __forceinline__ void window_finish(const BlockedArgs& A,
+                                              const typename V2<T>::type* tile, int64_t tb,
+                                              const typename V2<T>::type* cells, int64_t u0,
+                                              int nrows)
+{
+    using P2 = typename V2<T>::type;
+    __shared__ int s_scan[kBWarps + 1];
+    __shared__ int s_hub[kFinishHubs];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos);
+    Att<T, MODEL, COMP, kSrcShared> att;
+    att.src.set_shared(tile, (uint32_t)tb);
+    att.inv_d = (T)(1.0 / A.d);
+    att.p = A.p;
+    const uint32_t* col = reinterpret_cast<const uint32_t*>(A.col);
+    int nhub = 0;  // rows listed for the warps so far (the same in every thread)
+    for (int base = 0; base < nrows; base += kBThreads) {
+        const int i = base + (int)threadIdx.x;
+        const bool live = i < nrows;
+        int64_t rb = 0, re = 0;
+        if (live) {
+            rb = A.row[u0 + i];
+            re = A.row[u0 + i + 1];
+        }
+        const bool hub = live && re - rb > kFinishDeg;
+        int total;
+        const int incl = block_inclusive_scan<int, kBThreads>(hub ? 1 : 0, s_scan, &total);
+        const int slot = nhub + incl - 1;
+        if (hub && slot < kFinishHubs) {
+            s_hub[slot] = i;
+        } else if (live) {
+            Att<T, MODEL, COMP, kSrcShared> a1 = att;
+            const P2 pu = pos[u0 + i];
+            a1.xu = pu.x;
+            a1.yu = pu.y;
+            Acc<T, COMP> at;
+            row_sum_rel(col, rb, re, 0, 1, a1, at);
+            finish_row<T, MODEL, COMP>(A, att, cells, u0, i, at);
+        }
+        nhub += total;
+    }
+    __syncthreads();
+    const int nh = nhub < kFinishHubs ? nhub : kFinishHubs;
+    for (int h = warp; h < nh; h += kBWarps) {
+        const int i = s_hub[h];
+        const P2 pu = pos[u0 + i];
+        Att<T, MODEL, COMP, kSrcShared> a1 = att;
+        a1.xu = pu.x;
+        a1.yu = pu.y;
+        Acc<T, COMP> at;
+        row_sum_rel(col, A.row[u0 + i], A.row[u0 + i + 1], lane, 32, a1, at);
+        at.group_reduce(32);
+        if (lane == 0) finish_row<T, MODEL, COMP>(A, att, cells, u0, i, at);
     }
 }
 
@@ -554,103 +715,6 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(const CombineA
     if (live && gl == 0) finish_vertex<T, COMP>(A, u, pu.x, pu.y, rep, at);
 }
 
-// Window mode: one CTA per row range with the range's window of positions in
-// shared memory. Every row lies wholly in its range's window (attraction
-// too: the neighbours of u are in N_u(k)), so groups of G lanes form whole
-// rows, reduce them by shuffles and apply the capped move at once: no tile
-// partials and no second kernel. Groups advance together through the range
-// (warp-uniform trip counts) so the shuffles see whole warps.
-struct WindowArgs {
-    int32_t tv;                 // positions the shared-memory window holds
-    const int64_t* krow;
-    const uint32_t* kcol;
-    const int64_t* row;
-    const int32_t* col;
-    const int64_t* wtile;       // 2 nr: first id and length of range r's window
-    const int32_t* range_start;
-    int64_t n;
-    double d, t;
-    int p, q;
-    const void* pos_in;
-    void* pos_out;
-    void* disp_out;
-    uint64_t wait_ns;           // bound on the tile wait
-    int skip_copy;              // test hook: announce the tile but copy nothing
-};
-
-template <class T, int MODEL, bool COMP, int G>
-__global__ void __launch_bounds__(kBThreads, 1) window_kernel(const WindowArgs A)
-{
-    using P2 = typename V2<T>::type;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    P2* tile = reinterpret_cast<P2*>(smem_raw);
-    __shared__ __align__(8) uint64_t tile_bar;
-    __shared__ int tile_ok;
-    const int r = blockIdx.x;
-    const int64_t u0 = A.range_start[r], u1 = A.range_start[r + 1];
-    const int64_t tb = A.wtile[2 * r], tn = A.wtile[2 * r + 1];
-    // the range's k-hop and adjacency row offsets, staged beside the window
-    int64_t* KR = reinterpret_cast<int64_t*>(smem_raw + (size_t)A.tv * sizeof(P2));
-    int64_t* AR = KR + (kMaxRows + 1);
-    for (int64_t i = threadIdx.x; i <= u1 - u0; i += kBThreads) {
-        KR[i] = A.krow[u0 + i];
-        AR[i] = A.row[u0 + i];
-    }
-    const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos_in);
-    if (threadIdx.x == 0) {
-        // the window by the bulk-copy engine (first id even, placement
-        // 16-byte aligned); an odd float2 tail by hand
-        const uint32_t bytes = (uint32_t)(((size_t)tn * sizeof(P2)) & ~size_t(15));
-        mbar_init(&tile_bar, 1);
-        mbar_arrive_expect_tx(&tile_bar, bytes);
-        const unsigned char* src = reinterpret_cast<const unsigned char*>(pos + tb);
-        for (uint32_t o = 0; o < bytes && !A.skip_copy; o += kBulkChunk)
-            bulk_g2s(smem_raw + o, src + o, (bytes - o < kBulkChunk) ? bytes - o : kBulkChunk,
-                     &tile_bar);
-        if ((size_t)tn * sizeof(P2) != bytes) tile[tn - 1] = pos[tb + tn - 1];
-        bool ok = mbar_wait(&tile_bar, 0, A.wait_ns);
-        if (!ok) {
-            atomicExch(&g_tile_wait_failed, 1);
-            mbar_wait(&tile_bar, 0, A.wait_ns);
-        }
-        tile_ok = ok ? 1 : 0;
-    }
-    __syncthreads();
-    if (!tile_ok) return;
-    mbar_wait(&tile_bar, 0, A.wait_ns);
-    Rep<T, MODEL, COMP, kSrcShared> rep;
-    rep.src.set_shared(tile, (uint32_t)tb);
-    rep.d2 = (T)(A.d * A.d);
-    rep.q = A.q;
-    Att<T, MODEL, COMP, kSrcShared> att;
-    att.src.set_shared(tile, (uint32_t)tb);
-    att.inv_d = (T)(1.0 / A.d);
-    att.p = A.p;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gl = lane & (G - 1);
-    constexpr int kGroups = kBThreads / G, kPerWarp = 32 / G;
-    for (int64_t ub = u0 + (int64_t)warp * kPerWarp; ub < u1; ub += kGroups) {
-        const int64_t u = ub + lane / G;
-        const bool live = u < u1;
-        Acc<T, COMP> a;
-        P2 pu;
-        pu.x = T(0);
-        pu.y = T(0);
-        if (live) {
-            pu = pos[u];
-            rep.xu = pu.x;
-            rep.yu = pu.y;
-            const int64_t i = u - u0;
-            row_sum(A.kcol, KR[i], KR[i + 1], gl, G, rep, a);
-            att.xu = pu.x;
-            att.yu = pu.y;
-            row_sum_rel(reinterpret_cast<const uint32_t*>(A.col), AR[i], AR[i + 1], gl, G, att, a);
-        }
-        a.group_reduce(G);
-        if (live && gl == 0) apply_move<T>(A.t, A.pos_out, A.disp_out, u, pu.x, pu.y, a.fx(), a.fy());
-    }
-}
-
 // Length of row u's segment in tile j (binary search on the sorted row).
 __device__ __forceinline__ void seg_bounds(const int64_t* __restrict__ krow,
                                            const uint32_t* __restrict__ kcol, int64_t u, int j,
@@ -706,8 +770,9 @@ constexpr int kSpreadChunk = 1024;
 template <int G, bool SPREAD>
 __global__ void __launch_bounds__(kSpreadWarps * 32) block_layout_kernel(
     int64_t n, const int64_t* __restrict__ krow, const uint32_t* __restrict__ kcol, int nt,
-    int tv, const int64_t* __restrict__ toff, const int64_t* __restrict__ blk,
-    const int32_t* __restrict__ range_start, int nr, uint16_t* __restrict__ tk)
+    int tv, const int64_t* __restrict__ wbase, const int64_t* __restrict__ toff,
+    const int64_t* __restrict__ blk, const int32_t* __restrict__ range_start, int nr,
+    uint16_t* __restrict__ tk)
 {
     __shared__ uint32_t s_in[kSpreadWarps][kSpreadChunk];  // the chunk's ids by residue
     __shared__ int s_run[kSpreadWarps][G];
@@ -720,19 +785,21 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) block_layout_kernel(
     int64_t lo, hi;
     seg_bounds(krow, kcol, u, j, nt, tv, &lo, &hi);
     if (hi == lo) return;
-    const uint32_t tb = (uint32_t)j * (uint32_t)tv;
     // the block (j, r) that holds the segment
     int ra = 0, rb = nr - 1;
     while (ra < rb) {
         const int mid = (ra + rb + 1) >> 1;
         if (range_start[mid] <= u) ra = mid; else rb = mid - 1;
     }
+    // ids are relative to tile j, or in window mode to range ra's window;
+    // the padding takes the far slot one past the tile or window
+    const uint32_t tb = wbase ? (uint32_t)wbase[2 * ra] : (uint32_t)j * (uint32_t)tv;
+    const uint16_t pad = wbase ? (uint16_t)wbase[2 * ra + 1] : (uint16_t)tv;
     const int64_t bsp = blk[2 * ((int64_t)j * nr + ra)];
     const int32_t L = (int32_t)blk[2 * ((int64_t)j * nr + ra) + 1];
     const int32_t m8 = lane_len(L);
     const int32_t S0 = (int32_t)toff[i], S1 = S0 + (int32_t)(hi - lo);
     const int32_t S8 = S0 + (int32_t)((hi - lo + kStep - 1) & ~int64_t(kStep - 1));  // padded end
-    const uint16_t pad = (uint16_t)tv;  // the relative id of the tile's far slot
     // the share holding entry p (t follows p, which only grows) and the slot
     int t = (int)((int64_t)S0 * kBThreads / L);
     int32_t sidx = 0;  // p's index in its share, set by place
@@ -834,54 +901,36 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) block_layout_kernel(
     if (S1 + lane < S8) tk[place(S1 + lane)] = pad;
 }
 
-template <class T, int MODEL, bool COMP, int G>
-cudaError_t launch_window_g(const WindowArgs& W, int grid, size_t smem, cudaStream_t st,
-                            int device)
+template <class T, int MODEL, bool COMP, bool WIN>
+cudaError_t launch_blocked_typed(gila_graph* g, const BlockedArgs& B, const CombineArgs& C,
+                                 int grid, size_t smem, cudaStream_t st, int device)
 {
     static std::atomic<uint64_t> configured{0};  // one bit per device; callers may race
     const uint64_t bit = 1ull << (device & 63);
     if (!(configured.load() & bit)) {
-        cudaError_t e = cudaFuncSetAttribute(window_kernel<T, MODEL, COMP, G>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kSmemCap - 4096);
-        if (e != cudaSuccess) return e;
-        configured.fetch_or(bit);
-    }
-    window_kernel<T, MODEL, COMP, G><<<grid, kBThreads, smem, st>>>(W);
-    count_launch();
-    return cudaGetLastError();
-}
-
-template <class T, int MODEL, bool COMP>
-cudaError_t launch_window(const WindowArgs& W, int grid, size_t smem, cudaStream_t st, int device,
-                          bool wide)
-{
-    return wide ? launch_window_g<T, MODEL, COMP, 32>(W, grid, smem, st, device)
-                : launch_window_g<T, MODEL, COMP, 8>(W, grid, smem, st, device);
-}
-
-template <class T, int MODEL, bool COMP>
-cudaError_t launch_pair(gila_graph* g, const BlockedArgs& B, const CombineArgs& C, int grid,
-                        size_t smem, cudaStream_t st, int device)
-{
-    static std::atomic<uint64_t> configured{0};  // one bit per device; callers may race
-    const uint64_t bit = 1ull << (device & 63);
-    if (!(configured.load() & bit)) {
-        cudaError_t e = cudaFuncSetAttribute(blocked_kernel<T, MODEL, COMP>,
+        cudaError_t e = cudaFuncSetAttribute(blocked_kernel<T, MODEL, COMP, WIN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kSmemCap - 4096);
         if (e != cudaSuccess) return e;
         configured.fetch_or(bit);
     }
     cudaEvent_t pa = prof_kernel_begin(g);
-    blocked_kernel<T, MODEL, COMP><<<grid, kBThreads, smem, st>>>(B);
+    blocked_kernel<T, MODEL, COMP, WIN><<<grid, kBThreads, smem, st>>>(B);
     count_launch();
     cudaError_t e = cudaGetLastError();
-    prof_kernel_end(g, pa, "blocked_kernel");
-    if (e != cudaSuccess) return e;
+    prof_kernel_end(g, pa, WIN ? "blocked_kernel (window)" : "blocked_kernel");
+    if (e != cudaSuccess || WIN) return e;
     combine_kernel<T, MODEL, COMP><<<(unsigned)(C.nreg + C.nhub), kCombineThreads, 0, st>>>(C);
     count_launch();
     return cudaGetLastError();
+}
+
+template <class T, int MODEL, bool COMP>
+cudaError_t launch_pair(gila_graph* g, const BlockedArgs& B, const CombineArgs& C, int grid,
+                        size_t smem, cudaStream_t st, int device, bool win)
+{
+    return win ? launch_blocked_typed<T, MODEL, COMP, true>(g, B, C, grid, smem, st, device)
+               : launch_blocked_typed<T, MODEL, COMP, false>(g, B, C, grid, smem, st, device);
 }
 
 }  // namespace
@@ -960,15 +1009,28 @@ std::vector<int32_t> partition_rows(const std::vector<int64_t>& cost, int64_t to
     return rs;
 }
 
+// CTAs per SM the blocked grid aims at by default. Tiles: one wave below
+// 10^8 k-hop entries, where loading a tile per CTA is a large part of an
+// iteration (BA n = 100,000, k = 2: 0.0493 ms per iteration at 1, 0.0514 at
+// 2, 0.0646 at 4); 4 up to 2e9 entries; 8 beyond, where a CTA streams tens
+// of MB and the end of the grid waits on the slowest (Chung-Lu 1.1e10 best
+// at 8). Windows: 2 (the mesh, k = 3: 0.0888, 0.0866, 0.108 and 0.150 ms at
+// 1, 2, 4 and 8).
+int64_t default_ctas_per_sm(int64_t nnz_khop, bool window)
+{
+    if (window) return 2;
+    return nnz_khop < 100000000LL ? 1 : nnz_khop < 2000000000LL ? 4 : 8;
+}
+
 // Number of row ranges per tile that gives the grid about ctas_per_sm CTAs
 // per SM: 4 by default, 8 for lists of 2e9 entries and more, where a CTA
 // streams tens of MB and the end of the grid waits on the slowest
 // (measured: Barabasi-Albert 2.4e8 entries best at 4, Chung-Lu 1.1e10 at 8).
-int64_t ranges_target(const gila_graph* g, int64_t nt)
+int64_t ranges_target(const gila_graph* g, int64_t nt, bool window)
 {
     const int64_t n = g->n;
     const int64_t per_sm = g->tune.ctas_per_sm > 0 ? g->tune.ctas_per_sm
-                                                   : (g->nnz_khop >= 2000000000LL ? 8 : 4);
+                                                   : default_ctas_per_sm(g->nnz_khop, window);
     const int sms = sm_count(g->device);
     const int64_t t = std::max<int64_t>((per_sm * (int64_t)sms + nt - 1) / nt,
                                         (n + kMaxRows - 1) / kMaxRows);
@@ -998,19 +1060,28 @@ gila_status plan_hubs(gila_graph* g, TilePlan& P)
     return GILA_OK;
 }
 
-// Window mode: when every row range's k-hop ids lie in a window of at most
-// tv_max consecutive ids (meshes, grids, locality-preserving vertex orders),
-// each range gets that window as its own tile and streams its rows from
-// kcol in place (no rearranged copy). *fits tells whether it applies.
-gila_status plan_window(gila_graph* g, size_t esz, int64_t tv_max, TilePlan& P, bool* fits)
+// Shared memory a window-mode CTA needs: the window with the far slot, the
+// row directory, and two position-type cells per row.
+size_t window_smem(int64_t wmax, int64_t rmax, size_t esz)
+{
+    return (((size_t)(wmax + 1) * esz + (size_t)(rmax + 1) * 4 + 15) & ~size_t(15)) +
+           (size_t)rmax * 2 * esz;
+}
+
+// Window mode: rows are cut into ranges, and each range's rows, whose k-hop
+// ids span a window [b, b + len) of consecutive ids narrow enough for
+// shared memory (meshes, grids, locality-preserving orders, and every graph
+// small enough to fit whole), read their positions from that window. Each
+// row then lies wholly in its range's block, so the CTA finishes its rows
+// itself (no partials, no second kernel). *fits tells whether every range's
+// window fits; `len` receives the row lengths, `rs` the ranges, `wb` the
+// windows (2 nr: first id, length).
+gila_status plan_window(gila_graph* g, size_t esz, TilePlan& P, bool* fits,
+                        std::vector<int64_t>& len, std::vector<int32_t>& rs,
+                        std::vector<int64_t>& wb, int64_t* wmax_out, int64_t* rmax_out)
 {
     *fits = false;
     const int64_t n = g->n;
-    // automatic mode does not choose windows: on the 1000 x 1000 mesh (k = 3,
-    // rows of 36 entries) the window kernel took 0.176 ms per iteration
-    // against 0.161 ms for the plain kernel, whose smaller blocks keep more
-    // rows in flight; forced tiling (tiled = 1) uses windows where they fit
-    if (g->tune.tiled < 0) return GILA_OK;
     std::vector<int64_t> krow((size_t)n + 1);
     GILA_CUDA(cudaMemcpyAsync(krow.data(), g->krow, sizeof(int64_t) * (n + 1),
                               cudaMemcpyDeviceToHost, g->stream));
@@ -1024,16 +1095,21 @@ gila_status plan_window(gila_graph* g, size_t esz, int64_t tv_max, TilePlan& P, 
     GILA_CUDA(cudaMemcpyAsync(span.data(), P.rowspan, sizeof(int32_t) * 2 * n,
                               cudaMemcpyDeviceToHost, g->stream));
     GILA_CUDA(cudaStreamSynchronize(g->stream));
+    len.assign((size_t)n, 0);
     std::vector<int64_t> cost((size_t)n);
     int64_t total = 0;
     for (int64_t u = 0; u < n; ++u) {
-        cost[(size_t)u] = 8 + krow[(size_t)u + 1] - krow[(size_t)u];
+        len[(size_t)u] = krow[(size_t)u + 1] - krow[(size_t)u];
+        cost[(size_t)u] = 8 + len[(size_t)u];
         total += cost[(size_t)u];
     }
-    const std::vector<int32_t> rs = partition_rows(cost, total, ranges_target(g, 1));
+    // enough ranges for several CTAs per SM, but at least about 16 entries
+    // per thread of a CTA (a small graph is one or a few ranges)
+    const int64_t by_work = std::max<int64_t>(1, total / ((int64_t)kBThreads * 16));
+    rs = partition_rows(cost, total, std::min<int64_t>(ranges_target(g, 1, true), by_work));
     const int64_t nr = (int64_t)rs.size() - 1;
-    std::vector<int64_t> wt(2 * (size_t)nr), blk(2 * (size_t)nr);
-    int64_t widest = 0;
+    wb.assign(2 * (size_t)nr, 0);
+    int64_t wmax = 0, rmax = 0;
     for (int64_t r = 0; r < nr; ++r) {
         int64_t lo = INT64_MAX, hi = -1;
         for (int64_t u = rs[(size_t)r]; u < rs[(size_t)r + 1]; ++u) {
@@ -1041,36 +1117,106 @@ gila_status plan_window(gila_graph* g, size_t esz, int64_t tv_max, TilePlan& P, 
             hi = std::max<int64_t>(hi, span[2 * (size_t)u + 1]);
         }
         if (hi < 0) lo = hi = rs[(size_t)r];  // no entries: a one-id window
-        const int64_t base = lo & ~int64_t(1);  // even first id: a 16-byte aligned float2 tile
-        wt[2 * (size_t)r] = base;
-        wt[2 * (size_t)r + 1] = hi - base + 1;
-        widest = std::max<int64_t>(widest, hi - base + 1);
-        const int64_t start = krow[(size_t)rs[(size_t)r]] & ~int64_t(3);  // 16-byte aligned ids
-        blk[2 * (size_t)r] = start;
-        blk[2 * (size_t)r + 1] = krow[(size_t)rs[(size_t)r + 1]] - start;
+        const int64_t base = lo & ~int64_t(1);  // even first id: a 16-byte aligned float2 window
+        wb[2 * (size_t)r] = base;
+        wb[2 * (size_t)r + 1] = hi - base + 1;
+        wmax = std::max<int64_t>(wmax, hi - base + 1);
+        rmax = std::max<int64_t>(rmax, (int64_t)(rs[(size_t)r + 1] - rs[(size_t)r]));
+        if (wmax > kMaxTile) return GILA_OK;  // 16-bit relative ids
     }
-    // the window shares the CTA's shared memory with the range's row offsets
-    const int64_t window_max =
-        std::min<int64_t>(tv_max, (kSmemCap - 4096 - 2 * (kMaxRows + 1) * 8) / (int64_t)esz);
-    if (widest + 1 > window_max) return GILA_OK;
-    if ((s = ensure((void**)&P.blk, &P.blk_cap, sizeof(int64_t) * blk.size())) != GILA_OK) return s;
-    if ((s = ensure((void**)&P.wtile, &P.wtile_cap, sizeof(int64_t) * wt.size())) != GILA_OK)
+    if (window_smem(wmax, rmax, esz) > (size_t)(kSmemCap - 4096)) return GILA_OK;
+    // windows pay where they are narrow: the positions all CTAs load stay
+    // below half the bytes of the 16-bit id stream (the mesh: 22 MB of
+    // windows for 75 MB of ids, 0.086 ms per iteration against 0.150 plain;
+    // a Barabasi-Albert graph of 10,000 vertices at k = 3, whose every range
+    // needs the whole graph, about as many window bytes as id bytes: 0.039
+    // against 0.030 plain)
+    int64_t wsum = 0;
+    for (int64_t r = 0; r < nr; ++r) wsum += wb[2 * (size_t)r + 1];
+    if (g->tune.tiled < 0 && wsum * (int64_t)esz > g->nnz_khop) return GILA_OK;
+    *wmax_out = wmax;
+    *rmax_out = rmax;
+    *fits = true;
+    return GILA_OK;
+}
+
+// The block layout shared by tiles and windows: (j, r) blocks in that
+// order, each in share storage (lane_len(L) slots per thread; block starts
+// are multiples of 8 slots, 16 bytes); segments padded to multiples of 8
+// entries; segment starts within their block; ids rearranged into 16-bit
+// relative ids. wb (window mode) gives each range's window; tiles are
+// [j tv, (j + 1) tv).
+gila_status build_layout(gila_graph* g, size_t esz, TilePlan& P, int64_t nt, int64_t tv,
+                         const std::vector<int64_t>& len, const std::vector<int32_t>& rs,
+                         const std::vector<int64_t>* wb)
+{
+    const int64_t n = g->n;
+    const int64_t cells = n * nt;
+    const int64_t nr = (int64_t)rs.size() - 1;
+    std::vector<int64_t> toff((size_t)cells), blk((size_t)(2 * nt * nr));
+    int64_t slots = 0;
+    for (int64_t j = 0; j < nt; ++j)
+        for (int64_t r = 0; r < nr; ++r) {
+            int64_t off = 0;
+            for (int64_t u = rs[(size_t)r]; u < rs[(size_t)r + 1]; ++u) {
+                toff[(size_t)(j * n + u)] = off;
+                off += (len[(size_t)(j * n + u)] + kStep - 1) & ~int64_t(kStep - 1);  // padded
+            }
+            blk[(size_t)(2 * (j * nr + r))] = slots;
+            blk[(size_t)(2 * (j * nr + r) + 1)] = off;
+            slots += (int64_t)kBThreads * lane_len((int32_t)off);
+        }
+    const int64_t tk_len = slots + kStep;
+    gila_status s;
+    if ((s = ensure((void**)&P.toff, &P.toff_cap, sizeof(int64_t) * (size_t)cells)) != GILA_OK)
         return s;
+    if ((s = ensure((void**)&P.blk, &P.blk_cap, sizeof(int64_t) * blk.size())) != GILA_OK) return s;
     if ((s = ensure((void**)&P.range_start, &P.range_cap, sizeof(int32_t) * rs.size())) != GILA_OK)
         return s;
+    if ((s = ensure((void**)&P.tk, &P.tk_cap, sizeof(uint16_t) * (size_t)tk_len)) != GILA_OK)
+        return s;
+    if (wb) {
+        if ((s = ensure((void**)&P.wtile, &P.wtile_cap, sizeof(int64_t) * wb->size())) != GILA_OK)
+            return s;
+        GILA_CUDA(cudaMemcpyAsync(P.wtile, wb->data(), sizeof(int64_t) * wb->size(),
+                                  cudaMemcpyHostToDevice, g->stream));
+    } else if ((s = ensure(&P.part, &P.part_cap, 2 * esz * (size_t)cells)) != GILA_OK) {
+        return s;
+    }
+    GILA_CUDA(cudaMemcpyAsync(P.toff, toff.data(), sizeof(int64_t) * cells, cudaMemcpyHostToDevice,
+                              g->stream));
     GILA_CUDA(cudaMemcpyAsync(P.blk, blk.data(), sizeof(int64_t) * blk.size(),
-                              cudaMemcpyHostToDevice, g->stream));
-    GILA_CUDA(cudaMemcpyAsync(P.wtile, wt.data(), sizeof(int64_t) * wt.size(),
                               cudaMemcpyHostToDevice, g->stream));
     GILA_CUDA(cudaMemcpyAsync(P.range_start, rs.data(), sizeof(int32_t) * rs.size(),
                               cudaMemcpyHostToDevice, g->stream));
-    GILA_CUDA(cudaStreamSynchronize(g->stream));  // the host vectors go out of scope
-    P.window = true;
-    P.nt = 1;
-    P.tv = (int32_t)((widest + 1) & ~int64_t(1));
+    // ids ordered for conflict-free gathers, or in ascending order; the
+    // slots past each share's end stay zero
+    GILA_CUDA(cudaMemsetAsync(P.tk, 0, sizeof(uint16_t) * (size_t)tk_len, g->stream));
+    const int64_t* wdev = wb ? P.wtile : nullptr;
+    const unsigned lay_blocks = (unsigned)((cells + kSpreadWarps - 1) / kSpreadWarps);
+    if (g->tune.bank_spread >= 0 && esz == 8)
+        block_layout_kernel<16, true><<<lay_blocks, kSpreadWarps * 32, 0, g->stream>>>(
+            n, g->krow, g->kcol, (int)nt, (int)tv, wdev, P.toff, P.blk, P.range_start, (int)nr,
+            P.tk);
+    else if (g->tune.bank_spread >= 0)
+        block_layout_kernel<8, true><<<lay_blocks, kSpreadWarps * 32, 0, g->stream>>>(
+            n, g->krow, g->kcol, (int)nt, (int)tv, wdev, P.toff, P.blk, P.range_start, (int)nr,
+            P.tk);
+    else
+        block_layout_kernel<16, false><<<lay_blocks, kSpreadWarps * 32, 0, g->stream>>>(
+            n, g->krow, g->kcol, (int)nt, (int)tv, wdev, P.toff, P.blk, P.range_start, (int)nr,
+            P.tk);
+    count_launch();
+    GILA_CUDA(cudaGetLastError());
+    if (!wb) {
+        // hubs of the adjacency for the combine kernel (synchronises)
+        if ((s = plan_hubs(g, P)) != GILA_OK) return s;
+    }
+    // the host vectors above go out of scope
+    GILA_CUDA(cudaStreamSynchronize(g->stream));
+    P.nt = (int32_t)nt;
     P.nr = (int32_t)nr;
     P.use = true;
-    *fits = true;
     return GILA_OK;
 }
 
@@ -1089,19 +1235,37 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
     tv_max = std::max<int64_t>(2, std::min<int64_t>(tv_max, kMaxTile) & ~int64_t(1));
     const int64_t nt = (n + tv_max - 1) / tv_max;
     const int64_t tv = std::min<int64_t>(tv_max, (((n + nt - 1) / nt) + 1) & ~int64_t(1));
-    const int min_seg = g->tune.min_segment > 0 ? g->tune.min_segment : 48;
+    const int min_seg = g->tune.min_segment;  // 0: no limit
     const double avg_seg = (double)g->nnz_khop / ((double)n * (double)nt);
-    // automatic mode: only where the lists are long enough to pay for a
-    // tile per CTA: below about 10^8 entries the plain kernel was faster on
-    // every Barabasi-Albert graph measured (n = 10^3 .. 3 10^4, k = 2, 3).
-    // FP64 follows the same rule (its tiles hold half as many positions):
-    // on BA k = 3 blocked 5.14 ms vs plain 6.03 ms per iteration
-    const bool tiles_pay = !(g->tune.tiled < 0 && avg_seg < min_seg);
-    if (esz == 8 || g->tune.tiled == 1) {
-        bool fits = false;
-        gila_status s = plan_window(g, esz, tv_max, P, &fits);
-        if (s != GILA_OK || fits) return s;
+    {
+        // window mode wherever every range's window fits shared memory (a
+        // tile size set by the tuning asks for tiles instead); automatic mode
+        // leaves lists below 4 10^6 entries to the plain kernel, which
+        // spreads small graphs over more SMs (32 x 32 grid, FP64: 0.017 ms
+        // plain, 0.105 ms in one window; triangulated 200 x 200 mesh, k = 3:
+        // 0.015 against 0.021)
+        if (g->tune.tile_vertices <= 0 && (g->tune.tiled > 0 || g->nnz_khop >= kBlockedMinNnz)) {
+            bool fits = false;
+            std::vector<int64_t> len, wb;
+            std::vector<int32_t> rs;
+            int64_t wmax = 0, rmax = 0;
+            gila_status s = plan_window(g, esz, P, &fits, len, rs, wb, &wmax, &rmax);
+            if (s != GILA_OK) return s;
+            if (fits) {
+                if ((s = build_layout(g, esz, P, 1, 0, len, rs, &wb)) != GILA_OK) return s;
+                P.window = true;
+                P.tv = (int32_t)wmax;
+                P.rmax = (int32_t)rmax;
+                return GILA_OK;
+            }
+        }
     }
+    // automatic mode: tiles from 4 10^6 k-hop entries on (BA n = 100,000,
+    // k = 2, 1.4e7 entries in segments of 36: 0.0493 ms per iteration
+    // against 0.0609 plain; BA n = 333,334, k = 2, segments of 12: 0.183
+    // against 0.209). FP64 follows the same rule (its tiles hold half as
+    // many positions): on BA k = 3 blocked 5.14 ms vs plain 6.03 ms
+    const bool tiles_pay = !(g->tune.tiled < 0 && avg_seg < min_seg);
     if (!tiles_pay || (g->tune.tiled < 0 && g->nnz_khop < kBlockedMinNnz)) return GILA_OK;
     const int64_t cells = n * nt;
     gila_status s = ensure((void**)&P.len, &P.len_cap, sizeof(int64_t) * (size_t)cells);
@@ -1124,62 +1288,10 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
         cost[(size_t)u] = c;
         total += c;
     }
-    const std::vector<int32_t> rs = partition_rows(cost, total, ranges_target(g, nt));
-    const int64_t nr = (int64_t)rs.size() - 1;
-    // block layout: (j, r) blocks in that order, each in share storage
-    // (lane_len(L) slots per thread; block starts are multiples of 8 slots,
-    // 16 bytes); segments padded to multiples of 8 entries; segment starts
-    // within their block
-    std::vector<int64_t> toff((size_t)cells), blk((size_t)(2 * nt * nr));
-    int64_t slots = 0;
-    for (int64_t j = 0; j < nt; ++j)
-        for (int64_t r = 0; r < nr; ++r) {
-            int64_t off = 0;
-            for (int64_t u = rs[(size_t)r]; u < rs[(size_t)r + 1]; ++u) {
-                toff[(size_t)(j * n + u)] = off;
-                off += (len[(size_t)(j * n + u)] + kStep - 1) & ~int64_t(kStep - 1);  // padded
-            }
-            blk[(size_t)(2 * (j * nr + r))] = slots;
-            blk[(size_t)(2 * (j * nr + r) + 1)] = off;
-            slots += (int64_t)kBThreads * lane_len((int32_t)off);
-        }
-    const int64_t tk_len = slots + kStep;
-    if ((s = ensure((void**)&P.toff, &P.toff_cap, sizeof(int64_t) * (size_t)cells)) != GILA_OK)
-        return s;
-    if ((s = ensure((void**)&P.blk, &P.blk_cap, sizeof(int64_t) * blk.size())) != GILA_OK) return s;
-    if ((s = ensure((void**)&P.range_start, &P.range_cap, sizeof(int32_t) * rs.size())) != GILA_OK)
-        return s;
-    if ((s = ensure((void**)&P.tk, &P.tk_cap, sizeof(uint16_t) * (size_t)tk_len)) != GILA_OK)
-        return s;
-    if ((s = ensure(&P.part, &P.part_cap, 2 * esz * (size_t)cells)) != GILA_OK) return s;
-    GILA_CUDA(cudaMemcpyAsync(P.toff, toff.data(), sizeof(int64_t) * cells, cudaMemcpyHostToDevice,
-                              g->stream));
-    GILA_CUDA(cudaMemcpyAsync(P.blk, blk.data(), sizeof(int64_t) * blk.size(),
-                              cudaMemcpyHostToDevice, g->stream));
-    GILA_CUDA(cudaMemcpyAsync(P.range_start, rs.data(), sizeof(int32_t) * rs.size(),
-                              cudaMemcpyHostToDevice, g->stream));
-    // ids ordered for conflict-free gathers, or in ascending order; the
-    // slots past each share's end stay zero
-    GILA_CUDA(cudaMemsetAsync(P.tk, 0, sizeof(uint16_t) * (size_t)tk_len, g->stream));
-    const unsigned lay_blocks = (unsigned)((cells + kSpreadWarps - 1) / kSpreadWarps);
-    if (g->tune.bank_spread >= 0 && esz == 8)
-        block_layout_kernel<16, true><<<lay_blocks, kSpreadWarps * 32, 0, g->stream>>>(
-            n, g->krow, g->kcol, (int)nt, (int)tv, P.toff, P.blk, P.range_start, (int)nr, P.tk);
-    else if (g->tune.bank_spread >= 0)
-        block_layout_kernel<8, true><<<lay_blocks, kSpreadWarps * 32, 0, g->stream>>>(
-            n, g->krow, g->kcol, (int)nt, (int)tv, P.toff, P.blk, P.range_start, (int)nr, P.tk);
-    else
-        block_layout_kernel<16, false><<<lay_blocks, kSpreadWarps * 32, 0, g->stream>>>(
-            n, g->krow, g->kcol, (int)nt, (int)tv, P.toff, P.blk, P.range_start, (int)nr, P.tk);
-    count_launch();
-    GILA_CUDA(cudaGetLastError());
-    // hubs of the adjacency for the combine kernel; synchronises, so the
-    // host vectors above stay valid until their copies are done
-    if ((s = plan_hubs(g, P)) != GILA_OK) return s;
-    P.nt = (int32_t)nt;
+    const std::vector<int32_t> rs = partition_rows(cost, total, ranges_target(g, nt, false));
+    if ((s = build_layout(g, esz, P, nt, tv, len, rs, nullptr)) != GILA_OK) return s;
     P.tv = (int32_t)tv;
-    P.nr = (int32_t)nr;
-    P.use = true;
+    P.rmax = kMaxRows;
     return GILA_OK;
 }
 
@@ -1191,8 +1303,8 @@ bool blocked_auto_applies(int64_t n, int64_t nnz_khop, size_t esz, const gila_tu
     if (tune.tile_vertices > 0) tv_max = std::min<int64_t>(tv_max, tune.tile_vertices);
     tv_max = std::max<int64_t>(2, std::min<int64_t>(tv_max, kMaxTile) & ~int64_t(1));
     const int64_t nt = (n + tv_max - 1) / tv_max;
-    const int min_seg = tune.min_segment > 0 ? tune.min_segment : 48;
-    return nnz_khop >= kBlockedMinNnz && (double)nnz_khop / ((double)n * (double)nt) >= min_seg;
+    return nnz_khop >= kBlockedMinNnz &&
+           (double)nnz_khop / ((double)n * (double)nt) >= (double)tune.min_segment;
 }
 
 gila_status prepare_iteration(gila_graph* g, const gila_params* prm)
@@ -1215,50 +1327,6 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
         if (s != GILA_OK) return s;
     }
     if (!P.use || ((uintptr_t)pos_in & 15) != 0) return GILA_OK;
-    if (P.window) {
-        WindowArgs W;
-        W.krow = g->krow;
-        W.kcol = g->kcol;
-        W.row = g->row;
-        W.col = g->col;
-        W.wtile = P.wtile;
-        W.range_start = P.range_start;
-        W.n = g->n;
-        W.d = prm->d;
-        W.t = t;
-        W.p = prm->p;
-        W.q = prm->q;
-        W.pos_in = pos_in;
-        W.pos_out = pos_out;
-        W.disp_out = disp_out;
-        W.wait_ns = g->wait_test ? kTestWaitNs : kWaitNs;
-        W.skip_copy = g->wait_test ? 1 : 0;
-        W.tv = P.tv;
-        const size_t wsmem = (size_t)P.tv * esz + 2 * (size_t)(kMaxRows + 1) * sizeof(int64_t);
-        // groups of 8 lanes for rows of up to 64 entries on average, else warps
-        const bool wide = g->nnz_khop > 64 * g->n;
-        const bool fr = (prm->p == 2 && prm->q == 1);
-        cudaError_t e;
-        cudaEvent_t pa = prof_kernel_begin(g);
-        switch (prm->precision) {
-        case GILA_FP64:
-            e = fr ? launch_window<double, kFR, false>(W, P.nr, wsmem, g->stream, g->device, wide)
-                   : launch_window<double, kGeneric, false>(W, P.nr, wsmem, g->stream, g->device, wide);
-            break;
-        case GILA_FP32_COMPENSATED:
-            e = fr ? launch_window<float, kFR, true>(W, P.nr, wsmem, g->stream, g->device, wide)
-                   : launch_window<float, kGeneric, true>(W, P.nr, wsmem, g->stream, g->device, wide);
-            break;
-        default:
-            e = fr ? launch_window<float, kFR, false>(W, P.nr, wsmem, g->stream, g->device, wide)
-                   : launch_window<float, kGeneric, false>(W, P.nr, wsmem, g->stream, g->device, wide);
-            break;
-        }
-        prof_kernel_end(g, pa, "window_kernel");
-        if (e != cudaSuccess) return cuda_fail(e, "window_kernel");
-        *handled = true;
-        return GILA_OK;
-    }
     BlockedArgs B;
     B.tk = P.tk;
     B.toff = P.toff;
@@ -1273,6 +1341,21 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
     B.part = P.part;
     B.wait_ns = g->wait_test ? kTestWaitNs : kWaitNs;
     B.skip_copy = g->wait_test ? 1 : 0;
+    B.wbase = P.window ? P.wtile : nullptr;
+    B.wmax = P.window ? P.tv : 0;
+    B.rmax = P.rmax;
+    B.row = g->row;
+    B.col = g->col;
+    B.d = prm->d;
+    B.t = t;
+    B.p = prm->p;
+    B.pos_out = pos_out;
+    B.disp_out = disp_out;
+    // FP32 steps: warp-uniform where rows change every few steps (measured:
+    // BA k = 3, segments of ~600 entries, 0.186 -> 0.172 ms; the mesh's
+    // windows 0.112 -> 0.105 ms), divergent where segments are long
+    // (Chung-Lu, ~4,500 entries: 4.97 ms divergent, 5.23 ms uniform)
+    B.converge = g->nnz_khop < (int64_t)kConvergeSeg * g->n * P.nt;
     CombineArgs C;
     C.row = g->row;
     C.col = g->col;
@@ -1289,21 +1372,23 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
     C.nhub = P.nhub;
     C.nreg = (int32_t)((g->n * kCombineLanes + kCombineThreads - 1) / kCombineThreads);
     const int grid = P.nt * P.nr;
-    const size_t smem = (size_t)(P.tv + 1) * esz + (size_t)(kMaxRows + 1) * 4;
+    const size_t smem = P.window ? window_smem(P.tv, P.rmax, esz)
+                                 : (size_t)(P.tv + 1) * esz + (size_t)(kMaxRows + 1) * 4;
     const bool fr = (prm->p == 2 && prm->q == 1);
+    const bool w = P.window;
     cudaError_t e;
     switch (prm->precision) {
     case GILA_FP64:
-        e = fr ? launch_pair<double, kFR, false>(g, B, C, grid, smem, g->stream, g->device)
-               : launch_pair<double, kGeneric, false>(g, B, C, grid, smem, g->stream, g->device);
+        e = fr ? launch_pair<double, kFR, false>(g, B, C, grid, smem, g->stream, g->device, w)
+               : launch_pair<double, kGeneric, false>(g, B, C, grid, smem, g->stream, g->device, w);
         break;
     case GILA_FP32_COMPENSATED:
-        e = fr ? launch_pair<float, kFR, true>(g, B, C, grid, smem, g->stream, g->device)
-               : launch_pair<float, kGeneric, true>(g, B, C, grid, smem, g->stream, g->device);
+        e = fr ? launch_pair<float, kFR, true>(g, B, C, grid, smem, g->stream, g->device, w)
+               : launch_pair<float, kGeneric, true>(g, B, C, grid, smem, g->stream, g->device, w);
         break;
     default:
-        e = fr ? launch_pair<float, kFR, false>(g, B, C, grid, smem, g->stream, g->device)
-               : launch_pair<float, kGeneric, false>(g, B, C, grid, smem, g->stream, g->device);
+        e = fr ? launch_pair<float, kFR, false>(g, B, C, grid, smem, g->stream, g->device, w)
+               : launch_pair<float, kGeneric, false>(g, B, C, grid, smem, g->stream, g->device, w);
         break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "blocked_kernel");

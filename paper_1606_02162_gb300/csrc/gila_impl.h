@@ -92,7 +92,8 @@ struct Bins {
 struct TilePlan {
     bool ready = false;  // decided for the current k-hop lists
     bool use = false;    // the blocked path serves this graph
-    int32_t nt = 0, tv = 0, nr = 0;
+    int32_t nt = 0, tv = 0, nr = 0;  // tiles, tile (or largest window) size, row ranges
+    int32_t rmax = 0;                // most rows of a range (window mode: cells per CTA)
     int32_t* range_start = nullptr;  // nr + 1 row bounds
     size_t range_cap = 0;
     int64_t* blk = nullptr;          // 2 nt nr: start and length of block (tile j, range r)
@@ -108,8 +109,8 @@ struct TilePlan {
     int32_t nhub = 0;
     int64_t* len = nullptr;          // nt n segment lengths (plan scratch)
     size_t len_cap = 0;
-    // window mode: one tile per row range, the window of ids its rows touch;
-    // the ids are read from kcol in place (offsets krow)
+    // window mode: one window of positions per row range, covering every id
+    // its rows touch; rows are finished by their range's CTA
     bool window = false;
     int64_t* wtile = nullptr;        // 2 nr: first id and length of range r's window
     size_t wtile_cap = 0;
@@ -190,6 +191,8 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
 // Whether automatic mode (or the tuning) puts a graph of these sizes on the
 // blocked path; and building its plan ahead of the first iteration.
 bool blocked_auto_applies(int64_t n, int64_t nnz_khop, size_t esz, const gila_tuning& tune);
+// CTAs per SM the blocked grid aims at unless the tuning sets it.
+int64_t default_ctas_per_sm(int64_t nnz_khop, bool window);
 gila_status prepare_iteration(gila_graph* g, const gila_params* prm);
 // GILA_ECUDA (and clears the flag) when a blocked-path CTA gave up waiting
 // for its tile copy since the last call; synchronises st.

@@ -354,7 +354,10 @@ gila_status gila_prune_degree_one(gila_graph* g, gila_pruned** out)
         if ((s = check_launch("prune_fill_kernel")) != GILA_OK) return bail(s);
     }
     if ((s = graph_create_from_device(kept, prow, pcol, pnnz, st, &p->g)) != GILA_OK) return bail(s);
-    if (kept > 0 && (s = set_repulsion_weights(p->g, wt, true)) != GILA_OK) return bail(s);
+    // with nothing removed every weight is 1, the unweighted force: the
+    // pruned graph then runs exactly the kernels of the plain graph
+    if (kept > 0 && kept < n && (s = set_repulsion_weights(p->g, wt, true)) != GILA_OK)
+        return bail(s);
     cleanup();
     *out = p;
     return GILA_OK;

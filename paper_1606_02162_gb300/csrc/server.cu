@@ -2,21 +2,26 @@
 // memory their k-hop lists need, run concurrently on the GPU.
 //
 // Two threads serve a queue of jobs:
-//   admission  takes jobs in arrival order; uploads the graph, counts its
-//              k-hop lists (exact size, before any list memory exists),
-//              waits until the job's device bytes fit the budget and a slot
-//              is free, then fills the lists, frees the build scratch and
-//              uploads the placement. A job that can never fit fails with
-//              GILA_EBUDGET.
+//   admission  takes the smallest waiting job (fewest adjacency entries,
+//              then the earliest); uploads the graph, counts its k-hop lists
+//              (exact size, before any list memory exists), waits until the
+//              job's device bytes fit the budget and a slot is free, then
+//              fills the lists, frees the build scratch, plans the blocked
+//              path and uploads the placement. A job that can never fit
+//              fails with GILA_EBUDGET.
 //   runner     keeps every admitted job's placement and temperature resident
-//              on the device and advances them oldest first: each round
-//              enqueues the next chunk of iterations of every running job on
-//              the job's own stream (at most two chunks in flight per job),
-//              so the kernels of different jobs overlap on the GPU; a job
-//              that has not started joins while the running jobs' work per
-//              iteration is below what fills the GPU (large jobs run nearly
-//              alone, small ones side by side); finished jobs are copied
-//              back, their memory is returned and waiters are woken.
+//              on the device and advances them by least remaining work
+//              (pairs per iteration times iterations left, shrunk by the
+//              time the job has waited so that none starves): each round it
+//              enqueues the next chunk of iterations of the jobs in that
+//              order on each job's own stream (at most two chunks in flight
+//              per job) while their work per iteration stays below what
+//              fills the GPU, so small jobs run side by side and overtake
+//              large ones, whose kernels alone fill the GPU; chunks are cut
+//              to a bounded amount of work so that a newly admitted job
+//              waits at most about a millisecond for the GPU; finished jobs
+//              are copied back, their memory is returned and waiters are
+//              woken.
 // Requests arriving while others run are admitted as soon as memory and a
 // slot free up (continuous batching). A job runs exactly the kernels it
 // would run alone, so its result does not depend on the mix.
@@ -63,6 +68,7 @@ struct Job {
     cudaEvent_t done_ev = nullptr;
     int chunks_issued = 0;
     int next_iter = 0;
+    int chunk_iters = 8;  // iterations per chunk (fewer for jobs with large iterations)
     bool download_issued = false;
     double t0 = 0.0;
     size_t bytes = 0;
@@ -113,6 +119,13 @@ size_t job_bytes(int64_t n, int64_t nnz_adj, int64_t nnz_khop, int precision,
     b += 4 * (size_t)nnz_khop;                          // k-hop ids
     b += 12 * (size_t)n;                                // row classes, spare
     b += 2 * esz * (size_t)n + 16 * (size_t)n;          // placement buffers, staging
+    {
+        // window-mode layout (graphs whose ranges fit shared-memory windows):
+        // 16-bit ids with each row padded by at most 7 entries, each range's
+        // block by at most 15 per thread of its CTA, and per row an offset
+        const int64_t nr = std::min<int64_t>(8 * 152, std::max<int64_t>(1, (nnz_khop + 8 * n) / 16384));
+        b += 2 * (size_t)(nnz_khop + 7 * n) + 8 * (size_t)n + 2 * 15 * 1024 * (size_t)nr;
+    }
     if (blocked_auto_applies(n, nnz_khop, esz, tune)) {
         // blocked-path plan: the ids once more in block order as 16-bit
         // tile-relative ids (each row's segment per tile padded by at most 7
@@ -132,6 +145,12 @@ size_t job_bytes(int64_t n, int64_t nnz_adj, int64_t nnz_khop, int precision,
 // the GPU busy on its own (measured: a Barabasi-Albert graph with 1.4e7
 // k-hop entries already runs at 70% of the largest graphs' pair rate).
 constexpr double kSaturationPairs = 2e7;
+// Pair interactions per chunk of a job's iterations: about a millisecond of
+// GPU time, the longest a newly admitted small job waits behind a chunk.
+constexpr double kChunkPairs = 5e8;
+// Waiting time (s) over which a job's remaining work counts for half in the
+// runner's order (aging, so that large jobs are not starved).
+constexpr double kAgeSeconds = 0.5;
 
 void finish_job(gila_server* s, const JobPtr& j, gila_status st, const std::string& err)
 {
@@ -232,6 +251,12 @@ gila_status admit_job(gila_server* s, const JobPtr& j, std::string* err)
         *err = gila_last_error();
         return st;
     }
+    // a chunk holds at most about kChunkPairs pair interactions (one
+    // iteration at least, eight at most)
+    {
+        const double per_iter = (double)(nnz + j->g->nnz_adj) + 1.0;
+        j->chunk_iters = (int)std::max(1.0, std::min(8.0, kChunkPairs / per_iter));
+    }
     const size_t n = (size_t)j->n;
     const size_t esz = pos_size(j->prm.precision);
     if (n > 0) {
@@ -281,8 +306,12 @@ void admission_loop(gila_server* s)
             std::unique_lock<std::mutex> lock(s->mu);
             s->cv_admit.wait(lock, [&] { return s->stop.load() || !s->pending.empty(); });
             if (s->stop.load()) return;
-            j = s->pending.front();
-            s->pending.pop_front();
+            // the smallest waiting job first (ties: the earliest)
+            auto best = s->pending.begin();
+            for (auto it = s->pending.begin(); it != s->pending.end(); ++it)
+                if ((*it)->col.size() < (*best)->col.size()) best = it;
+            j = *best;
+            s->pending.erase(best);
         }
         std::string err;
         const gila_status st = admit_job(s, j, &err);
@@ -313,7 +342,7 @@ bool advance(gila_server* s, Job& j, std::string* err, gila_status* st)
         if (j.chunks_issued >= 2 &&
             cudaEventQuery(j.chunk_ev[j.chunks_issued & 1]) == cudaErrorNotReady)
             return false;
-        const int end = std::min(iters, j.next_iter + s->chunk);
+        const int end = std::min(iters, j.next_iter + std::min(s->chunk, j.chunk_iters));
         for (int i = j.next_iter; i < end; ++i) {
             *st = launch_iteration(j.g, &j.prm, temperature_of(j, i), j.pos[i & 1],
                                    j.pos[(i + 1) & 1], nullptr);
@@ -365,8 +394,26 @@ void runner_loop(gila_server* s)
             }
         }
         bool progressed = false;
-        // oldest first: a job that has not started joins only while the
-        // running jobs leave the GPU short of work
+        // least remaining work first (aged by the time waited): jobs are
+        // advanced in that order while the work per iteration issued this
+        // round leaves the GPU short of work; the first job always runs
+        {
+            const Clock::time_point now = Clock::now();
+            auto key = [&](const JobPtr& j) {
+                const double per_iter = (double)(j->nnz_khop + j->g->nnz_adj) + 1.0;
+                const double left = per_iter * (double)(j->prm.iters - j->next_iter + 1);
+                const double age = std::chrono::duration<double>(now - j->t_submit).count();
+                return left / (1.0 + age / kAgeSeconds);
+            };
+            std::vector<std::pair<double, size_t>> order;
+            for (size_t i = 0; i < active.size(); ++i) order.emplace_back(key(active[i]), i);
+            std::stable_sort(order.begin(), order.end(),
+                             [](const std::pair<double, size_t>& a,
+                                const std::pair<double, size_t>& b) { return a.first < b.first; });
+            std::vector<JobPtr> sorted;
+            for (auto& o : order) sorted.push_back(active[o.second]);
+            active.swap(sorted);
+        }
         double running_work = 0.0;
         for (size_t i = 0; i < active.size();) {
             JobPtr j = active[i];
@@ -378,8 +425,7 @@ void runner_loop(gila_server* s)
                 active.erase(active.begin() + i);
                 continue;
             }
-            const bool started = j->chunks_issued > 0;
-            if (!started && running_work >= kSaturationPairs) {
+            if (!j->download_issued && running_work >= kSaturationPairs) {
                 ++i;
                 continue;
             }

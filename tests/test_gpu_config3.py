@@ -217,7 +217,7 @@ def test_chunglu_capped_moves_sample(chunglu, chunglu_sample, prec, tol):
     G.gila_profile_enable(h.handle, 2)
     G.gila_layout_step(h.handle, G.params(k=3, precision=prec), t, x, y, disp)
     G.gila_profile_read(h.handle)
-    assert G.gila_profile_read_kernel(h.handle)["name"] == "blocked_kernel"
+    assert G.gila_profile_read_kernel(h.handle)["name"].startswith("blocked_kernel")
     G.gila_profile_enable(h.handle, 0)
     got = disp.double().cpu().numpy()[sel]
     base = x.double().cpu().numpy()
@@ -256,4 +256,4 @@ def test_chunglu_shape_fp64_first_ten_iterations():
             assert np.abs(got - odisp).max() <= 1e-12 * np.abs(odisp).max(), i
             x = xnext
         G.gila_profile_read(h.handle)
-        assert G.gila_profile_read_kernel(h.handle)["name"] == "blocked_kernel"
+        assert G.gila_profile_read_kernel(h.handle)["name"].startswith("blocked_kernel")

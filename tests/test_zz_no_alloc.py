@@ -51,10 +51,17 @@ def test_noalloc_counts_match_allocating_path(name, maker, k):
     want, want_total = _allocating_counts(g, k)
     row = torch.tensor(g.row_ptr, dtype=torch.int64, device="cuda")
     col = torch.tensor(g.col_idx, dtype=torch.int32, device="cuda")
-    for _ in range(2):  # the second call must not see the first call's scratch
+    for i in range(2):  # the second call must not see the first call's scratch
         counts = torch.full((g.n,), -7, dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+        before = (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
         total = G.gila_khop_count_noalloc(g.n, row, col, k, counts)
         torch.cuda.synchronize()
+        after = (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
+        if i == 1:
+            # the defining property: the call takes no device memory (the
+            # first call may still load the library's module on the device)
+            assert after == before, (before, after)
         assert total == want_total
         assert np.array_equal(counts.cpu().numpy(), want)
 
