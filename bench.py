@@ -73,20 +73,15 @@ WORKLOADS = {
 }
 PREC = {"fp32": 0, "fp64": 1, "fp32c": 2}
 
-# DRAM traffic of one iteration (ncu dram__bytes_read.sum + dram__bytes_write.sum
-# of its blocked_kernel and combine_kernel launches) on a workload, with the
-# SHA-256 of the kernel sources it was measured on: reported only while those
-# sources are unchanged, else null.
+# DRAM traffic of one iteration (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of its blocked_kernel launch and, in tile mode, its
+# combine_kernel launch) on a workload, with the SHA-256 of the kernel
+# sources it was measured on: reported only while those sources are
+# unchanged, else null.
 KERNEL_SOURCES = ("paper_1606_02162_gb300/csrc/blocked.cu",
                   "paper_1606_02162_gb300/csrc/force.cuh",
                   "paper_1606_02162_gb300/csrc/device_util.cuh")
-NCU_TRAFFIC = {
-    "ba100k_k3": {"bytes": 978219264 + 7552000 + 10422272,
-                  "kernels": "blocked_kernel + combine_kernel (one iteration)",
-                  "profile": "profiles/blocked_kernel_ba100k_k3.md, "
-                             "profiles/combine_kernel_ba100k_k3.md",
-                  "sources_sha256": "e81b21c6068c2752cf450f67a196abcc01fe412af0bd11c57fd931560bca3109"},
-}
+NCU_TRAFFIC = {}
 
 
 def kernel_sources_sha256() -> str:
