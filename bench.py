@@ -58,6 +58,11 @@ WORKLOADS = {
                            oracle_sample=2048,
                            desc="Chung-Lu gamma=2.3, n=250000, E=1000000, k=3, 300 iterations, "
                                 "FP32 compensated"),
+    "chunglu40k_k3": dict(graph="chunglu40k", k=3, iters=300, precision="fp32c",
+                          oracle_sample=2048,
+                          desc="Chung-Lu gamma=2.3, n=40000, E=160000, k=3, 300 iterations, "
+                               "FP32 compensated (the default workload's shape at a size a full "
+                               "profiler capture handles)"),
     "ba1m_k2": dict(graph="ba1m", k=2, iters=500, precision="fp32", oracle_sample=4096,
                     desc="Barabasi-Albert n=333,334 m=3 (999,996 edges), k=2, 500 iterations, "
                          "linear cooling from 0.1*sqrt(n), d=1, FP32"),

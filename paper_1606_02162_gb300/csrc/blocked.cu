@@ -94,12 +94,15 @@ struct Slot {
     T v[4];
 };
 
-// Cell (tile j, row u) of the partials, as two position-type pairs.
-template <class T>
+// Cell (tile j, row u) of the partials: the sum as one position-type pair,
+// followed by its compensation pair in the compensated mode (8 bytes a cell
+// for plain FP32, so that the partials of short-row graphs with many tiles
+// do not outweigh their id stream).
+template <class T, bool COMP>
 __device__ __forceinline__ typename V2<T>::type* cell_ptr(void* part, int64_t n, int j, int64_t u)
 {
     using P2 = typename V2<T>::type;
-    return reinterpret_cast<P2*>(part) + ((int64_t)j * n + u) * 2;
+    return reinterpret_cast<P2*>(part) + ((int64_t)j * n + u) * (COMP ? 2 : 1);
 }
 
 template <class T, bool COMP>
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
     // the cell of row i of the range: in shared memory (window mode) or the
     // global partial of (tile j, row u0 + i)
     auto cellp = [&](int64_t i) -> P2* {
-        return WIN ? cells + 2 * i : cell_ptr<T>(A.part, A.n, j, u0 + i);
+        return WIN ? cells + 2 * i : cell_ptr<T, COMP>(A.part, A.n, j, u0 + i);
     };
     if (threadIdx.x == 0) {
         // tile j by the bulk-copy engine (tv is even and the placement is
@@ -621,7 +624,7 @@ __device__ __forceinline__ void add_cell(const void* part, int64_t n, int j, int
                                          Acc<T, COMP>& s)
 {
     using P2 = typename V2<T>::type;
-    const P2* c = cell_ptr<T>(const_cast<void*>(part), n, j, u);
+    const P2* c = cell_ptr<T, COMP>(const_cast<void*>(part), n, j, u);
     const P2 v = c[0];
     if (COMP) {
         const P2 k = c[1];

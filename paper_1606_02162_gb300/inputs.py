@@ -392,6 +392,7 @@ def workload(name: str) -> tuple[Graph, np.ndarray]:
     grid32      : 32x32 grid, positions U[0, 32]^2, seed 1
     ba100k      : Barabasi-Albert n=100,000, m=3, seed 2, U[0, sqrt n]^2
     chunglu250k : Chung-Lu gamma=2.3, n=250,000, E=1,000,000, seed 3
+    chunglu40k  : Chung-Lu gamma=2.3, n=40,000, E=160,000, seed 3 (profiling size)
     mesh1000    : 1000x1000 triangulated mesh, seed 3
     ba1m        : Barabasi-Albert n=333,334, m=3 (999,996 edges), seed 12, U[0, sqrt n]^2
     """
@@ -403,6 +404,9 @@ def workload(name: str) -> tuple[Graph, np.ndarray]:
         return g, uniform_positions(g.n, 2)
     if name == "chunglu250k":
         g = chung_lu(250_000, 2.3, 8.0, 1_000_000, 3)
+        return g, uniform_positions(g.n, 3)
+    if name == "chunglu40k":
+        g = chung_lu(40_000, 2.3, 8.0, 160_000, 3)
         return g, uniform_positions(g.n, 3)
     if name == "mesh1000":
         g = tri_mesh(1000, 1000)
