@@ -86,7 +86,12 @@ PREC = {"fp32": 0, "fp64": 1, "fp32c": 2}
 KERNEL_SOURCES = ("paper_1606_02162_gb300/csrc/blocked.cu",
                   "paper_1606_02162_gb300/csrc/force.cuh",
                   "paper_1606_02162_gb300/csrc/device_util.cuh")
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "chunglu250k_k3": {"bytes": 22750000000 + 93430000 + 52050000 + 768,
+                       "kernels": "blocked_kernel + combine_kernel (one iteration)",
+                       "profile": "profiles/launches_chunglu250k_k3.md",
+                       "sources_sha256": "eaf03f1c9b530487a985cf2d93824ed268a2d6d59506e1257f964f9a87b34689"},
+}
 
 
 def kernel_sources_sha256() -> str:
