@@ -277,6 +277,7 @@ t2_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __restrict_
 // over the marks gives every edge its slot.
 constexpr int64_t kT2SmemWords = (160 * 1024) / 4;
 constexpr size_t kStoreCap = (size_t)16 << 30;  // device bytes for the stored tier-2 balls
+constexpr size_t kB2Cap = (size_t)16 << 30;     // device bytes for the radius-2 balls (k = 3)
 
 template <bool FILL>
 __global__ void __launch_bounds__(kT2Threads)
@@ -382,6 +383,107 @@ t2s_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __restrict
         }
         __syncthreads();
         for (int i = tid; i < cnt; i += kT2Threads) B[V[i] >> 5] = 0u;
+        __syncthreads();
+    }
+}
+
+// Radius-3 balls as unions of radius-2 balls (the count pass of k = 3 when
+// most balls are large, as on power-law graphs): a vertex w is within 3 hops
+// of s exactly when it is within 2 hops of s or of a neighbour of s, so
+//   B3(s) = B2(s) | OR over v in N(s) of B2(v).
+// ball2_kernel writes B2(v) of every vertex as a bitmap of n bits (one block
+// per vertex: its own bit, its neighbours', their neighbours', by
+// shared-memory atomics); ball3_or_kernel then forms B3 of each tier-2
+// source by OR-ing the (deg + 1) bitmaps, kept in registers, the block's
+// threads each owning a fixed slice of the words; the popcount gives the
+// count, and the ball is stored for the fill (t2_fill_stored_kernel). The
+// work is (2E + n) bitmaps read, n / 8 bytes each, instead of a
+// breadth-first search per source whose cost grows with the edges of every
+// ball of radius 2.
+__global__ void __launch_bounds__(kT2Threads)
+ball2_kernel(int64_t n, const int64_t* __restrict__ row, const int32_t* __restrict__ col,
+             int64_t nwords, uint32_t* __restrict__ b2)
+{
+    extern __shared__ uint32_t B[];
+    const int tid = threadIdx.x;
+    for (int64_t i = tid; i < nwords; i += kT2Threads) B[i] = 0u;
+    __syncthreads();
+    for (int64_t v = blockIdx.x; v < n; v += gridDim.x) {
+        if (tid == 0) atomicOr(&B[v >> 5], 1u << (v & 31));
+        const int64_t vb = row[v], ve = row[v + 1];
+        for (int64_t e = vb + tid; e < ve; e += kT2Threads) {
+            const int32_t u = col[e];
+            atomicOr(&B[u >> 5], 1u << (u & 31));
+        }
+        for (int64_t e = vb; e < ve; ++e) {
+            const int32_t u = col[e];
+            const int64_t ub = row[u], ue = row[u + 1];
+            for (int64_t f = ub + tid; f < ue; f += kT2Threads) {
+                const int32_t x = col[f];
+                atomicOr(&B[x >> 5], 1u << (x & 31));
+            }
+        }
+        __syncthreads();
+        uint4* dst = reinterpret_cast<uint4*>(b2 + v * nwords);
+        uint4* b4 = reinterpret_cast<uint4*>(B);
+        for (int64_t i = tid; i < nwords / 4; i += kT2Threads) {
+            dst[i] = b4[i];
+            b4[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncthreads();
+    }
+}
+
+constexpr int kOrRegs = 8;  // uint4 words of the ball each thread keeps per pass
+
+__global__ void __launch_bounds__(kT2Threads)
+ball3_or_kernel(const int32_t* __restrict__ queue, int nq, const int64_t* __restrict__ row,
+                const int32_t* __restrict__ col, int64_t nwords, const uint32_t* __restrict__ b2,
+                int64_t* __restrict__ counts, uint32_t* __restrict__ store)
+{
+    __shared__ int64_t s_wt[kT2Threads / 32 + 1];
+    const int tid = threadIdx.x;
+    const int64_t n4 = nwords / 4;  // nwords is a multiple of 4
+    for (int qi = blockIdx.x; qi < nq; qi += gridDim.x) {
+        const int32_t src = queue[qi];
+        const int64_t sb = row[src], se = row[src + 1];
+        int64_t cnt = 0;
+        uint4* dst = reinterpret_cast<uint4*>(store + (int64_t)qi * nwords);
+        for (int64_t c0 = 0; c0 < n4; c0 += (int64_t)kT2Threads * kOrRegs) {
+            uint4 acc[kOrRegs];
+            const uint4* own = reinterpret_cast<const uint4*>(b2 + (int64_t)src * nwords);
+#pragma unroll
+            for (int r = 0; r < kOrRegs; ++r) {
+                const int64_t i = c0 + (int64_t)r * kT2Threads + tid;
+                acc[r] = i < n4 ? own[i] : make_uint4(0u, 0u, 0u, 0u);
+            }
+            for (int64_t e = sb; e < se; ++e) {
+                const uint4* nb = reinterpret_cast<const uint4*>(b2 + (int64_t)col[e] * nwords);
+#pragma unroll
+                for (int r = 0; r < kOrRegs; ++r) {
+                    const int64_t i = c0 + (int64_t)r * kT2Threads + tid;
+                    if (i < n4) {
+                        const uint4 w = __ldg(nb + i);
+                        acc[r].x |= w.x;
+                        acc[r].y |= w.y;
+                        acc[r].z |= w.z;
+                        acc[r].w |= w.w;
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kOrRegs; ++r) {
+                const int64_t i = c0 + (int64_t)r * kT2Threads + tid;
+                if (i < n4) {
+                    dst[i] = acc[r];
+                    cnt += __popc(acc[r].x) + __popc(acc[r].y) + __popc(acc[r].z) +
+                           __popc(acc[r].w);
+                }
+            }
+        }
+        int64_t total;
+        block_inclusive_scan<int64_t, kT2Threads>(cnt, s_wt, &total);
+        if (tid == 0) counts[src] = total - 1;  // the source itself is not in its list
         __syncthreads();
     }
 }
@@ -757,6 +859,34 @@ gila_status build_khop_count(gila_graph* g, int k, int64_t* nnz_out)
     return s;
 }
 
+// Whether radius-3 balls are expected to cover a tenth of the graph or
+// more, from the degree moments: a ball of radius 3 holds about
+// mean(deg) kappa^2 vertices, kappa = E[deg^2] / E[deg] the mean excess
+// degree (the 1M-edge Chung-Lu graph: 0.67 by this estimate, 0.18 measured;
+// Barabasi-Albert n = 100,000: 0.034 and 0.024). Above that, unions of
+// radius-2 bitmaps build the balls faster than a breadth-first search per
+// source (Chung-Lu: 137 ms less per build); below it they do not (BA
+// n = 100,000: 1.4 ms more).
+bool dense_balls(const int64_t* row_dev, int64_t n, cudaStream_t st)
+{
+    std::vector<int64_t> row((size_t)n + 1);
+    if (cudaMemcpyAsync(row.data(), row_dev, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t u = 0; u < n; ++u) {
+        const double d = (double)(row[(size_t)u + 1] - row[(size_t)u]);
+        s1 += d;
+        s2 += d * d;
+    }
+    if (s1 <= 0.0) return false;
+    const double kappa = s2 / s1;
+    return (s1 / (double)n) * kappa * kappa >= 0.1 * (double)n;
+}
+
 gila_status build_khop_count_impl(gila_graph* g, int k)
 {
     const int64_t n = g->n;
@@ -821,12 +951,40 @@ gila_status build_khop_count_impl(gila_graph* g, int k)
                 if (cudaMalloc(&p, store_bytes) == cudaSuccess) S.store = (uint32_t*)p;
                 else cudaGetLastError();
             }
-            GILA_CUDA(cudaFuncSetAttribute(t2s_kernel<false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            t2s_kernel<false><<<t2_blocks, kT2Threads, smem, st>>>(
-                n, g->row, g->col, k, S.queue, nq, S.lists, nwords, S.counts, nullptr, nullptr,
-                S.store);
-            count_launch();
+            // k = 3 with the balls stored and most sources in tier 2: the
+            // balls as unions of the radius-2 balls (one n-bit bitmap per
+            // vertex, at most kB2Cap bytes, freed right after)
+            uint32_t* b2 = nullptr;
+            const size_t b2_bytes = (size_t)n * (size_t)nwords * 4;
+            if (k == 3 && S.store && nq >= n / 4 && b2_bytes <= kB2Cap &&
+                dense_balls(g->row, n, st)) {
+                void* p = nullptr;
+                if (cudaMalloc(&p, b2_bytes) == cudaSuccess) b2 = (uint32_t*)p;
+                else cudaGetLastError();
+            }
+            if (b2) {
+                GILA_CUDA(cudaFuncSetAttribute(ball2_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+                ball2_kernel<<<(unsigned)std::min<int64_t>(n, (int64_t)sms * 8), kT2Threads, smem,
+                               st>>>(n, g->row, g->col, nwords, b2);
+                count_launch();
+                ball3_or_kernel<<<(unsigned)std::min<int64_t>(nq, (int64_t)sms * 8), kT2Threads, 0,
+                                  st>>>(S.queue, nq, g->row, g->col, nwords, b2, S.counts,
+                                        S.store);
+                count_launch();
+                cudaError_t e = cudaStreamSynchronize(st);
+                cudaFree(b2);
+                if (e != cudaSuccess) return cuda_fail(e, "radius-3 balls");
+            } else {
+                GILA_CUDA(cudaFuncSetAttribute(t2s_kernel<false>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+                t2s_kernel<false><<<t2_blocks, kT2Threads, smem, st>>>(
+                    n, g->row, g->col, k, S.queue, nq, S.lists, nwords, S.counts, nullptr,
+                    nullptr, S.store);
+                count_launch();
+            }
         } else if (S.t2_blocks < t2_blocks || S.bitmap_words != nwords || !S.bitmaps) {
             cudaFree(S.bitmaps);
             cudaFree(S.lists);
