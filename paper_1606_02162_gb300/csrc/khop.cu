@@ -489,13 +489,18 @@ ball3_or_kernel(const int32_t* __restrict__ queue, int nq, const int64_t* __rest
 }
 
 // Fill from the balls the count pass stored: each block writes the sorted
-// rows of its sources straight from their bitmaps (no second search).
+// rows of its sources straight from their bitmaps (no second search). A
+// chunk of 256 words is expanded into shared memory at the offsets a block
+// scan of their popcounts gives, then copied out with coalesced stores.
+constexpr int kFillStage = kT2Threads * 32;  // ids a chunk of 256 words can hold
+
 __global__ void __launch_bounds__(kT2Threads)
 t2_fill_stored_kernel(const int32_t* __restrict__ queue, int nq, int64_t nwords,
                       const uint32_t* __restrict__ store, const int64_t* __restrict__ krow,
                       uint32_t* __restrict__ kcol)
 {
     __shared__ int64_t s_wt[kT2Threads / 32 + 1];
+    __shared__ uint32_t s_ids[kFillStage];
     const int tid = threadIdx.x;
     for (int qi = blockIdx.x; qi < nq; qi += gridDim.x) {
         const int32_t src = queue[qi];
@@ -509,12 +514,15 @@ t2_fill_stored_kernel(const int32_t* __restrict__ queue, int nq, int64_t nwords,
             int64_t total;
             const int64_t incl =
                 block_inclusive_scan<int64_t, kT2Threads>((int64_t)__popc(w), s_wt, &total);
-            int64_t o = base + incl - __popc(w);
+            int o = (int)(incl - __popc(w));
             while (w) {
                 const int b = __ffs(w) - 1;
-                out[o++] = (uint32_t)(wi * 32 + b);
+                s_ids[o++] = (uint32_t)(wi * 32 + b);
                 w &= w - 1;
             }
+            __syncthreads();
+            for (int i = tid; i < (int)total; i += kT2Threads) out[base + i] = s_ids[i];
+            __syncthreads();
             base += total;
         }
     }
