@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "device_util.cuh"
+#include "ff.cuh"
 #include "force.cuh"
 #include "gila_impl.h"
 
@@ -936,6 +937,128 @@ cudaError_t launch_pair(gila_graph* g, const BlockedArgs& B, const CombineArgs& 
                : launch_blocked_typed<T, MODEL, COMP, false>(g, B, C, grid, smem, st, device);
 }
 
+// The k-hop term of the quality reductions, sum over unordered k-hop pairs
+// {u, v} of d^2 / delta^q, for FP32 placements that have a blocked plan:
+// one CTA per (tile or window, row range), positions from the shared-memory
+// tile, each pair counted once from its smaller end. Every row of the range
+// is sorted, so the entries of row u that lie in the tile and above u are
+// one contiguous run, found by two binary searches; a warp walks it with
+// each term in double-float arithmetic (ff.cuh), sixteen terms per lane
+// summed as a double-float, then added in FP64; the CTA's FP64 partial goes
+// to its own slot, and the partials are added in CTA order.
+constexpr int kMetThreads = 1024;
+constexpr int kMetWarps = kMetThreads / 32;
+
+struct MetricArgs {
+    const int64_t* krow;
+    const uint32_t* kcol;
+    const int32_t* range_start;
+    const int64_t* wbase;  // window mode: 2 nr (first id, length), else null
+    int64_t n;
+    int32_t nt, tv, nr, tcap;
+    double d;
+    int q;
+    const float2* pos;
+    double* partial;       // one per CTA
+    uint64_t wait_ns;
+};
+
+__global__ void __launch_bounds__(kMetThreads, 1) khop_metric_kernel(const MetricArgs A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2* tile = reinterpret_cast<float2*>(smem_raw);
+    __shared__ __align__(8) uint64_t tile_bar;
+    __shared__ int tile_ok;
+    __shared__ double s_part[kMetWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = (int)(blockIdx.x / A.nr), r = (int)(blockIdx.x % A.nr);
+    const int64_t u0 = A.range_start[r], u1 = A.range_start[r + 1];
+    const int64_t tb = A.wbase ? A.wbase[2 * r] : (int64_t)j * A.tv;
+    const int64_t tn = A.wbase ? A.wbase[2 * r + 1]
+                               : ((A.n - tb < A.tv) ? A.n - tb : (int64_t)A.tv);
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)(((size_t)tn * sizeof(float2)) & ~size_t(15));
+        mbar_init(&tile_bar, 1);
+        mbar_arrive_expect_tx(&tile_bar, bytes);
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(A.pos + tb);
+        for (uint32_t o = 0; o < bytes; o += kBulkChunk)
+            bulk_g2s(smem_raw + o, src + o, (bytes - o < kBulkChunk) ? bytes - o : kBulkChunk,
+                     &tile_bar);
+        if ((size_t)tn * sizeof(float2) != bytes) tile[tn - 1] = A.pos[tb + tn - 1];
+        bool ok = mbar_wait(&tile_bar, 0, A.wait_ns);
+        if (!ok) {
+            atomicExch(&g_tile_wait_failed, 1);
+            mbar_wait(&tile_bar, 0, A.wait_ns);
+        }
+        tile_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    double part = 0.0;
+    if (tile_ok) {
+        mbar_wait(&tile_bar, 0, A.wait_ns);
+        const Ff d2f = ff_from_double(A.d * A.d);
+        for (int64_t u = u0 + warp; u < u1; u += kMetWarps) {
+            const int64_t kb = A.krow[u], ke = A.krow[u + 1];
+            const uint32_t key_lo = (uint32_t)(tb > u + 1 ? tb : u + 1);
+            const uint32_t key_hi = (uint32_t)(tb + tn);
+            if (key_lo >= key_hi || kb == ke) continue;
+            auto lower = [&](uint32_t key) {
+                int64_t x = kb, y = ke;
+                while (x < y) {
+                    const int64_t mid = (x + y) >> 1;
+                    if (A.kcol[mid] < key) x = mid + 1; else y = mid;
+                }
+                return x;
+            };
+            const int64_t lo = lower(key_lo), hi = lower(key_hi);
+            if (lo >= hi) continue;
+            const float2 qu = A.pos[u];
+            Ff s = {0.f, 0.f};
+            int cnt = 0;
+            for (int64_t e = lo + lane; e < hi; e += 32) {
+                const float2 pv = tile[A.kcol[e] - tb];
+                const Ff r2 = ff_dist2(qu.x, qu.y, pv.x, pv.y);
+                if (r2.hi >= 1e-30f && r2.hi <= 1e30f) {
+                    s = ff_add(s, ff_mul(d2f, ff_rsqrt_pow(r2, A.q)));
+                } else {
+                    const double dx = (double)qu.x - (double)pv.x;
+                    const double dy = (double)qu.y - (double)pv.y;
+                    const double dl = sqrt(dx * dx + dy * dy);
+                    if (dl > 0.0) {
+                        double w = 1.0;
+                        for (int i = 0; i < A.q; ++i) w *= dl;
+                        part += A.d * A.d / w;
+                    }
+                }
+                if (++cnt == 16) {
+                    part += (double)s.hi + (double)s.lo;
+                    s = {0.f, 0.f};
+                    cnt = 0;
+                }
+            }
+            part += (double)s.hi + (double)s.lo;
+        }
+    }
+    // fixed-order block sum: lanes, then warps in order
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+    if (lane == 0) s_part[warp] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kMetWarps; ++w) t += s_part[w];
+        A.partial[blockIdx.x] = t;
+    }
+}
+
+__global__ void sum_in_order_kernel(const double* __restrict__ v, int count, double* out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < count; ++i) t += v[i];
+        *out = t;
+    }
+}
+
 }  // namespace
 
 void invalidate_tile_plans(gila_graph* g)
@@ -1396,6 +1519,54 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
     }
     if (e != cudaSuccess) return cuda_fail(e, "blocked_kernel");
     *handled = true;
+    return GILA_OK;
+}
+
+gila_status blocked_khop_metric(gila_graph* g, const gila_params* prm, const void* pos,
+                                bool* done, double* rep_total)
+{
+    *done = false;
+    const TilePlan& P = g->tplan[0];
+    if (is_f64(prm->precision) || !P.ready || !P.use || g->n == 0 || g->wt64) return GILA_OK;
+    if (((uintptr_t)pos & 15) != 0) return GILA_OK;
+    const int grid = P.nt * P.nr;
+    gila_status s = ensure((void**)&g->red, &g->red_cap, sizeof(double) * ((size_t)grid + 8));
+    if (s != GILA_OK) return s;
+    MetricArgs M;
+    M.krow = g->krow;
+    M.kcol = g->kcol;
+    M.range_start = P.range_start;
+    M.wbase = P.window ? P.wtile : nullptr;
+    M.n = g->n;
+    M.nt = P.nt;
+    M.tv = P.tv;
+    M.nr = P.nr;
+    M.tcap = P.tv;
+    M.d = prm->d;
+    M.q = prm->q;
+    M.pos = reinterpret_cast<const float2*>(pos);
+    M.partial = g->red;
+    M.wait_ns = kWaitNs;
+    const size_t smem = ((size_t)P.tv + 1) * sizeof(float2);
+    static std::atomic<uint64_t> configured{0};
+    const uint64_t bit = 1ull << (g->device & 63);
+    if (!(configured.load() & bit)) {
+        GILA_CUDA(cudaFuncSetAttribute(khop_metric_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kSmemCap - 4096));
+        configured.fetch_or(bit);
+    }
+    khop_metric_kernel<<<grid, kMetThreads, smem, g->stream>>>(M);
+    count_launch();
+    sum_in_order_kernel<<<1, 32, 0, g->stream>>>(g->red, grid, g->red + grid);
+    count_launch();
+    GILA_CUDA(cudaGetLastError());
+    double h = 0.0;
+    GILA_CUDA(cudaMemcpyAsync(&h, g->red + grid, sizeof(double), cudaMemcpyDeviceToHost,
+                              g->stream));
+    GILA_CUDA(cudaStreamSynchronize(g->stream));
+    *rep_total = h;
+    *done = true;
     return GILA_OK;
 }
 

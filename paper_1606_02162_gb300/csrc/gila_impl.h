@@ -194,6 +194,10 @@ bool blocked_auto_applies(int64_t n, int64_t nnz_khop, size_t esz, const gila_tu
 // CTAs per SM the blocked grid aims at unless the tuning sets it.
 int64_t default_ctas_per_sm(int64_t nnz_khop, bool window);
 gila_status prepare_iteration(gila_graph* g, const gila_params* prm);
+// The repulsive total of the quality reductions over the blocked plan's
+// position tiles (FP32 placements with a plan only; *done = false otherwise).
+gila_status blocked_khop_metric(gila_graph* g, const gila_params* prm, const void* pos,
+                                bool* done, double* rep_total);
 // GILA_ECUDA (and clears the flag) when a blocked-path CTA gave up waiting
 // for its tile copy since the last call; synchronises st.
 gila_status blocked_tile_wait_failed(cudaStream_t st);

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "device_util.cuh"
+#include "ff.cuh"
 #include "force.cuh"
 #include "gila_impl.h"
 
@@ -307,93 +308,6 @@ __device__ __forceinline__ double dipow(double x, int e)
     return r;
 }
 
-// Double-float arithmetic: a value held as an unevaluated sum hi + lo of
-// two FP32 numbers (|lo| at most half an ulp of hi), 48 significant bits.
-// The building blocks are the exact error-free transformations of Knuth
-// (two-sum) and Dekker (two-product, here through a fused multiply-add);
-// every FP32 operation below is an explicitly rounded intrinsic, so the
-// compiler neither contracts nor reorders them.
-struct Ff {
-    float hi, lo;
-};
-
-__device__ __forceinline__ Ff ff_two_sum(float a, float b)
-{
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, err};
-}
-
-// |a| >= |b| (or a = 0)
-__device__ __forceinline__ Ff ff_fast_two_sum(float a, float b)
-{
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-
-__device__ __forceinline__ Ff ff_two_prod(float a, float b)
-{
-    const float p = __fmul_rn(a, b);
-    return {p, __fmaf_rn(a, b, -p)};
-}
-
-__device__ __forceinline__ Ff ff_from_double(double x)
-{
-    const float h = (float)x;
-    return {h, (float)(x - (double)h)};
-}
-
-__device__ __forceinline__ Ff ff_add(Ff a, Ff b)
-{
-    const Ff s = ff_two_sum(a.hi, b.hi);
-    return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-
-__device__ __forceinline__ Ff ff_mul(Ff a, Ff b)
-{
-    const Ff p = ff_two_prod(a.hi, b.hi);
-    const float c = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
-    return ff_fast_two_sum(p.hi, __fadd_rn(p.lo, c));
-}
-
-// |x_u - x_v|^2 from FP32 coordinates: the differences are exact as
-// double-floats (two-sum), their squares exact as double-floats
-// (two-product); only the square of each difference's low part (below
-// 2^-48 of the result) is left out.
-__device__ __forceinline__ Ff ff_dist2(float ax, float ay, float bx, float by)
-{
-    const Ff dx = ff_two_sum(ax, -bx);
-    const Ff dy = ff_two_sum(ay, -by);
-    const Ff px = ff_two_prod(dx.hi, dx.hi);
-    const Ff py = ff_two_prod(dy.hi, dy.hi);
-    const Ff s = ff_two_sum(px.hi, py.hi);
-    const float cross = __fmaf_rn(2.0f * dx.hi, dx.lo, __fmul_rn(2.0f * dy.hi, dy.lo));
-    const float low = __fadd_rn(__fadd_rn(s.lo, __fadd_rn(px.lo, py.lo)), cross);
-    return ff_fast_two_sum(s.hi, low);
-}
-
-// (1 / sqrt(r2))^q for r2 = hi + lo > 0 (q >= 0): the hardware's
-// approximate reciprocal square root y0 of hi (relative error below 2^-22)
-// refined by the series y = y0 (1 + e/2 + 3e^2/8) of y0 / sqrt(1 - e), with
-// e = 1 - r2 y0^2 formed exactly up to the rounding of its low parts (the
-// classical Newton step for the inverse square root carried one order
-// further); then q double-float products.
-__device__ __forceinline__ Ff ff_rsqrt_pow(Ff r2, int q)
-{
-    float y0;
-    asm("rsqrt.approx.f32 %0, %1;" : "=f"(y0) : "f"(r2.hi));
-    const Ff y2 = ff_two_prod(y0, y0);
-    const Ff t = ff_two_prod(r2.hi, y2.hi);
-    const float tl = __fadd_rn(t.lo, __fmaf_rn(r2.hi, y2.lo, __fmul_rn(r2.lo, y2.hi)));
-    const float e = __fsub_rn(__fsub_rn(1.0f, t.hi), tl);  // 1 - t.hi is exact near 1
-    const float corr = __fmul_rn(y0, __fmaf_rn(0.375f * e, e, 0.5f * e));
-    const Ff y = ff_fast_two_sum(y0, corr);
-    Ff r = {1.0f, 0.0f};
-    for (int i = 0; i < q; ++i) r = ff_mul(r, y);
-    return r;
-}
-
 // pass 0: [sum delta, count, sum delta^p/d, sum over k-hop pairs d^2/delta^q]
 // pass 1: [sum (delta - mean)^2, 0, 0, 0]
 // Each warp owns a fixed set of vertices; partial sums are combined in a
@@ -403,7 +317,7 @@ __global__ void __launch_bounds__(kRedThreads)
 metrics_kernel(int pass, int64_t n, const int64_t* __restrict__ row,
                const int32_t* __restrict__ col, const int64_t* __restrict__ krow,
                const uint32_t* __restrict__ kcol, const void* pos, double d, int p, int q,
-               double mean, double* __restrict__ partials)
+               double mean, double* __restrict__ partials, int skip_khop)
 {
     __shared__ double sh[kRedThreads / 32][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -425,7 +339,7 @@ metrics_kernel(int pass, int64_t n, const int64_t* __restrict__ row,
                 a0 += (dl - mean) * (dl - mean);
             }
         }
-        if (pass == 0 && sizeof(T) == 4) {
+        if (pass == 0 && sizeof(T) == 4 && !skip_khop) {
             // FP32 placements: each pair's term d^2 / delta^q in double-float
             // arithmetic (pairs of FP32 numbers, relative error about 1e-14,
             // far below FP32's 6e-8), eight terms per lane summed as a
@@ -461,7 +375,7 @@ metrics_kernel(int pass, int64_t n, const int64_t* __restrict__ row,
                 }
                 a3 += (double)s.hi + (double)s.lo;
             }
-        } else if (pass == 0) {
+        } else if (pass == 0 && !skip_khop) {
             for (int64_t e = krow[u] + lane; e < krow[u + 1]; e += 32) {
                 const int64_t v = kcol[e];
                 if (v <= u) continue;
@@ -639,15 +553,24 @@ gila_status compute_metrics(gila_graph* g, const gila_params* prm, const void* p
     double* res = g->red + (size_t)kRedBlocks * 4;
     double h[4];
     const bool f64 = is_f64(prm->precision);
+    // FP32 placements with a blocked plan take the k-hop term over the
+    // plan's shared-memory position tiles (the pairs' positions are
+    // otherwise random gathers through L2); the edge terms stay here
+    bool tiled = false;
+    double rep_tiled = 0.0;
+    {
+        gila_status bs = blocked_khop_metric(g, prm, pos, &tiled, &rep_tiled);
+        if (bs != GILA_OK) return bs;
+    }
     auto run = [&](int pass, double mean) -> cudaError_t {
         if (f64)
             metrics_kernel<double><<<kRedBlocks, kRedThreads, 0, g->stream>>>(
                 pass, g->n, g->row, g->col, g->krow, g->kcol, pos, prm->d, prm->p, prm->q, mean,
-                part);
+                part, 0);
         else
             metrics_kernel<float><<<kRedBlocks, kRedThreads, 0, g->stream>>>(
                 pass, g->n, g->row, g->col, g->krow, g->kcol, pos, prm->d, prm->p, prm->q, mean,
-                part);
+                part, tiled ? 1 : 0);
         count_launch();
         reduce_partials_kernel<<<1, 32, 0, g->stream>>>(part, kRedBlocks, res);
         count_launch();
@@ -658,7 +581,7 @@ gila_status compute_metrics(gila_graph* g, const gila_params* prm, const void* p
     if (e != cudaSuccess) return cuda_fail(e, "metrics pass 0");
     const double m = h[1];
     const double mean = m > 0 ? h[0] / m : 0.0;
-    const double att = h[2], rep = h[3];
+    const double att = h[2], rep = tiled ? rep_tiled : h[3];
     e = run(1, mean);
     if (e != cudaSuccess) return cuda_fail(e, "metrics pass 1");
     const double var = m > 0 ? h[0] / m : 0.0;

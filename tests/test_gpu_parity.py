@@ -593,3 +593,34 @@ def test_graph_create_flags():
         assert krow.tolist() == [0, 1, 3, 4] and kcol.tolist() == [1, 0, 2, 1]
     finally:
         G.gila_graph_destroy(h)
+
+
+@pytest.mark.parametrize("name,maker,k,tune", [
+    ("ba_tiles", lambda: I.barabasi_albert(12000, 3, 21), 2, dict(tiled=1, tile_vertices=2000)),
+    ("ba_tiles_k3", lambda: I.barabasi_albert(6000, 3, 22), 3, dict(tiled=1, tile_vertices=1000)),
+    ("mesh_windows", lambda: I.tri_mesh(70, 60), 3, dict(tiled=1)),
+], ids=["ba_tiles", "ba_tiles_k3", "mesh_windows"])
+@pytest.mark.parametrize("pq", [(2, 1), (3, 2)], ids=["fr", "p3q2"])
+def test_metrics_over_blocked_plan_match_oracle(name, maker, k, tune, pq):
+    """Once a graph has a blocked plan (FP32), its repulsive total is summed
+    over the plan's shared-memory position tiles or windows (each unordered
+    pair from its smaller end): every figure within 1e-11 of the oracle on
+    the same seeded FP32-rounded placement, as on the unplanned path."""
+    torch = _torch()
+    g = maker()
+    p, q = pq
+    pos = I.uniform_positions(g.n, 31).astype(np.float32).astype(np.float64)
+    okrow, okcol = O.khop(g.n, g.row_ptr, g.col_idx, k)
+    mo = O.metrics(g.n, g.row_ptr, g.col_idx, okrow, okcol, pos, d=1.3, p=p, q=q)
+    prm = G.params(k=k, d=1.3, p=p, q=q, precision=G.GILA_FP32)
+    with G.Graph.from_inputs(g) as h:
+        G.gila_graph_tune(h.handle, **tune)
+        x = torch.tensor(pos, dtype=torch.float32, device="cuda")
+        y, disp = torch.empty_like(x), torch.empty_like(x)
+        G.gila_profile_enable(h.handle, 2)
+        G.gila_layout_step(h.handle, prm, 0.5, x, y, disp)  # builds the plan
+        G.gila_profile_read(h.handle)
+        assert G.gila_profile_read_kernel(h.handle)["name"].startswith("blocked_kernel")
+        m = G.gila_layout_metrics(h.handle, prm, x)
+    for key in mo:
+        assert m[key] == pytest.approx(mo[key], rel=1e-11), key
