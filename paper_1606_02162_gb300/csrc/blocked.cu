@@ -169,9 +169,8 @@ __device__ __forceinline__ void add_compensated(Acc<T, COMP>& acc, T x, T y)
 // cells (sum of the unscaled repulsion terms, with compensation) are
 // complete in shared memory: F = d^2 cell + attraction, then the capped move.
 // Rows with at most kFinishDeg neighbours take one thread each; longer ones
-// are listed in row order (a block scan, so the list does not depend on
-// timing) and taken by whole warps, lanes striding the adjacency row. Every
-// row's order of additions is fixed.
+// are taken by the whole warp their row falls to, lanes striding the
+// adjacency row. Every row's order of additions is fixed.
 template <class T, int MODEL, bool COMP>
 __device__ __forceinline__ void window_finish(const struct BlockedArgs& A,
                                               const typename V2<T>::type* tile, int64_t tb,
@@ -515,7 +514,6 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
     }
 }
 
-constexpr int kFinishHubs = 256;  // rows per range finished by warps (more: by threads)
 
 template <class T, int MODEL, bool COMP>
 __device__ __forceinline__ void finish_row(const BlockedArgs& A, const Att<T, MODEL, COMP, kSrcShared>& att0,
@@ -545,8 +543,6 @@ __device__ __forceinline__ void window_finish(const BlockedArgs& A,
                                               int nrows)
 {
     using P2 = typename V2<T>::type;
-    __shared__ int s_scan[kBWarps + 1];
-    __shared__ int s_hub[kFinishHubs];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos);
     Att<T, MODEL, COMP, kSrcShared> att;
@@ -554,9 +550,12 @@ __device__ __forceinline__ void window_finish(const BlockedArgs& A,
     att.inv_d = (T)(1.0 / A.d);
     att.p = A.p;
     const uint32_t* col = reinterpret_cast<const uint32_t*>(A.col);
-    int nhub = 0;  // rows listed for the warps so far (the same in every thread)
-    for (int base = 0; base < nrows; base += kBThreads) {
-        const int i = base + (int)threadIdx.x;
+    // warp w takes rows [32 w, 32 w + 32), then 1024 further on: each lane
+    // one row; rows with more than kFinishDeg neighbours are then taken by
+    // the whole warp, one after the other, lanes striding the adjacency row
+    // (no barrier; a row's order of additions depends only on its length)
+    for (int base = warp * 32; base < nrows; base += kBThreads) {
+        const int i = base + lane;
         const bool live = i < nrows;
         int64_t rb = 0, re = 0;
         if (live) {
@@ -564,12 +563,7 @@ __device__ __forceinline__ void window_finish(const BlockedArgs& A,
             re = A.row[u0 + i + 1];
         }
         const bool hub = live && re - rb > kFinishDeg;
-        int total;
-        const int incl = block_inclusive_scan<int, kBThreads>(hub ? 1 : 0, s_scan, &total);
-        const int slot = nhub + incl - 1;
-        if (hub && slot < kFinishHubs) {
-            s_hub[slot] = i;
-        } else if (live) {
+        if (live && !hub) {
             Att<T, MODEL, COMP, kSrcShared> a1 = att;
             const P2 pu = pos[u0 + i];
             a1.xu = pu.x;
@@ -578,20 +572,21 @@ __device__ __forceinline__ void window_finish(const BlockedArgs& A,
             row_sum_rel(col, rb, re, 0, 1, a1, at);
             finish_row<T, MODEL, COMP>(A, att, cells, u0, i, at);
         }
-        nhub += total;
-    }
-    __syncthreads();
-    const int nh = nhub < kFinishHubs ? nhub : kFinishHubs;
-    for (int h = warp; h < nh; h += kBWarps) {
-        const int i = s_hub[h];
-        const P2 pu = pos[u0 + i];
-        Att<T, MODEL, COMP, kSrcShared> a1 = att;
-        a1.xu = pu.x;
-        a1.yu = pu.y;
-        Acc<T, COMP> at;
-        row_sum_rel(col, A.row[u0 + i], A.row[u0 + i + 1], lane, 32, a1, at);
-        at.group_reduce(32);
-        if (lane == 0) finish_row<T, MODEL, COMP>(A, att, cells, u0, i, at);
+        unsigned hubs = __ballot_sync(kFull, hub);
+        while (hubs) {
+            const int l = __ffs(hubs) - 1;
+            hubs &= hubs - 1;
+            const int ih = base + l;
+            const int64_t hb = __shfl_sync(kFull, rb, l), he = __shfl_sync(kFull, re, l);
+            const P2 pu = pos[u0 + ih];
+            Att<T, MODEL, COMP, kSrcShared> a1 = att;
+            a1.xu = pu.x;
+            a1.yu = pu.y;
+            Acc<T, COMP> at;
+            row_sum_rel(col, hb, he, lane, 32, a1, at);
+            at.group_reduce(32);
+            if (lane == 0) finish_row<T, MODEL, COMP>(A, att, cells, u0, ih, at);
+        }
     }
 }
 
