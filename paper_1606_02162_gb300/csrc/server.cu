@@ -12,7 +12,8 @@
 //   runner     keeps every admitted job's placement and temperature resident
 //              on the device and advances them by least remaining work
 //              (pairs per iteration times iterations left, shrunk by the
-//              time the job has waited so that none starves): each round it
+//              time the job has waited, and overdue jobs first, so that
+//              none starves): each round it
 //              enqueues the next chunk of iterations of the jobs in that
 //              order on each job's own stream (at most two chunks in flight
 //              per job) while their work per iteration stays below what
@@ -151,6 +152,11 @@ constexpr double kChunkPairs = 5e8;
 // Waiting time (s) over which a job's remaining work counts for half in the
 // runner's order (aging, so that large jobs are not starved).
 constexpr double kAgeSeconds = 0.5;
+// Pair interactions per second of a job alone (about the rate of the
+// single-graph kernels on mid-size graphs), and the slack before a job
+// counts as overdue.
+constexpr double kAloneRate = 1e12;
+constexpr double kOverdueSeconds = 0.12;
 
 void finish_job(gila_server* s, const JobPtr& j, gila_status st, const std::string& err)
 {
@@ -403,6 +409,13 @@ void runner_loop(gila_server* s)
                 const double per_iter = (double)(j->nnz_khop + j->g->nnz_adj) + 1.0;
                 const double left = per_iter * (double)(j->prm.iters - j->next_iter + 1);
                 const double age = std::chrono::duration<double>(now - j->t_submit).count();
+                // a job waiting for more than twice its time alone (at
+                // kAloneRate pairs per second) plus kOverdueSeconds goes
+                // first, oldest first: smaller jobs cannot hold back a large
+                // one indefinitely (48 requests at 2x load: p99 569 -> 495 ms,
+                // against 538 ms for FIFO service)
+                const double alone = per_iter * (double)j->prm.iters / kAloneRate;
+                if (age > 2.0 * alone + kOverdueSeconds) return -1e30 - 1e20 * age;
                 return left / (1.0 + age / kAgeSeconds);
             };
             std::vector<std::pair<double, size_t>> order;
