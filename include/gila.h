@@ -472,8 +472,8 @@ gila_status gila_profile_read(gila_graph* g, int64_t* builds, double* build_ms,
                               int64_t* iter_launches, double* iter_ms);
 
 /* With on = 2 each iteration's repulsion kernel (the one that streams the
- * k-hop lists of Section 4.5: blocked_kernel, window_kernel,
- * iteration_kernel or ordered_kernel) is also timed on its own, between
+ * k-hop lists of Section 4.5: "blocked_kernel", "blocked_kernel (window)",
+ * "iteration_kernel" or "ordered_kernel") is also timed on its own, between
  * events recorded directly before and after its launch. Returns the number
  * of such launches since the previous call and their total ms, and copies
  * the name of the last kernel timed into name (NUL-terminated, at most

@@ -202,8 +202,10 @@ def _mesh_with_isolated(r, c, extra):
                                   dict(tiled=1, ctas_per_sm=12)], ids=["cps4", "cps1", "cps12"])
 def test_step_parity_window_mode(k, prec, tune):
     """Banded ids (a triangulated mesh, then 37 isolated vertices with empty
-    rows): every row range gets its own window of positions and reads kcol in
-    place, starting at a 16-byte boundary before its first row."""
+    rows): every row range gets its own shared-memory window of positions
+    (its first id rounded down to a 16-byte boundary), streams its rows'
+    16-bit window-relative ids and finishes its rows in the CTA; the
+    isolated vertices' ranges have nothing to stream and must not move."""
     torch = _torch()
     g = _mesh_with_isolated(37, 41, 37)
     pos = I.uniform_positions(g.n, 6)
