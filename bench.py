@@ -832,7 +832,7 @@ def main():
             s = run_graph(args, name, 3, 1, False, False, ws, rank, dist, local)
             secondary[name] = secondary_record(s)
         secondary["batch4096"] = bench_batch(1, 1, ws, local, dist)
-        secondary["serve"] = bench_serve(ws, local, dist, count=24, emax=1e6, mults=(2.0, 4.0))
+        secondary["serve"] = bench_serve(ws, local, dist, count=48, emax=1e6, mults=(2.0, 4.0))
 
     if dist is not None:
         dist.destroy_process_group()

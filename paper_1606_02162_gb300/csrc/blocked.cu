@@ -935,9 +935,11 @@ cudaError_t launch_pair(gila_graph* g, const BlockedArgs& B, const CombineArgs& 
 // The k-hop term of the quality reductions, sum over unordered k-hop pairs
 // {u, v} of d^2 / delta^q, for FP32 placements that have a blocked plan:
 // one CTA per (tile or window, row range), positions from the shared-memory
-// tile, each pair counted once from its smaller end. Every row of the range
-// is sorted, so the entries of row u that lie in the tile and above u are
-// one contiguous run, found by two binary searches; a warp walks it with
+// tile, each pair counted once from its smaller end. Every row is sorted,
+// so the entries of row u in the tile are one contiguous run that starts
+// after the row's runs in earlier tiles (the plan's segment lengths), and
+// only the tile that holds u itself needs a binary search to drop the ids
+// up to u; a warp walks the run with
 // each term in double-float arithmetic (ff.cuh), sixteen terms per lane
 // summed as a double-float, then added in FP64; the CTA's FP64 partial goes
 // to its own slot, and the partials are added in CTA order.
@@ -946,6 +948,7 @@ constexpr int kMetWarps = kMetThreads / 32;
 
 struct MetricArgs {
     const int64_t* krow;
+    const int64_t* len;    // tile mode: nt n segment lengths (row u's entries in tile j)
     const uint32_t* kcol;
     const int32_t* range_start;
     const int64_t* wbase;  // window mode: 2 nr (first id, length), else null
@@ -993,19 +996,26 @@ __global__ void __launch_bounds__(kMetThreads, 1) khop_metric_kernel(const Metri
         mbar_wait(&tile_bar, 0, A.wait_ns);
         const Ff d2f = ff_from_double(A.d * A.d);
         for (int64_t u = u0 + warp; u < u1; u += kMetWarps) {
-            const int64_t kb = A.krow[u], ke = A.krow[u + 1];
-            const uint32_t key_lo = (uint32_t)(tb > u + 1 ? tb : u + 1);
-            const uint32_t key_hi = (uint32_t)(tb + tn);
-            if (key_lo >= key_hi || kb == ke) continue;
-            auto lower = [&](uint32_t key) {
-                int64_t x = kb, y = ke;
+            if (tb + tn <= u + 1) continue;  // no id of this tile lies above u
+            // the row's entries in this tile: the whole row in window mode;
+            // in tile mode the segment after the row's segments in earlier
+            // tiles (their lengths, summed in order)
+            int64_t lo = A.krow[u], hi;
+            if (A.wbase) {
+                hi = A.krow[u + 1];
+            } else {
+                for (int jj = 0; jj < j; ++jj) lo += A.len[(int64_t)jj * A.n + u];
+                hi = lo + A.len[(int64_t)j * A.n + u];
+            }
+            if (tb <= u) {
+                // the tile holds u: keep the ids above it (binary search)
+                int64_t x = lo, y = hi;
                 while (x < y) {
                     const int64_t mid = (x + y) >> 1;
-                    if (A.kcol[mid] < key) x = mid + 1; else y = mid;
+                    if (A.kcol[mid] <= (uint32_t)u) x = mid + 1; else y = mid;
                 }
-                return x;
-            };
-            const int64_t lo = lower(key_lo), hi = lower(key_hi);
+                lo = x;
+            }
             if (lo >= hi) continue;
             const float2 qu = A.pos[u];
             Ff s = {0.f, 0.f};
@@ -1529,6 +1539,7 @@ gila_status blocked_khop_metric(gila_graph* g, const gila_params* prm, const voi
     if (s != GILA_OK) return s;
     MetricArgs M;
     M.krow = g->krow;
+    M.len = P.window ? nullptr : P.len;
     M.kcol = g->kcol;
     M.range_start = P.range_start;
     M.wbase = P.window ? P.wtile : nullptr;
