@@ -97,3 +97,39 @@ def test_whole_layout_quality(ba, k):
     for key in ("edge_cv", "rep_att_ratio"):
         assert abs(m32[key] - mo[key]) <= 0.02 * abs(mo[key]), (key, m32[key], mo[key])
         assert abs(m32[key] - m64[key]) <= 0.02 * abs(m64[key]), (key, m32[key], m64[key])
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_ba_1m_edges_sampled(k):
+    """The 1M-edge Barabasi-Albert graph (n = 333,334; the serving stream's
+    largest requests), on the blocked path in 14 tiles with short segments:
+    sampled k-hop rows exact, and the capped moves (first temperature) of a
+    systematic sample of 2,048 vertices and the 16 largest hubs within 1e-4
+    of the largest move, against the oracle's step over a k-hop CSR that
+    holds only the sample's rows."""
+    import torch
+    g, pos = I.workload("ba1m")
+    deg = np.diff(g.row_ptr)
+    sel = np.unique(np.concatenate([np.arange(0, g.n, g.n // 2048, dtype=np.int64)[:2048],
+                                    np.argsort(-deg, kind="stable")[:16]]))
+    counts, rows = O.khop_rows(g.n, g.row_ptr, g.col_idx, k, sel)
+    c = np.zeros(g.n, dtype=np.int64)
+    c[sel] = counts
+    krow = np.zeros(g.n + 1, dtype=np.int64)
+    np.cumsum(c, out=krow[1:])
+    t = 0.1 * np.sqrt(g.n)
+    with G.Graph.from_inputs(g) as h:
+        G.gila_build_khop(h.handle, k)
+        gc, grows = G.gila_khop_export_rows(h.handle, sel)
+        assert np.array_equal(gc, counts) and np.array_equal(grows, rows)
+        x = torch.tensor(pos, dtype=torch.float32, device="cuda")
+        y, disp = torch.empty_like(x), torch.empty_like(x)
+        G.gila_profile_enable(h.handle, 2)
+        G.gila_layout_step(h.handle, G.params(k=k), t, x, y, disp)
+        G.gila_profile_read(h.handle)
+        assert G.gila_profile_read_kernel(h.handle)["name"].startswith("blocked_kernel")
+        base = x.double().cpu().numpy()
+        got = disp.double().cpu().numpy()[sel]
+    _, odisp = O.step(g.n, g.row_ptr, g.col_idx, krow, rows, base, t)
+    odisp = odisp[sel]
+    assert np.abs(got - odisp).max() <= 1e-4 * np.abs(odisp).max()
