@@ -123,9 +123,10 @@ typedef struct gila_tuning {
     int32_t warp_max;      /* ... rows <= this use one warp (8192) */
     int32_t block_max;     /* ... rows <= this use one block (65536); longer rows are chunked */
     int32_t chunk;         /* entries per chunk of a chunked row (32768) */
-    int32_t ctas_per_sm;   /* blocked path: row ranges per tile chosen so that the grid holds
-                              about this many CTAs per SM (tiles: 1 below 10^8 k-hop
-                              entries, 4 below 2e9, 8 beyond; windows: 2) */
+    int32_t ctas_per_sm;   /* blocked path: each tile's rows are cut into ranges so that the
+                              grid holds at most about this many CTAs per SM, all of about
+                              equal cost (tiles: 1 below 10^8 k-hop entries, 4 below 2e9, 8
+                              beyond; windows: 2) */
     int32_t bank_spread;   /* blocked path: 0 or 1 (default on) orders each row's entries of
                               a tile so that the lanes of one shared-memory gather read
                               distinct banks where the entries allow; -1 keeps ascending

@@ -1,8 +1,10 @@
 // Blocked iteration path: positions staged in shared memory by tiles, the
 // k-hop ids rearranged once so that every CTA streams one contiguous block.
 //
-// Tiles: tile j holds the positions of ids [j tv, (j+1) tv). Ranges: rows are
-// cut into contiguous ranges of about equal total list length. Block (j, r)
+// Tiles: tile j holds the positions of ids [j tv, (j+1) tv). Ranges: each
+// tile's rows are cut into contiguous ranges on their own, so that the
+// blocks (j, r) cost about the same whichever tile holds the most entries
+// (on a power-law graph the hubs' tile holds twice the mean). Block (j, r)
 // holds, for every row u of range r in order, the entries of u's k-hop row
 // that fall in tile j, in an order chosen so that the lanes of one gather
 // read distinct shared-memory banks; block starts are 16-byte aligned. An
@@ -36,12 +38,11 @@ namespace {
 
 constexpr int kBThreads = 1024;
 constexpr int kBWarps = kBThreads / 32;
+static_assert(kBWarps == 32, "the slot flush gives lane w of warp 0 the slots of warp w");
 constexpr int kSmemCap = 227 * 1024;
 constexpr int kMaxRows = 4096;  // rows per range (directory in shared memory)
 constexpr int kTileBudget = kSmemCap - (kMaxRows + 1) * 4 - 4096;
 constexpr int64_t kMaxTile = 65534;  // tile-relative ids and the far slot's id fit 16 bits
-constexpr int64_t kConvergeSeg = 2048;  // mean entries per (tile, row) below which FP32 steps
-                                        // are taken warp-uniformly
 constexpr uint32_t kBulkChunk = 32768;      // bytes per bulk copy instruction
 constexpr int64_t kBlockedMinNnz = 4000000;  // automatic mode: k-hop entries needed (tiles)
 constexpr uint64_t kWaitNs = 1000000000ull;  // bound on a tile wait (1 s, far above any copy)
@@ -66,19 +67,19 @@ __device__ int g_tile_wait_failed = 0;
 struct BlockedArgs {
     const uint16_t* tk;        // tile-relative ids, block by block, in share storage order
     const int64_t* toff;       // nt n: start of segment (tile j, row u) within its block
-    const int64_t* blk;        // 2 nt nr: first slot in tk and entry count of block (j, r)
-    const int32_t* range_start;
+    const int64_t* blk;        // 2 nb: first slot in tk and entry count of block b
+    const int4* bdesc;         // nb: first row, end row and tile of block b
     int64_t n;
-    int32_t nt, tv, nr;
+    int32_t nt, tv;
     int q;
     const void* pos;
     void* part;                // nt n cells of 4 T: (sx, sy, cx, cy) without the factor d^2
     uint64_t wait_ns;          // bound on the tile wait
     int skip_copy;             // test hook: announce the tile but copy nothing
     // window mode (one window of positions per row range, rows finished in
-    // the CTA): first id and length of range r's window, the largest window
+    // the CTA): first id and length of block b's window, the largest window
     // and range, and what the finish needs
-    const int64_t* wbase;      // 2 nr
+    const int64_t* wbase;      // 2 nb
     int32_t wmax, rmax;
     const int64_t* row;
     const int32_t* col;
@@ -86,7 +87,6 @@ struct BlockedArgs {
     int p;
     void* pos_out;
     void* disp_out;
-    int converge;              // FP32 steps taken warp-uniformly (short segments)
 };
 
 template <class T, bool COMP>
@@ -198,15 +198,17 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
     __shared__ __align__(8) uint64_t tile_bar;
     __shared__ int tile_ok;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int j = WIN ? 0 : blockIdx.x / A.nr, r = WIN ? blockIdx.x : blockIdx.x % A.nr;
-    const int64_t u0 = A.range_start[r], u1 = A.range_start[r + 1];
+    const int4 bd = A.bdesc[blockIdx.x];  // rows [bd.x, bd.y) of tile bd.z (0 in window mode)
+    const int j = WIN ? 0 : bd.z;
+    const int64_t u0 = bd.x, u1 = bd.y;
     const int nrows = (int)(u1 - u0);
     const int64_t bsp = A.blk[2 * (int64_t)blockIdx.x];  // the block's first slot in tk
     // a block holds at most kMaxRows segments of at most tv entries: < 2^31
     const int32_t L = (int32_t)A.blk[2 * (int64_t)blockIdx.x + 1];
     const P2* __restrict__ pos = reinterpret_cast<const P2*>(A.pos);
-    const int64_t tb = WIN ? A.wbase[2 * r] : (int64_t)j * A.tv;
-    const int64_t tn = WIN ? A.wbase[2 * r + 1] : ((A.n - tb < A.tv) ? A.n - tb : (int64_t)A.tv);
+    const int64_t tb = WIN ? A.wbase[2 * blockIdx.x] : (int64_t)j * A.tv;
+    const int64_t tn = WIN ? A.wbase[2 * blockIdx.x + 1]
+                           : ((A.n - tb < A.tv) ? A.n - tb : (int64_t)A.tv);
     // the cell of row i of the range: in shared memory (window mode) or the
     // global partial of (tile j, row u0 + i)
     auto cellp = [&](int64_t i) -> P2* {
@@ -227,6 +229,15 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
         far.x = FarSlot<T>::v;
         far.y = FarSlot<T>::v;
         tile[WIN ? tn : (int64_t)A.tv] = far;
+    }
+    if (WIN && threadIdx.x == 32) {
+        // the finish's adjacency (row offsets, neighbour ids) and the rows'
+        // own positions, pulled into L2 while the window loads and the
+        // entries stream
+        const int64_t ab = A.row[u0], ae = A.row[u1];
+        prefetch_l2_range(A.row + u0, sizeof(int64_t) * (size_t)(u1 - u0 + 1));
+        prefetch_l2_range(A.col + ab, sizeof(int32_t) * (size_t)(ae - ab));
+        prefetch_l2_range(pos + u0, sizeof(P2) * (size_t)(u1 - u0));
     }
     // meanwhile: the row directory (segment starts within the block) and
     // zero partials for rows with no entries in this tile
@@ -377,20 +388,17 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                         while (p >= re) close_row();
                         eight(c);
                     }
-                } else if (A.converge) {
-                    // short segments (rows change often): only the closing of
-                    // rows diverges, the terms are issued once for the warp
+                } else {
+                    // FP32: only the closing of rows diverges, the terms are
+                    // issued once for the warp (measured against issuing the
+                    // step's terms separately for the lanes that close a row:
+                    // Chung-Lu n = 250,000, k = 3, 4.88 vs 4.96 ms per launch;
+                    // Barabasi-Albert n = 100,000, k = 3, 0.172 vs 0.186)
                     if (p >= lim && p < b) {
                         while (p >= re) close_row();
                         lim = (re < b) ? re : b;
                     }
                     if (p < b) eight(c);
-                } else if (p < lim) {
-                    eight(c);
-                } else if (p < b) {
-                    while (p >= re) close_row();
-                    lim = (re < b) ? re : b;
-                    eight(c);
                 }
                 p += kStep;
             }
@@ -484,26 +492,77 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // rows cut by warp bounds: add their slots in warp order
-        int cur = -1;
-        Acc<T, COMP> sum;
-        auto flush = [&]() {
-            if (cur >= 0) store_cell<T, COMP>(cellp(cur), sum);
+    if (warp == 0) {
+        // rows cut by warp bounds: warp w's slots (a row begun before the
+        // warp, a row running past its end) go to lane w of warp 0, and a
+        // segmented scan across the lanes adds each row's slots in warp
+        // order (a row's slots lie in consecutive warps; a warp without
+        // slots lies between no two slots of one row)
+        const Slot<T, COMP>& hs = head[lane];
+        const Slot<T, COMP>& ts = tail[lane];
+        auto acc_of = [](const Slot<T, COMP>& sl) {
+            Acc<T, COMP> v;
+            v.sx = sl.v[0];
+            v.sy = sl.v[1];
+            v.cx = sl.v[2];
+            v.cy = sl.v[3];
+            return v;
         };
-        for (int w = 0; w < kBWarps; ++w) {
-            const Slot<T, COMP>* sl[2] = {&head[w], &tail[w]};
-            for (int h = 0; h < 2; ++h) {
-                if (sl[h]->row < 0) continue;
-                if (sl[h]->row != cur) {
-                    flush();
-                    cur = sl[h]->row;
-                    sum = Acc<T, COMP>();
-                }
-                sum.merge(sl[h]->v[0], sl[h]->v[1], sl[h]->v[2], sl[h]->v[3]);
+        // the lane's elements: A (its first row) and, with has_b, B (a
+        // second row); a lane without slots takes a row no lane has
+        const bool hh = hs.row >= 0, ht = ts.row >= 0;
+        const int ra = hh ? hs.row : (ht ? ts.row : -2 - lane);
+        Acc<T, COMP> ea = hh ? acc_of(hs) : (ht ? acc_of(ts) : Acc<T, COMP>());
+        bool has_b = false;
+        Acc<T, COMP> eb;
+        if (hh && ht) {
+            if (ts.row == hs.row) {
+                ea.merge(ts.v[0], ts.v[1], ts.v[2], ts.v[3]);
+            } else {
+                has_b = true;
+                eb = acc_of(ts);
             }
         }
-        flush();
+        const int orow = has_b ? ts.row : ra;
+        Acc<T, COMP> x = has_b ? eb : ea;
+        const int prev_orow = __shfl_up_sync(kFull, orow, 1);
+        const bool cont = lane > 0 && prev_orow == ra;
+        const unsigned starts = __ballot_sync(kFull, has_b || !cont);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned span = (lane >= o) ? (((1u << o) - 1u) << (lane - o + 1)) : 0u;
+            const T sx = __shfl_up_sync(kFull, x.sx, o);
+            const T sy = __shfl_up_sync(kFull, x.sy, o);
+            const T cx = COMP ? __shfl_up_sync(kFull, x.cx, o) : T(0);
+            const T cy = COMP ? __shfl_up_sync(kFull, x.cy, o) : T(0);
+            if (lane >= o && (starts & span) == 0) {
+                Acc<T, COMP> y;
+                y.sx = sx;
+                y.sy = sy;
+                y.cx = cx;
+                y.cy = cy;
+                y.merge(x.sx, x.sy, x.cx, x.cy);
+                x = y;
+            }
+        }
+        const T px = __shfl_up_sync(kFull, x.sx, 1);
+        const T py = __shfl_up_sync(kFull, x.sy, 1);
+        const T pcx = COMP ? __shfl_up_sync(kFull, x.cx, 1) : T(0);
+        const T pcy = COMP ? __shfl_up_sync(kFull, x.cy, 1) : T(0);
+        if (has_b) {
+            // A's run ends here: the run reaching into A, then A
+            Acc<T, COMP> carry;
+            if (cont) {
+                carry.sx = px;
+                carry.sy = py;
+                carry.cx = pcx;
+                carry.cy = pcy;
+            }
+            carry.merge(ea.sx, ea.sy, ea.cx, ea.cy);
+            store_cell<T, COMP>(cellp(ra), carry);
+        }
+        const int next_ra = __shfl_down_sync(kFull, ra, 1);
+        if (orow >= 0 && (lane == 31 || next_ra != orow)) store_cell<T, COMP>(cellp(orow), x);
     }
     if constexpr (WIN) {
         // every row of the range is complete here: F = d^2 (its cell) + the
@@ -770,7 +829,8 @@ template <int G, bool SPREAD>
 __global__ void __launch_bounds__(kSpreadWarps * 32) block_layout_kernel(
     int64_t n, const int64_t* __restrict__ krow, const uint32_t* __restrict__ kcol, int nt,
     int tv, const int64_t* __restrict__ wbase, const int64_t* __restrict__ toff,
-    const int64_t* __restrict__ blk, const int32_t* __restrict__ range_start, int nr,
+    const int64_t* __restrict__ blk, const int32_t* __restrict__ tfirst,
+    const int32_t* __restrict__ rstart, const int32_t* __restrict__ rblock,
     uint16_t* __restrict__ tk)
 {
     __shared__ uint32_t s_in[kSpreadWarps][kSpreadChunk];  // the chunk's ids by residue
@@ -784,18 +844,23 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) block_layout_kernel(
     int64_t lo, hi;
     seg_bounds(krow, kcol, u, j, nt, tv, &lo, &hi);
     if (hi == lo) return;
-    // the block (j, r) that holds the segment
-    int ra = 0, rb = nr - 1;
+    // the range of tile j that holds row u (tile j's ranges: blocks
+    // tfirst[j] .. tfirst[j + 1] - 1 in tile order, their row bounds at
+    // rstart + tfirst[j] + j), and that range's block
+    const int32_t f0 = tfirst[j];
+    const int32_t* st = rstart + f0 + j;
+    int ra = 0, rb = tfirst[j + 1] - f0 - 1;
     while (ra < rb) {
         const int mid = (ra + rb + 1) >> 1;
-        if (range_start[mid] <= u) ra = mid; else rb = mid - 1;
+        if (st[mid] <= u) ra = mid; else rb = mid - 1;
     }
-    // ids are relative to tile j, or in window mode to range ra's window;
+    const int64_t b = rblock[f0 + ra];
+    // ids are relative to tile j, or in window mode to block b's window;
     // the padding takes the far slot one past the tile or window
-    const uint32_t tb = wbase ? (uint32_t)wbase[2 * ra] : (uint32_t)j * (uint32_t)tv;
-    const uint16_t pad = wbase ? (uint16_t)wbase[2 * ra + 1] : (uint16_t)tv;
-    const int64_t bsp = blk[2 * ((int64_t)j * nr + ra)];
-    const int32_t L = (int32_t)blk[2 * ((int64_t)j * nr + ra) + 1];
+    const uint32_t tb = wbase ? (uint32_t)wbase[2 * b] : (uint32_t)j * (uint32_t)tv;
+    const uint16_t pad = wbase ? (uint16_t)wbase[2 * b + 1] : (uint16_t)tv;
+    const int64_t bsp = blk[2 * b];
+    const int32_t L = (int32_t)blk[2 * b + 1];
     const int32_t m8 = lane_len(L);
     const int32_t S0 = (int32_t)toff[i], S1 = S0 + (int32_t)(hi - lo);
     const int32_t S8 = S0 + (int32_t)((hi - lo + kStep - 1) & ~int64_t(kStep - 1));  // padded end
@@ -950,10 +1015,10 @@ struct MetricArgs {
     const int64_t* krow;
     const int64_t* len;    // tile mode: nt n segment lengths (row u's entries in tile j)
     const uint32_t* kcol;
-    const int32_t* range_start;
-    const int64_t* wbase;  // window mode: 2 nr (first id, length), else null
+    const int4* bdesc;     // nb: first row, end row and tile of block b
+    const int64_t* wbase;  // window mode: 2 nb (first id, length), else null
     int64_t n;
-    int32_t nt, tv, nr, tcap;
+    int32_t nt, tv, tcap;
     double d;
     int q;
     const float2* pos;
@@ -969,10 +1034,11 @@ __global__ void __launch_bounds__(kMetThreads, 1) khop_metric_kernel(const Metri
     __shared__ int tile_ok;
     __shared__ double s_part[kMetWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int j = (int)(blockIdx.x / A.nr), r = (int)(blockIdx.x % A.nr);
-    const int64_t u0 = A.range_start[r], u1 = A.range_start[r + 1];
-    const int64_t tb = A.wbase ? A.wbase[2 * r] : (int64_t)j * A.tv;
-    const int64_t tn = A.wbase ? A.wbase[2 * r + 1]
+    const int4 bd = A.bdesc[blockIdx.x];
+    const int j = bd.z;
+    const int64_t u0 = bd.x, u1 = bd.y;
+    const int64_t tb = A.wbase ? A.wbase[2 * blockIdx.x] : (int64_t)j * A.tv;
+    const int64_t tn = A.wbase ? A.wbase[2 * blockIdx.x + 1]
                                : ((A.n - tb < A.tv) ? A.n - tb : (int64_t)A.tv);
     if (threadIdx.x == 0) {
         const uint32_t bytes = (uint32_t)(((size_t)tn * sizeof(float2)) & ~size_t(15));
@@ -1094,7 +1160,8 @@ void free_tile_plans(gila_graph* g)
         cudaFree(P.hubs);
         cudaFree(P.wtile);
         cudaFree(P.rowspan);
-        cudaFree(P.range_start);
+        cudaFree(P.bdesc);
+        cudaFree(P.rdir);
         cudaFree(P.blk);
         cudaFree(P.toff);
         cudaFree(P.tk);
@@ -1116,27 +1183,63 @@ __global__ void rowspan_kernel(int64_t n, const int64_t* __restrict__ krow,
     span[2 * u + 1] = b < e ? (int32_t)kcol[e - 1] : -1;
 }
 
-// Row ranges of about equal cost (entries + a per-row term), at most
-// kMaxRows rows each: rs[r] .. rs[r + 1].
-std::vector<int32_t> partition_rows(const std::vector<int64_t>& cost, int64_t total,
-                                    int64_t nr_target)
+// Cost of a row in one tile's (or window's) block: its padded entries and a
+// per-row term where it has entries (directory, row change, cell store),
+// else only the zeroed cell.
+inline int64_t row_cost(int64_t len)
 {
-    const int64_t n = (int64_t)cost.size();
-    std::vector<int32_t> rs;
-    rs.push_back(0);
-    const double per = (double)total / (double)std::max<int64_t>(nr_target, 1);
-    double acc = 0.0;
-    int64_t rows = 0;
-    for (int64_t u = 0; u < n; ++u) {
-        if (rows > 0 &&
-            (acc + cost[(size_t)u] / 2.0 > per * (double)rs.size() || rows >= kMaxRows)) {
-            rs.push_back((int32_t)u);
-            rows = 0;
-        }
-        acc += (double)cost[(size_t)u];
-        ++rows;
+    return len > 0 ? 8 + ((len + kStep - 1) & ~int64_t(kStep - 1)) : 1;
+}
+
+// Greedy cut of one tile's rows into ranges of cost at most cap (a range
+// takes at least one row) and at most kMaxRows rows; pre holds the prefix
+// sums of the rows' costs (n + 1 values). Returns the number of ranges,
+// stopping once it exceeds limit; fills cuts (the range bounds) if given.
+int64_t cut_rows(const int64_t* pre, int64_t n, int64_t cap, int64_t limit,
+                 std::vector<int32_t>* cuts)
+{
+    int64_t s = 0, count = 0;
+    if (cuts) cuts->assign(1, 0);
+    while (s < n) {
+        // the last e with pre[e] - pre[s] <= cap, at least s + 1
+        int64_t e = (int64_t)(std::upper_bound(pre + s + 1, pre + n + 1, pre[s] + cap) - pre) - 1;
+        e = std::min<int64_t>(std::max<int64_t>(e, s + 1), s + kMaxRows);
+        if (cuts) cuts->push_back((int32_t)e);
+        if (++count > limit) return count;
+        s = e;
     }
-    rs.push_back((int32_t)n);
+    return count;
+}
+
+// Row ranges of every tile (window mode: one), all blocks with at most the
+// same cost, the smallest for which the blocks number at most `target` (or
+// the fewest the row limit allows). pre: nt prefix-sum arrays of n + 1
+// costs, tile after tile. A grid of about target equal CTAs then ends
+// together, where equal row ranges for all tiles left the hubs' tile with
+// CTAs twice the mean and one more range than the target sent a few CTAs
+// into a second wave (Barabasi-Albert n = 100,000, k = 2: 156 CTAs on 152
+// SMs, the SMs busy 54% of the kernel's time).
+std::vector<std::vector<int32_t>> partition_blocks(const std::vector<int64_t>& pre, int64_t n,
+                                                   int64_t nt, int64_t target)
+{
+    auto count = [&](int64_t cap, int64_t limit) {
+        int64_t c = 0;
+        for (int64_t j = 0; j < nt && c <= limit; ++j)
+            c += cut_rows(pre.data() + j * (n + 1), n, cap, limit - c, nullptr);
+        return c;
+    };
+    int64_t hi = 0;  // a cap every tile fits in whole: the fewest ranges
+    for (int64_t j = 0; j < nt; ++j) hi = std::max<int64_t>(hi, pre[(size_t)(j * (n + 1) + n)]);
+    target = std::max<int64_t>(target, count(hi, INT64_MAX));
+    int64_t lo = 0;  // count(lo) > target unless single rows already fit
+    if (count(lo, target) <= target) hi = lo;
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (count(mid, target) <= target) hi = mid; else lo = mid;
+    }
+    std::vector<std::vector<int32_t>> rs((size_t)nt);
+    for (int64_t j = 0; j < nt; ++j)
+        cut_rows(pre.data() + j * (n + 1), n, hi, INT64_MAX, &rs[(size_t)j]);
     return rs;
 }
 
@@ -1153,19 +1256,12 @@ int64_t default_ctas_per_sm(int64_t nnz_khop, bool window)
     return nnz_khop < 100000000LL ? 1 : nnz_khop < 2000000000LL ? 4 : 8;
 }
 
-// Number of row ranges per tile that gives the grid about ctas_per_sm CTAs
-// per SM: 4 by default, 8 for lists of 2e9 entries and more, where a CTA
-// streams tens of MB and the end of the grid waits on the slowest
-// (measured: Barabasi-Albert 2.4e8 entries best at 4, Chung-Lu 1.1e10 at 8).
-int64_t ranges_target(const gila_graph* g, int64_t nt, bool window)
+// CTAs (blocks) the grid aims at: about ctas_per_sm per SM.
+int64_t blocks_target(const gila_graph* g, bool window)
 {
-    const int64_t n = g->n;
     const int64_t per_sm = g->tune.ctas_per_sm > 0 ? g->tune.ctas_per_sm
                                                    : default_ctas_per_sm(g->nnz_khop, window);
-    const int sms = sm_count(g->device);
-    const int64_t t = std::max<int64_t>((per_sm * (int64_t)sms + nt - 1) / nt,
-                                        (n + kMaxRows - 1) / kMaxRows);
-    return std::min<int64_t>(t, n);
+    return std::max<int64_t>(1, per_sm * (int64_t)sm_count(g->device));
 }
 
 // The adjacency rows longer than kHubDeg, which the combine kernel gives a
@@ -1227,17 +1323,15 @@ gila_status plan_window(gila_graph* g, size_t esz, TilePlan& P, bool* fits,
                               cudaMemcpyDeviceToHost, g->stream));
     GILA_CUDA(cudaStreamSynchronize(g->stream));
     len.assign((size_t)n, 0);
-    std::vector<int64_t> cost((size_t)n);
-    int64_t total = 0;
+    std::vector<int64_t> pre((size_t)n + 1, 0);
     for (int64_t u = 0; u < n; ++u) {
         len[(size_t)u] = krow[(size_t)u + 1] - krow[(size_t)u];
-        cost[(size_t)u] = 8 + len[(size_t)u];
-        total += cost[(size_t)u];
+        pre[(size_t)u + 1] = pre[(size_t)u] + row_cost(len[(size_t)u]);
     }
     // enough ranges for several CTAs per SM, but at least about 16 entries
     // per thread of a CTA (a small graph is one or a few ranges)
-    const int64_t by_work = std::max<int64_t>(1, total / ((int64_t)kBThreads * 16));
-    rs = partition_rows(cost, total, std::min<int64_t>(ranges_target(g, 1, true), by_work));
+    const int64_t by_work = std::max<int64_t>(1, pre[(size_t)n] / ((int64_t)kBThreads * 16));
+    rs = partition_blocks(pre, n, 1, std::min<int64_t>(blocks_target(g, true), by_work))[0];
     const int64_t nr = (int64_t)rs.size() - 1;
     wb.assign(2 * (size_t)nr, 0);
     int64_t wmax = 0, rmax = 0;
@@ -1271,45 +1365,87 @@ gila_status plan_window(gila_graph* g, size_t esz, TilePlan& P, bool* fits,
     return GILA_OK;
 }
 
-// The block layout shared by tiles and windows: (j, r) blocks in that
-// order, each in share storage (lane_len(L) slots per thread; block starts
-// are multiples of 8 slots, 16 bytes); segments padded to multiples of 8
-// entries; segment starts within their block; ids rearranged into 16-bit
-// relative ids. wb (window mode) gives each range's window; tiles are
-// [j tv, (j + 1) tv).
+// The block layout shared by tiles and windows: blocks (j, r) for each
+// tile j's ranges rs[j], each in share storage (lane_len(L) slots per
+// thread; block starts are multiples of 8 slots, 16 bytes); segments padded
+// to multiples of 8 entries; segment starts within their block; ids
+// rearranged into 16-bit relative ids. wb (window mode, one tile) gives each
+// range's window; tiles are [j tv, (j + 1) tv). Blocks are numbered (and
+// launched) costliest first, so that in a grid of several waves the CTAs
+// that start last are short ones.
 gila_status build_layout(gila_graph* g, size_t esz, TilePlan& P, int64_t nt, int64_t tv,
-                         const std::vector<int64_t>& len, const std::vector<int32_t>& rs,
+                         const std::vector<int64_t>& len,
+                         const std::vector<std::vector<int32_t>>& rs,
                          const std::vector<int64_t>* wb)
 {
     const int64_t n = g->n;
     const int64_t cells = n * nt;
-    const int64_t nr = (int64_t)rs.size() - 1;
-    std::vector<int64_t> toff((size_t)cells), blk((size_t)(2 * nt * nr));
-    int64_t slots = 0;
-    for (int64_t j = 0; j < nt; ++j)
-        for (int64_t r = 0; r < nr; ++r) {
-            int64_t off = 0;
-            for (int64_t u = rs[(size_t)r]; u < rs[(size_t)r + 1]; ++u) {
+    struct Blk {
+        int32_t j, r, u0, u1;
+        int64_t L, cost;
+    };
+    std::vector<Blk> bl;
+    std::vector<int64_t> toff((size_t)cells);
+    // directory for the layout kernel: tfirst (nt + 1), then each tile's
+    // range bounds (nb + nt), then the block of each (tile, range) (nb)
+    std::vector<int32_t> tfirst((size_t)nt + 1, 0), rstart;
+    for (int64_t j = 0; j < nt; ++j) {
+        tfirst[(size_t)j] = (int32_t)bl.size();
+        const std::vector<int32_t>& c = rs[(size_t)j];
+        rstart.insert(rstart.end(), c.begin(), c.end());
+        for (size_t r = 0; r + 1 < c.size(); ++r) {
+            int64_t off = 0, cost = 0;
+            for (int64_t u = c[r]; u < c[r + 1]; ++u) {
+                const int64_t l = len[(size_t)(j * n + u)];
                 toff[(size_t)(j * n + u)] = off;
-                off += (len[(size_t)(j * n + u)] + kStep - 1) & ~int64_t(kStep - 1);  // padded
+                off += (l + kStep - 1) & ~int64_t(kStep - 1);  // padded
+                cost += row_cost(l);
             }
-            blk[(size_t)(2 * (j * nr + r))] = slots;
-            blk[(size_t)(2 * (j * nr + r) + 1)] = off;
-            slots += (int64_t)kBThreads * lane_len((int32_t)off);
+            bl.push_back({(int32_t)j, (int32_t)r, c[r], c[r + 1], off, cost});
         }
+    }
+    tfirst[(size_t)nt] = (int32_t)bl.size();
+    const int64_t nb = (int64_t)bl.size();
+    std::vector<int32_t> order((size_t)nb);
+    for (int64_t b = 0; b < nb; ++b) order[(size_t)b] = (int32_t)b;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return bl[(size_t)x].cost > bl[(size_t)y].cost; });
+    std::vector<int64_t> blk(2 * (size_t)nb), wbb(wb ? 2 * (size_t)nb : 0);
+    std::vector<int32_t> bdesc(4 * (size_t)nb), rblock((size_t)nb);
+    int64_t slots = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        const Blk& x = bl[(size_t)order[(size_t)b]];
+        blk[2 * (size_t)b] = slots;
+        blk[2 * (size_t)b + 1] = x.L;
+        slots += (int64_t)kBThreads * lane_len((int32_t)x.L);
+        bdesc[4 * (size_t)b] = x.u0;
+        bdesc[4 * (size_t)b + 1] = x.u1;
+        bdesc[4 * (size_t)b + 2] = x.j;
+        bdesc[4 * (size_t)b + 3] = 0;
+        rblock[(size_t)(tfirst[(size_t)x.j] + x.r)] = (int32_t)b;
+        if (wb) {
+            wbb[2 * (size_t)b] = (*wb)[2 * (size_t)x.r];
+            wbb[2 * (size_t)b + 1] = (*wb)[2 * (size_t)x.r + 1];
+        }
+    }
+    std::vector<int32_t> dir(tfirst);
+    dir.insert(dir.end(), rstart.begin(), rstart.end());
+    dir.insert(dir.end(), rblock.begin(), rblock.end());
     const int64_t tk_len = slots + kStep;
     gila_status s;
     if ((s = ensure((void**)&P.toff, &P.toff_cap, sizeof(int64_t) * (size_t)cells)) != GILA_OK)
         return s;
     if ((s = ensure((void**)&P.blk, &P.blk_cap, sizeof(int64_t) * blk.size())) != GILA_OK) return s;
-    if ((s = ensure((void**)&P.range_start, &P.range_cap, sizeof(int32_t) * rs.size())) != GILA_OK)
+    if ((s = ensure((void**)&P.bdesc, &P.bdesc_cap, sizeof(int32_t) * bdesc.size())) != GILA_OK)
+        return s;
+    if ((s = ensure((void**)&P.rdir, &P.rdir_cap, sizeof(int32_t) * dir.size())) != GILA_OK)
         return s;
     if ((s = ensure((void**)&P.tk, &P.tk_cap, sizeof(uint16_t) * (size_t)tk_len)) != GILA_OK)
         return s;
     if (wb) {
-        if ((s = ensure((void**)&P.wtile, &P.wtile_cap, sizeof(int64_t) * wb->size())) != GILA_OK)
+        if ((s = ensure((void**)&P.wtile, &P.wtile_cap, sizeof(int64_t) * wbb.size())) != GILA_OK)
             return s;
-        GILA_CUDA(cudaMemcpyAsync(P.wtile, wb->data(), sizeof(int64_t) * wb->size(),
+        GILA_CUDA(cudaMemcpyAsync(P.wtile, wbb.data(), sizeof(int64_t) * wbb.size(),
                                   cudaMemcpyHostToDevice, g->stream));
     } else if ((s = ensure(&P.part, &P.part_cap, 2 * esz * (size_t)cells)) != GILA_OK) {
         return s;
@@ -1318,25 +1454,30 @@ gila_status build_layout(gila_graph* g, size_t esz, TilePlan& P, int64_t nt, int
                               g->stream));
     GILA_CUDA(cudaMemcpyAsync(P.blk, blk.data(), sizeof(int64_t) * blk.size(),
                               cudaMemcpyHostToDevice, g->stream));
-    GILA_CUDA(cudaMemcpyAsync(P.range_start, rs.data(), sizeof(int32_t) * rs.size(),
+    GILA_CUDA(cudaMemcpyAsync(P.bdesc, bdesc.data(), sizeof(int32_t) * bdesc.size(),
+                              cudaMemcpyHostToDevice, g->stream));
+    GILA_CUDA(cudaMemcpyAsync(P.rdir, dir.data(), sizeof(int32_t) * dir.size(),
                               cudaMemcpyHostToDevice, g->stream));
     // ids ordered for conflict-free gathers, or in ascending order; the
     // slots past each share's end stay zero
     GILA_CUDA(cudaMemsetAsync(P.tk, 0, sizeof(uint16_t) * (size_t)tk_len, g->stream));
     const int64_t* wdev = wb ? P.wtile : nullptr;
+    const int32_t* d_tfirst = P.rdir;
+    const int32_t* d_rstart = P.rdir + nt + 1;
+    const int32_t* d_rblock = P.rdir + nt + 1 + nb + nt;
     const unsigned lay_blocks = (unsigned)((cells + kSpreadWarps - 1) / kSpreadWarps);
     if (g->tune.bank_spread >= 0 && esz == 8)
         block_layout_kernel<16, true><<<lay_blocks, kSpreadWarps * 32, 0, g->stream>>>(
-            n, g->krow, g->kcol, (int)nt, (int)tv, wdev, P.toff, P.blk, P.range_start, (int)nr,
-            P.tk);
+            n, g->krow, g->kcol, (int)nt, (int)tv, wdev, P.toff, P.blk, d_tfirst, d_rstart,
+            d_rblock, P.tk);
     else if (g->tune.bank_spread >= 0)
         block_layout_kernel<8, true><<<lay_blocks, kSpreadWarps * 32, 0, g->stream>>>(
-            n, g->krow, g->kcol, (int)nt, (int)tv, wdev, P.toff, P.blk, P.range_start, (int)nr,
-            P.tk);
+            n, g->krow, g->kcol, (int)nt, (int)tv, wdev, P.toff, P.blk, d_tfirst, d_rstart,
+            d_rblock, P.tk);
     else
         block_layout_kernel<16, false><<<lay_blocks, kSpreadWarps * 32, 0, g->stream>>>(
-            n, g->krow, g->kcol, (int)nt, (int)tv, wdev, P.toff, P.blk, P.range_start, (int)nr,
-            P.tk);
+            n, g->krow, g->kcol, (int)nt, (int)tv, wdev, P.toff, P.blk, d_tfirst, d_rstart,
+            d_rblock, P.tk);
     count_launch();
     GILA_CUDA(cudaGetLastError());
     if (!wb) {
@@ -1346,7 +1487,7 @@ gila_status build_layout(gila_graph* g, size_t esz, TilePlan& P, int64_t nt, int
     // the host vectors above go out of scope
     GILA_CUDA(cudaStreamSynchronize(g->stream));
     P.nt = (int32_t)nt;
-    P.nr = (int32_t)nr;
+    P.nb = (int32_t)nb;
     P.use = true;
     return GILA_OK;
 }
@@ -1383,7 +1524,7 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
             gila_status s = plan_window(g, esz, P, &fits, len, rs, wb, &wmax, &rmax);
             if (s != GILA_OK) return s;
             if (fits) {
-                if ((s = build_layout(g, esz, P, 1, 0, len, rs, &wb)) != GILA_OK) return s;
+                if ((s = build_layout(g, esz, P, 1, 0, len, {rs}, &wb)) != GILA_OK) return s;
                 P.window = true;
                 P.tv = (int32_t)wmax;
                 P.rmax = (int32_t)rmax;
@@ -1409,17 +1550,15 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
     GILA_CUDA(cudaMemcpyAsync(len.data(), P.len, sizeof(int64_t) * cells, cudaMemcpyDeviceToHost,
                               g->stream));
     GILA_CUDA(cudaStreamSynchronize(g->stream));
-    // row ranges of about equal cost (entries + a per-row term), at most
-    // kMaxRows rows each, enough of them for several CTAs per SM in total
-    std::vector<int64_t> cost((size_t)n, 0);
-    int64_t total = 0;
-    for (int64_t u = 0; u < n; ++u) {
-        int64_t c = 8;
-        for (int64_t j = 0; j < nt; ++j) c += len[(size_t)(j * n + u)];
-        cost[(size_t)u] = c;
-        total += c;
+    // each tile's row ranges: blocks of about equal cost (padded entries +
+    // a per-row term), at most kMaxRows rows each, about ctas_per_sm per SM
+    std::vector<int64_t> pre((size_t)(nt * (n + 1)), 0);
+    for (int64_t j = 0; j < nt; ++j) {
+        int64_t* pj = pre.data() + j * (n + 1);
+        for (int64_t u = 0; u < n; ++u) pj[u + 1] = pj[u] + row_cost(len[(size_t)(j * n + u)]);
     }
-    const std::vector<int32_t> rs = partition_rows(cost, total, ranges_target(g, nt, false));
+    const std::vector<std::vector<int32_t>> rs =
+        partition_blocks(pre, n, nt, blocks_target(g, false));
     if ((s = build_layout(g, esz, P, nt, tv, len, rs, nullptr)) != GILA_OK) return s;
     P.tv = (int32_t)tv;
     P.rmax = kMaxRows;
@@ -1462,11 +1601,10 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
     B.tk = P.tk;
     B.toff = P.toff;
     B.blk = P.blk;
-    B.range_start = P.range_start;
+    B.bdesc = reinterpret_cast<const int4*>(P.bdesc);
     B.n = g->n;
     B.nt = P.nt;
     B.tv = P.tv;
-    B.nr = P.nr;
     B.q = prm->q;
     B.pos = pos_in;
     B.part = P.part;
@@ -1482,11 +1620,6 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
     B.p = prm->p;
     B.pos_out = pos_out;
     B.disp_out = disp_out;
-    // FP32 steps: warp-uniform where rows change every few steps (measured:
-    // BA k = 3, segments of ~600 entries, 0.186 -> 0.172 ms; the mesh's
-    // windows 0.112 -> 0.105 ms), divergent where segments are long
-    // (Chung-Lu, ~4,500 entries: 4.97 ms divergent, 5.23 ms uniform)
-    B.converge = g->nnz_khop < (int64_t)kConvergeSeg * g->n * P.nt;
     CombineArgs C;
     C.row = g->row;
     C.col = g->col;
@@ -1502,7 +1635,7 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
     C.hubs = P.hubs;
     C.nhub = P.nhub;
     C.nreg = (int32_t)((g->n * kCombineLanes + kCombineThreads - 1) / kCombineThreads);
-    const int grid = P.nt * P.nr;
+    const int grid = P.nb;
     const size_t smem = P.window ? window_smem(P.tv, P.rmax, esz)
                                  : (size_t)(P.tv + 1) * esz + (size_t)(kMaxRows + 1) * 4;
     const bool fr = (prm->p == 2 && prm->q == 1);
@@ -1534,19 +1667,18 @@ gila_status blocked_khop_metric(gila_graph* g, const gila_params* prm, const voi
     const TilePlan& P = g->tplan[0];
     if (is_f64(prm->precision) || !P.ready || !P.use || g->n == 0 || g->wt64) return GILA_OK;
     if (((uintptr_t)pos & 15) != 0) return GILA_OK;
-    const int grid = P.nt * P.nr;
+    const int grid = P.nb;
     gila_status s = ensure((void**)&g->red, &g->red_cap, sizeof(double) * ((size_t)grid + 8));
     if (s != GILA_OK) return s;
     MetricArgs M;
     M.krow = g->krow;
     M.len = P.window ? nullptr : P.len;
     M.kcol = g->kcol;
-    M.range_start = P.range_start;
+    M.bdesc = reinterpret_cast<const int4*>(P.bdesc);
     M.wbase = P.window ? P.wtile : nullptr;
     M.n = g->n;
     M.nt = P.nt;
     M.tv = P.tv;
-    M.nr = P.nr;
     M.tcap = P.tv;
     M.d = prm->d;
     M.q = prm->q;

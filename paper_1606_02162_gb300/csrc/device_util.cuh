@@ -105,6 +105,18 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
+// L2 prefetch of the 16-byte aligned part of [p, p + bytes) (the start
+// rounded up, the end rounded down, so nothing outside the range is
+// touched), in chunks of 16 KiB.
+__device__ __forceinline__ void prefetch_l2_range(const void* p, size_t bytes)
+{
+    const uintptr_t s = ((uintptr_t)p + 15) & ~uintptr_t(15);
+    const uintptr_t e = ((uintptr_t)p + bytes) & ~uintptr_t(15);
+    for (uintptr_t a = s; a < e; a += 16384)
+        bulk_prefetch_l2(reinterpret_cast<const void*>(a),
+                         (uint32_t)((e - a < 16384) ? e - a : 16384));
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns()
 {
     uint64_t t;

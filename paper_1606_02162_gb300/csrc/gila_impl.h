@@ -92,11 +92,13 @@ struct Bins {
 struct TilePlan {
     bool ready = false;  // decided for the current k-hop lists
     bool use = false;    // the blocked path serves this graph
-    int32_t nt = 0, tv = 0, nr = 0;  // tiles, tile (or largest window) size, row ranges
+    int32_t nt = 0, tv = 0, nb = 0;  // tiles, tile (or largest window) size, blocks (CTAs)
     int32_t rmax = 0;                // most rows of a range (window mode: cells per CTA)
-    int32_t* range_start = nullptr;  // nr + 1 row bounds
-    size_t range_cap = 0;
-    int64_t* blk = nullptr;          // 2 nt nr: start and length of block (tile j, range r)
+    int32_t* bdesc = nullptr;        // 4 nb: first row, end row and tile of block b, 0
+    size_t bdesc_cap = 0;
+    int32_t* rdir = nullptr;         // per tile its row ranges and their blocks (layout scratch)
+    size_t rdir_cap = 0;
+    int64_t* blk = nullptr;          // 2 nb: start in tk and entry count of block b
     size_t blk_cap = 0;
     int64_t* toff = nullptr;         // nt n: start of (tile j, row u) in tk
     size_t toff_cap = 0;
@@ -112,7 +114,7 @@ struct TilePlan {
     // window mode: one window of positions per row range, covering every id
     // its rows touch; rows are finished by their range's CTA
     bool window = false;
-    int64_t* wtile = nullptr;        // 2 nr: first id and length of range r's window
+    int64_t* wtile = nullptr;        // 2 nb: first id and length of block b's window
     size_t wtile_cap = 0;
     int32_t* rowspan = nullptr;      // 2 n: first and last id of each row (plan scratch)
     size_t rowspan_cap = 0;
