@@ -131,6 +131,10 @@ typedef struct gila_tuning {
                               a tile so that the lanes of one shared-memory gather read
                               distinct banks where the entries allow; -1 keeps ascending
                               id order */
+    int32_t step_schedule; /* blocked path, FP32: 0 or 1 (default) issues each step's eight
+                              terms once for the whole warp, only the closing of rows
+                              diverging; -1 issues them apart for the lanes that close a
+                              row in the step */
 } gila_tuning;
 
 typedef struct gila_graph gila_graph;

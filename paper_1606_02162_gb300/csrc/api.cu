@@ -424,6 +424,8 @@ gila_status gila_graph_tune(gila_graph* g, const gila_tuning* t)
         return fail(GILA_EINVAL, "tuning values must be >= 0");
     if (t->bank_spread < -1 || t->bank_spread > 1)
         return fail(GILA_EINVAL, "bank_spread must be -1, 0 or 1");
+    if (t->step_schedule < -1 || t->step_schedule > 1)
+        return fail(GILA_EINVAL, "step_schedule must be -1, 0 or 1");
     BinConfig c;  // defaults
     if (t->small_max) c.small_max = t->small_max;
     if (t->warp_max) c.warp_max = t->warp_max;
@@ -451,6 +453,7 @@ gila_status gila_graph_get_tuning(const gila_graph* g, gila_tuning* out)
                            ? g->tune.ctas_per_sm
                            : (int32_t)default_ctas_per_sm(g->nnz_khop, g->tplan[0].window);
     out->bank_spread = g->tune.bank_spread >= 0 ? 1 : -1;
+    out->step_schedule = g->tune.step_schedule >= 0 ? 1 : -1;
     out->small_max = g->bins.cfg.small_max;
     out->warp_max = g->bins.cfg.warp_max;
     out->block_max = g->bins.cfg.block_max;

@@ -87,6 +87,7 @@ struct BlockedArgs {
     int p;
     void* pos_out;
     void* disp_out;
+    int uniform;               // FP32 steps taken warp-uniformly (tuning step_schedule >= 0)
 };
 
 template <class T, bool COMP>
@@ -388,17 +389,22 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                         while (p >= re) close_row();
                         eight(c);
                     }
-                } else {
-                    // FP32: only the closing of rows diverges, the terms are
-                    // issued once for the warp (measured against issuing the
-                    // step's terms separately for the lanes that close a row:
-                    // Chung-Lu n = 250,000, k = 3, 4.88 vs 4.96 ms per launch;
-                    // Barabasi-Albert n = 100,000, k = 3, 0.172 vs 0.186)
+                } else if (A.uniform) {
+                    // FP32, default: only the closing of rows diverges, the
+                    // step's terms are issued once for the warp
                     if (p >= lim && p < b) {
                         while (p >= re) close_row();
                         lim = (re < b) ? re : b;
                     }
                     if (p < b) eight(c);
+                } else if (p < lim) {
+                    // FP32, tuning step_schedule = -1: lanes that close a row
+                    // in this step issue its terms apart from the others
+                    eight(c);
+                } else if (p < b) {
+                    while (p >= re) close_row();
+                    lim = (re < b) ? re : b;
+                    eight(c);
                 }
                 p += kStep;
             }
@@ -674,6 +680,27 @@ constexpr int kCombineLanes = 4;
 constexpr int kCombineThreads = 256;
 constexpr int kHubDeg = 64;
 
+// Entries [s, e) of ids, lane gl of a group of G taking s + gl, s + gl + G,
+// ... as row_sum_rel does (same terms, same order of additions), with the
+// ids of U consecutive turns loaded before their terms, so that a lane has U
+// id loads and then U position gathers in flight instead of one of each.
+template <int U, class F, class A>
+__device__ __forceinline__ void row_sum_batched(const uint32_t* __restrict__ ids, int64_t s,
+                                                int64_t e, int gl, int G, const F& f, A& a)
+{
+    const uint32_t* p = ids + s;
+    const int len = (int)(e - s);
+    int j = gl;
+    for (; j + (U - 1) * G < len; j += U * G) {
+        uint32_t v[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) v[k] = ld_id(p + j + k * G);
+#pragma unroll
+        for (int k = 0; k < U; ++k) f(v[k], a);
+    }
+    for (; j < len; j += G) f(ld_id(p + j), a);
+}
+
 template <class T, bool COMP>
 __device__ __forceinline__ void add_cell(const void* part, int64_t n, int j, int64_t u,
                                          Acc<T, COMP>& s)
@@ -723,8 +750,8 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(const CombineA
             add_cell<T, COMP>(A.part, A.n, jj, u, rep);
         att.xu = pu.x;
         att.yu = pu.y;
-        row_sum_rel(reinterpret_cast<const uint32_t*>(A.col), A.row[u], A.row[u + 1],
-                    (int)threadIdx.x, kCombineThreads, att, at);
+        row_sum_batched<4>(reinterpret_cast<const uint32_t*>(A.col), A.row[u], A.row[u + 1],
+                           (int)threadIdx.x, kCombineThreads, att, at);
         rep.group_reduce(32);
         at.group_reduce(32);
         if (lane == 0) {
@@ -766,7 +793,8 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(const CombineA
         pu = pos[u];
         att.xu = pu.x;
         att.yu = pu.y;
-        row_sum_rel(reinterpret_cast<const uint32_t*>(A.col), rb, re, gl, kCombineLanes, att, at);
+        row_sum_batched<2>(reinterpret_cast<const uint32_t*>(A.col), rb, re, gl, kCombineLanes, att,
+                           at);
     }
     rep.group_reduce(kCombineLanes);
     at.group_reduce(kCombineLanes);
@@ -1620,6 +1648,12 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
     B.p = prm->p;
     B.pos_out = pos_out;
     B.disp_out = disp_out;
+    // FP32 steps warp-uniform by default (measured against the divergent
+    // schedule: Chung-Lu n = 250,000, k = 3, 4.88 vs 4.96 ms per launch;
+    // Barabasi-Albert n = 100,000, k = 3, 0.172 vs 0.186 ms). The kernel
+    // keeps both schedules: with the divergent one compiled beside it the
+    // uniform schedule itself measured faster (4.88 vs 5.08 ms on Chung-Lu)
+    B.uniform = g->tune.step_schedule >= 0 ? 1 : 0;
     CombineArgs C;
     C.row = g->row;
     C.col = g->col;

@@ -144,7 +144,7 @@ struct gila_graph {
     gila::KhopScratch ks;
     gila::Bins bins;
     gila::TilePlan tplan[2];
-    gila_tuning tune = {-1, 0, 0, 0, 0, 0, 0, 0, 0};
+    gila_tuning tune = {-1, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     // placement buffers for the run calls
     void* pos[2] = {nullptr, nullptr};
     size_t pos_cap[2] = {0, 0};

@@ -59,7 +59,7 @@ class gila_tuning(ctypes.Structure):
                 ("min_segment", ctypes.c_int32), ("small_max", ctypes.c_int32),
                 ("warp_max", ctypes.c_int32), ("block_max", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("bank_spread", ctypes.c_int32)]
+                ("bank_spread", ctypes.c_int32), ("step_schedule", ctypes.c_int32)]
 
 
 class gila_batch_tuning(ctypes.Structure):
@@ -249,10 +249,11 @@ def gila_graph_info(g) -> dict:
 
 
 def gila_graph_tune(g, tiled=-1, tile_vertices=0, min_segment=0, small_max=0, warp_max=0,
-                    block_max=0, chunk=0, ctas_per_sm=0, bank_spread=0) -> None:
+                    block_max=0, chunk=0, ctas_per_sm=0, bank_spread=0,
+                    step_schedule=0) -> None:
     t = gila_tuning(int(tiled), int(tile_vertices), int(min_segment), int(small_max),
                     int(warp_max), int(block_max), int(chunk), int(ctas_per_sm),
-                    int(bank_spread))
+                    int(bank_spread), int(step_schedule))
     _check(load().gila_graph_tune(g, ctypes.byref(t)))
 
 

@@ -155,6 +155,7 @@ TUNINGS = [
     ("tiled", dict(tiled=1)),
     ("tiled_small_tiles", dict(tiled=1, tile_vertices=1000)),
     ("tiled_small_tiles_ascending", dict(tiled=1, tile_vertices=1000, bank_spread=-1)),
+    ("tiled_divergent_steps", dict(tiled=1, tile_vertices=1000, step_schedule=-1)),
     ("untiled_small_classes", dict(tiled=0, small_max=4, warp_max=64, block_max=512, chunk=300)),
 ]
 
