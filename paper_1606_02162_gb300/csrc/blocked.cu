@@ -329,8 +329,7 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
         const int nsteps = m8 / kStep;  // the same for every thread of the block
         uint4 ring[kRing];
 #pragma unroll
-        for (int st = 0; st < kRing; ++st)
-            ring[st] = (st < nsteps) ? ld_ids4(ids4 + 32 * st) : make_uint4(0, 0, 0, 0);
+        for (int st = 0; st < kRing; ++st) ring[st] = ld_ids4(ids4 + 32 * st);
         // the warp's ids kPrefetch steps ahead of the ring are pulled into L2
         // by one lane, kRing steps (kRing x 512 bytes) at a time
         const uint4* warp_ids = ids4 - lane;
@@ -369,46 +368,56 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                 f(c.w >> 16, acc);
             }
         };
-        for (int k0 = 0; k0 < nsteps; k0 += kRing) {
+        // one step: its eight terms, after closing the rows that end before
+        // it; the ring register refilled kRing steps ahead (the id array has
+        // kRing steps of slack at its end, so the refill needs no test)
+        auto step = [&](uint4& r, int k) {
+            const uint4 c = r;
+            r = ld_ids4(ids4 + 32 * (k + kRing));
+            if (sizeof(T) == 8) {
+                // FP64 (costly terms): the warp takes every step together
+                // and only the closing of rows diverges, so no term is
+                // issued twice (BA k = 3: 5.15 ms; 7.08 ms as for FP32)
+                if (p < b) {
+                    while (p >= re) close_row();
+                    eight(c);
+                }
+            } else if (A.uniform) {
+                // FP32, default: only the closing of rows diverges, the
+                // step's terms are issued once for the warp; steps past the
+                // share hold the far slot's id and add zeros
+                if (p >= lim) {
+                    if (p < b) {
+                        while (p >= re) close_row();
+                        lim = (re < b) ? re : b;
+                    } else {
+                        lim = INT32_MAX;
+                    }
+                }
+                eight(c);
+            } else if (p < lim) {
+                // FP32, tuning step_schedule = -1: lanes that close a row
+                // in this step issue its terms apart from the others
+                eight(c);
+            } else if (p < b) {
+                while (p >= re) close_row();
+                lim = (re < b) ? re : b;
+                eight(c);
+            }
+            p += kStep;
+        };
+        int k0 = 0;
+        for (; k0 + kRing <= nsteps; k0 += kRing) {
             const int kp = k0 + kPrefetch + kRing;
             if (lane == 0 && kp < nsteps)
                 bulk_prefetch_l2(warp_ids + 32 * kp,
                                  (uint32_t)(512 * ((nsteps - kp < kRing) ? nsteps - kp : kRing)));
 #pragma unroll
-            for (int st = 0; st < kRing; ++st) {
-                const int k = k0 + st;
-                if (k >= nsteps) break;  // uniform
-                const uint4 c = ring[st];
-                ring[st] = (k + kRing < nsteps) ? ld_ids4(ids4 + 32 * (k + kRing))
-                                                : make_uint4(0, 0, 0, 0);
-                if (sizeof(T) == 8) {
-                    // FP64 (costly terms): the warp takes every step together
-                    // and only the closing of rows diverges, so no term is
-                    // issued twice (BA k = 3: 5.15 ms; 7.08 ms as for FP32)
-                    if (p < b) {
-                        while (p >= re) close_row();
-                        eight(c);
-                    }
-                } else if (A.uniform) {
-                    // FP32, default: only the closing of rows diverges, the
-                    // step's terms are issued once for the warp
-                    if (p >= lim && p < b) {
-                        while (p >= re) close_row();
-                        lim = (re < b) ? re : b;
-                    }
-                    if (p < b) eight(c);
-                } else if (p < lim) {
-                    // FP32, tuning step_schedule = -1: lanes that close a row
-                    // in this step issue its terms apart from the others
-                    eight(c);
-                } else if (p < b) {
-                    while (p >= re) close_row();
-                    lim = (re < b) ? re : b;
-                    eight(c);
-                }
-                p += kStep;
-            }
+            for (int st = 0; st < kRing; ++st) step(ring[st], k0 + st);
         }
+#pragma unroll
+        for (int st = 0; st < kRing - 1; ++st)
+            if (k0 + st < nsteps) step(ring[st], k0 + st);
         const bool has_b = !in_first;  // the share ends in a later row than it began
         if (in_first) first = acc;
         const int orow = has_b ? ri : ra;  // the row the share ends in
@@ -852,6 +861,25 @@ __global__ void seglen_kernel(int64_t n, const int64_t* __restrict__ krow,
 // (stable), deal them 32 entries at a time.
 constexpr int kSpreadWarps = 4;
 constexpr int kSpreadChunk = 1024;
+
+// Every slot of block b's share storage set to the block's padding id (its
+// far slot) before the layout kernel writes the entries: the slots past
+// each thread's share keep it, so that the FP32 kernel takes a thread's
+// last steps like any other (their terms are exact zeros). Block starts are
+// multiples of 8 slots: whole 16-byte stores.
+__global__ void pad_fill_kernel(uint16_t* __restrict__ tk, const int64_t* __restrict__ blk,
+                                const int64_t* __restrict__ wbase, int tv, int64_t nb)
+{
+    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int64_t bsp = blk[2 * b];
+        const int64_t words = (int64_t)kBThreads * lane_len((int32_t)blk[2 * b + 1]) / 8;
+        const uint32_t pad = wbase ? (uint32_t)wbase[2 * b + 1] : (uint32_t)tv;
+        const uint32_t pp = pad | (pad << 16);
+        const uint4 v = make_uint4(pp, pp, pp, pp);
+        uint4* dst = reinterpret_cast<uint4*>(tk + bsp);
+        for (int64_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = v;
+    }
+}
 
 template <int G, bool SPREAD>
 __global__ void __launch_bounds__(kSpreadWarps * 32) block_layout_kernel(
@@ -1459,7 +1487,7 @@ gila_status build_layout(gila_graph* g, size_t esz, TilePlan& P, int64_t nt, int
     std::vector<int32_t> dir(tfirst);
     dir.insert(dir.end(), rstart.begin(), rstart.end());
     dir.insert(dir.end(), rblock.begin(), rblock.end());
-    const int64_t tk_len = slots + kStep;
+    const int64_t tk_len = slots + kStep + 256 * 4;  // slack: the kernel's ring reads ahead
     gila_status s;
     if ((s = ensure((void**)&P.toff, &P.toff_cap, sizeof(int64_t) * (size_t)cells)) != GILA_OK)
         return s;
@@ -1486,10 +1514,18 @@ gila_status build_layout(gila_graph* g, size_t esz, TilePlan& P, int64_t nt, int
                               cudaMemcpyHostToDevice, g->stream));
     GILA_CUDA(cudaMemcpyAsync(P.rdir, dir.data(), sizeof(int32_t) * dir.size(),
                               cudaMemcpyHostToDevice, g->stream));
-    // ids ordered for conflict-free gathers, or in ascending order; the
-    // slots past each share's end stay zero
-    GILA_CUDA(cudaMemsetAsync(P.tk, 0, sizeof(uint16_t) * (size_t)tk_len, g->stream));
+    // every block's slots set to its padding id, then the ids ordered for
+    // conflict-free gathers, or in ascending order; the slack after the
+    // last block (read ahead by the kernel's ring, never used) is zeroed
     const int64_t* wdev = wb ? P.wtile : nullptr;
+    GILA_CUDA(cudaMemsetAsync(P.tk + slots, 0, sizeof(uint16_t) * (size_t)(tk_len - slots),
+                              g->stream));
+    if (nb > 0) {
+        pad_fill_kernel<<<(unsigned)std::min<int64_t>(nb, 4096), 256, 0, g->stream>>>(
+            P.tk, P.blk, wdev, (int)tv, nb);
+        count_launch();
+        GILA_CUDA(cudaGetLastError());
+    }
     const int32_t* d_tfirst = P.rdir;
     const int32_t* d_rstart = P.rdir + nt + 1;
     const int32_t* d_rblock = P.rdir + nt + 1 + nb + nt;
