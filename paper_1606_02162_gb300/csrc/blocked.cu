@@ -303,10 +303,21 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
         f.xu = xr.x;
         f.yu = xr.y;
         Acc<T, COMP> acc, first;
+        // compensated mode: the terms of the steps since the last merge,
+        // summed plainly; added to acc with its error term at the end of
+        // each ring of steps and before a row closes
+        Acc<T, false> pend;
+        auto merge_pending = [&]() {
+            if (COMP) {
+                add_compensated(acc, pend.sx, pend.sy);
+                pend = Acc<T, false>();
+            }
+        };
         bool in_first = true;
         // the current row is complete: the first row's sum is kept for the
         // warp's scan; a later row lies wholly in [a, b) and is stored
         auto close_row = [&]() {
+            merge_pending();
             if (in_first) {
                 first = acc;
                 in_first = false;
@@ -345,18 +356,15 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
         int32_t p = a;
         auto eight = [&](const uint4 c) {
             if (COMP) {
-                // compensated mode: the step's eight terms summed plainly,
-                // the partial added with its error term
-                Acc<T, false> s8;
-                f(c.x & 0xffffu, s8);
-                f(c.x >> 16, s8);
-                f(c.y & 0xffffu, s8);
-                f(c.y >> 16, s8);
-                f(c.z & 0xffffu, s8);
-                f(c.z >> 16, s8);
-                f(c.w & 0xffffu, s8);
-                f(c.w >> 16, s8);
-                add_compensated(acc, s8.sx, s8.sy);
+                // compensated mode: into the plain pending sum
+                f(c.x & 0xffffu, pend);
+                f(c.x >> 16, pend);
+                f(c.y & 0xffffu, pend);
+                f(c.y >> 16, pend);
+                f(c.z & 0xffffu, pend);
+                f(c.z >> 16, pend);
+                f(c.w & 0xffffu, pend);
+                f(c.w >> 16, pend);
             } else {
                 f(c.x & 0xffffu, acc);
                 f(c.x >> 16, acc);
@@ -414,10 +422,12 @@ __global__ void __launch_bounds__(kBThreads, 1) blocked_kernel(const BlockedArgs
                                  (uint32_t)(512 * ((nsteps - kp < kRing) ? nsteps - kp : kRing)));
 #pragma unroll
             for (int st = 0; st < kRing; ++st) step(ring[st], k0 + st);
+            merge_pending();
         }
 #pragma unroll
         for (int st = 0; st < kRing - 1; ++st)
             if (k0 + st < nsteps) step(ring[st], k0 + st);
+        merge_pending();
         const bool has_b = !in_first;  // the share ends in a later row than it began
         if (in_first) first = acc;
         const int orow = has_b ? ri : ra;  // the row the share ends in
