@@ -783,7 +783,7 @@ def secondary_record(r):
     return rec
 
 
-SECONDARY = ("mesh1000_k3", "ba1m_k2", "ba100k_k3", "ba100k_k2")
+SECONDARY = ("mesh1000_k3", "ba1m_k2", "ba1m_k3", "ba100k_k3", "ba100k_k2")
 
 
 def main():

@@ -41,6 +41,8 @@ constexpr int kBWarps = kBThreads / 32;
 static_assert(kBWarps == 32, "the slot flush gives lane w of warp 0 the slots of warp w");
 constexpr int kSmemCap = 227 * 1024;
 constexpr int kMaxRows = 4096;  // rows per range (directory in shared memory)
+constexpr int kMaxRowsTiles = 16384;  // tile mode: the directory may grow to this where the
+                                      // 4096-row limit alone would exceed the CTA target
 constexpr int kTileBudget = kSmemCap - (kMaxRows + 1) * 4 - 4096;
 constexpr int64_t kMaxTile = 65534;  // tile-relative ids and the far slot's id fit 16 bits
 constexpr uint32_t kBulkChunk = 32768;      // bytes per bulk copy instruction
@@ -1264,10 +1266,10 @@ inline int64_t row_cost(int64_t len)
 }
 
 // Greedy cut of one tile's rows into ranges of cost at most cap (a range
-// takes at least one row) and at most kMaxRows rows; pre holds the prefix
+// takes at least one row) and at most max_rows rows; pre holds the prefix
 // sums of the rows' costs (n + 1 values). Returns the number of ranges,
 // stopping once it exceeds limit; fills cuts (the range bounds) if given.
-int64_t cut_rows(const int64_t* pre, int64_t n, int64_t cap, int64_t limit,
+int64_t cut_rows(const int64_t* pre, int64_t n, int64_t cap, int64_t limit, int64_t max_rows,
                  std::vector<int32_t>* cuts)
 {
     int64_t s = 0, count = 0;
@@ -1275,7 +1277,7 @@ int64_t cut_rows(const int64_t* pre, int64_t n, int64_t cap, int64_t limit,
     while (s < n) {
         // the last e with pre[e] - pre[s] <= cap, at least s + 1
         int64_t e = (int64_t)(std::upper_bound(pre + s + 1, pre + n + 1, pre[s] + cap) - pre) - 1;
-        e = std::min<int64_t>(std::max<int64_t>(e, s + 1), s + kMaxRows);
+        e = std::min<int64_t>(std::max<int64_t>(e, s + 1), s + max_rows);
         if (cuts) cuts->push_back((int32_t)e);
         if (++count > limit) return count;
         s = e;
@@ -1292,12 +1294,12 @@ int64_t cut_rows(const int64_t* pre, int64_t n, int64_t cap, int64_t limit,
 // into a second wave (Barabasi-Albert n = 100,000, k = 2: 156 CTAs on 152
 // SMs, the SMs busy 54% of the kernel's time).
 std::vector<std::vector<int32_t>> partition_blocks(const std::vector<int64_t>& pre, int64_t n,
-                                                   int64_t nt, int64_t target)
+                                                   int64_t nt, int64_t target, int64_t max_rows)
 {
     auto count = [&](int64_t cap, int64_t limit) {
         int64_t c = 0;
         for (int64_t j = 0; j < nt && c <= limit; ++j)
-            c += cut_rows(pre.data() + j * (n + 1), n, cap, limit - c, nullptr);
+            c += cut_rows(pre.data() + j * (n + 1), n, cap, limit - c, max_rows, nullptr);
         return c;
     };
     int64_t hi = 0;  // a cap every tile fits in whole: the fewest ranges
@@ -1311,7 +1313,7 @@ std::vector<std::vector<int32_t>> partition_blocks(const std::vector<int64_t>& p
     }
     std::vector<std::vector<int32_t>> rs((size_t)nt);
     for (int64_t j = 0; j < nt; ++j)
-        cut_rows(pre.data() + j * (n + 1), n, hi, INT64_MAX, &rs[(size_t)j]);
+        cut_rows(pre.data() + j * (n + 1), n, hi, INT64_MAX, max_rows, &rs[(size_t)j]);
     return rs;
 }
 
@@ -1403,7 +1405,8 @@ gila_status plan_window(gila_graph* g, size_t esz, TilePlan& P, bool* fits,
     // enough ranges for several CTAs per SM, but at least about 16 entries
     // per thread of a CTA (a small graph is one or a few ranges)
     const int64_t by_work = std::max<int64_t>(1, pre[(size_t)n] / ((int64_t)kBThreads * 16));
-    rs = partition_blocks(pre, n, 1, std::min<int64_t>(blocks_target(g, true), by_work))[0];
+    rs = partition_blocks(pre, n, 1, std::min<int64_t>(blocks_target(g, true), by_work),
+                          kMaxRows)[0];
     const int64_t nr = (int64_t)rs.size() - 1;
     wb.assign(2 * (size_t)nr, 0);
     int64_t wmax = 0, rmax = 0;
@@ -1582,11 +1585,17 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
     P.window = false;
     const int64_t n = g->n;
     if (n == 0 || g->nnz_khop == 0 || g->tune.tiled == 0) return GILA_OK;
-    int64_t tv_max = kTileBudget / (int64_t)esz - 1;  // one slot for the padding's position
-    if (g->tune.tile_vertices > 0) tv_max = std::min<int64_t>(tv_max, g->tune.tile_vertices);
-    tv_max = std::max<int64_t>(2, std::min<int64_t>(tv_max, kMaxTile) & ~int64_t(1));
-    const int64_t nt = (n + tv_max - 1) / tv_max;
-    const int64_t tv = std::min<int64_t>(tv_max, (((n + nt - 1) / nt) + 1) & ~int64_t(1));
+    // tiles for a row directory of rmax entries: positions per tile (one
+    // slot for the padding's position) and the number of tiles
+    int64_t tv = 0, nt = 0;
+    auto geometry = [&](int64_t rmax) {
+        int64_t tv_max = (kSmemCap - (rmax + 1) * 4 - 4096) / (int64_t)esz - 1;
+        if (g->tune.tile_vertices > 0) tv_max = std::min<int64_t>(tv_max, g->tune.tile_vertices);
+        tv_max = std::max<int64_t>(2, std::min<int64_t>(tv_max, kMaxTile) & ~int64_t(1));
+        nt = (n + tv_max - 1) / tv_max;
+        tv = std::min<int64_t>(tv_max, (((n + nt - 1) / nt) + 1) & ~int64_t(1));
+    };
+    geometry(kMaxRows);
     const int min_seg = g->tune.min_segment;  // 0: no limit
     const double avg_seg = (double)g->nnz_khop / ((double)n * (double)nt);
     {
@@ -1619,6 +1628,19 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
     // many positions): on BA k = 3 blocked 5.14 ms vs plain 6.03 ms
     const bool tiles_pay = !(g->tune.tiled < 0 && avg_seg < min_seg);
     if (!tiles_pay || (g->tune.tiled < 0 && g->nnz_khop < kBlockedMinNnz)) return GILA_OK;
+    // many rows: where 4096-row ranges alone make more blocks than the CTA
+    // target, a larger directory (smaller tiles) gives fewer blocks, each
+    // loading its tile once; but only for segments long enough that the
+    // extra tiles add little padding (BA n = 333,334, k = 3, 323 entries a
+    // segment: 0.702 -> 0.588 ms per iteration with 8192-row ranges; k = 2,
+    // 12 entries: 0.148 -> 0.170 ms, so it keeps 4096)
+    int64_t rmax = kMaxRows;
+    const int64_t target = blocks_target(g, false);
+    while (rmax < kMaxRowsTiles && (n + rmax - 1) / rmax * nt > target &&
+           (double)g->nnz_khop >= 64.0 * (double)n * (double)nt) {
+        rmax *= 2;
+        geometry(rmax);
+    }
     const int64_t cells = n * nt;
     gila_status s = ensure((void**)&P.len, &P.len_cap, sizeof(int64_t) * (size_t)cells);
     if (s != GILA_OK) return s;
@@ -1631,17 +1653,16 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
                               g->stream));
     GILA_CUDA(cudaStreamSynchronize(g->stream));
     // each tile's row ranges: blocks of about equal cost (padded entries +
-    // a per-row term), at most kMaxRows rows each, about ctas_per_sm per SM
+    // a per-row term), at most rmax rows each, about ctas_per_sm per SM
     std::vector<int64_t> pre((size_t)(nt * (n + 1)), 0);
     for (int64_t j = 0; j < nt; ++j) {
         int64_t* pj = pre.data() + j * (n + 1);
         for (int64_t u = 0; u < n; ++u) pj[u + 1] = pj[u] + row_cost(len[(size_t)(j * n + u)]);
     }
-    const std::vector<std::vector<int32_t>> rs =
-        partition_blocks(pre, n, nt, blocks_target(g, false));
+    const std::vector<std::vector<int32_t>> rs = partition_blocks(pre, n, nt, target, rmax);
     if ((s = build_layout(g, esz, P, nt, tv, len, rs, nullptr)) != GILA_OK) return s;
     P.tv = (int32_t)tv;
-    P.rmax = kMaxRows;
+    P.rmax = (int32_t)rmax;
     return GILA_OK;
 }
 
@@ -1723,7 +1744,7 @@ gila_status launch_blocked(gila_graph* g, const gila_params* prm, double t, cons
     C.nreg = (int32_t)((g->n * kCombineLanes + kCombineThreads - 1) / kCombineThreads);
     const int grid = P.nb;
     const size_t smem = P.window ? window_smem(P.tv, P.rmax, esz)
-                                 : (size_t)(P.tv + 1) * esz + (size_t)(kMaxRows + 1) * 4;
+                                 : (size_t)(P.tv + 1) * esz + (size_t)(P.rmax + 1) * 4;
     const bool fr = (prm->p == 2 && prm->q == 1);
     const bool w = P.window;
     cudaError_t e;
