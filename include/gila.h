@@ -125,7 +125,7 @@ typedef struct gila_tuning {
     int32_t chunk;         /* entries per chunk of a chunked row (32768) */
     int32_t ctas_per_sm;   /* blocked path: each tile's rows are cut into ranges so that the
                               grid holds at most about this many CTAs per SM, all of about
-                              equal cost (tiles: 1 below 10^8 k-hop entries, 4 below 2e9, 8
+                              equal cost (tiles: 1 below 10^8 k-hop entries, 3 below 2e9, 6
                               beyond; windows: 2) */
     int32_t bank_spread;   /* blocked path: 0 or 1 (default on) orders each row's entries of
                               a tile so that the lanes of one shared-memory gather read

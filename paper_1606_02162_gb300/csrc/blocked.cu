@@ -41,8 +41,8 @@ constexpr int kBWarps = kBThreads / 32;
 static_assert(kBWarps == 32, "the slot flush gives lane w of warp 0 the slots of warp w");
 constexpr int kSmemCap = 227 * 1024;
 constexpr int kMaxRows = 4096;  // rows per range (directory in shared memory)
-constexpr int kMaxRowsTiles = 16384;  // tile mode: the directory may grow to this where the
-                                      // 4096-row limit alone would exceed the CTA target
+constexpr int kMaxRowsTiles = 8192;  // tile mode: the directory may grow to this where the
+                                     // 4096-row limit alone would exceed the CTA target
 constexpr int kTileBudget = kSmemCap - (kMaxRows + 1) * 4 - 4096;
 constexpr int64_t kMaxTile = 65534;  // tile-relative ids and the far slot's id fit 16 bits
 constexpr uint32_t kBulkChunk = 32768;      // bytes per bulk copy instruction
@@ -1317,17 +1317,19 @@ std::vector<std::vector<int32_t>> partition_blocks(const std::vector<int64_t>& p
     return rs;
 }
 
-// CTAs per SM the blocked grid aims at by default. Tiles: one wave below
-// 10^8 k-hop entries, where loading a tile per CTA is a large part of an
-// iteration (BA n = 100,000, k = 2: 0.0493 ms per iteration at 1, 0.0514 at
-// 2, 0.0646 at 4); 4 up to 2e9 entries; 8 beyond, where a CTA streams tens
-// of MB and the end of the grid waits on the slowest (Chung-Lu 1.1e10 best
-// at 8). Windows: 2 (the mesh, k = 3: 0.0888, 0.0866, 0.108 and 0.150 ms at
-// 1, 2, 4 and 8).
+// CTAs per SM the blocked grid aims at by default (blocks of equal cost,
+// costliest first). Tiles: one wave below 10^8 k-hop entries, where loading
+// a tile per CTA is a large part of an iteration (BA n = 100,000, k = 2:
+// 0.0374 ms per iteration at 1, 0.0419 at 2); 3 up to 2e9 entries (BA
+// n = 100,000, k = 3: 0.140, 0.138, 0.148, 0.157 ms per launch at 2, 3, 4,
+// 6); 6 beyond, where a CTA streams tens of MB and the end of the grid
+// waits on the slowest (Chung-Lu 1.1e10: 4.38, 4.15, 4.19, 4.19, 4.26 ms
+// at 4, 6, 8, 12, 16). Windows: 2 (the mesh, k = 3: 0.0698, 0.0680, 0.0742
+// ms at 1, 2, 3).
 int64_t default_ctas_per_sm(int64_t nnz_khop, bool window)
 {
     if (window) return 2;
-    return nnz_khop < 100000000LL ? 1 : nnz_khop < 2000000000LL ? 4 : 8;
+    return nnz_khop < 100000000LL ? 1 : nnz_khop < 2000000000LL ? 3 : 6;
 }
 
 // CTAs (blocks) the grid aims at: about ctas_per_sm per SM.
@@ -1659,7 +1661,17 @@ gila_status plan_tiles(gila_graph* g, size_t esz, TilePlan& P)
         int64_t* pj = pre.data() + j * (n + 1);
         for (int64_t u = 0; u < n; ++u) pj[u + 1] = pj[u] + row_cost(len[(size_t)(j * n + u)]);
     }
-    const std::vector<std::vector<int32_t>> rs = partition_blocks(pre, n, nt, target, rmax);
+    // the block count: at least 5% above what the row limit alone makes,
+    // so that a tile with more entries than the others (the hubs' ids) can
+    // still be cut finer, and whole waves of one CTA per SM, since blocks of
+    // equal cost end together (BA n = 333,334, k = 3: 574 row-limited blocks
+    // against a target of 456: 1.27 ms per iteration with no room, 0.63 with
+    // 631 blocks, 0.59 with 608)
+    const int64_t sms = sm_count(g->device);
+    const int64_t floor_blocks = (n + rmax - 1) / rmax * nt;
+    const int64_t want = std::max<int64_t>(target, (floor_blocks * 21 + 19) / 20);
+    const int64_t tgt = (want + sms - 1) / sms * sms;
+    const std::vector<std::vector<int32_t>> rs = partition_blocks(pre, n, nt, tgt, rmax);
     if ((s = build_layout(g, esz, P, nt, tv, len, rs, nullptr)) != GILA_OK) return s;
     P.tv = (int32_t)tv;
     P.rmax = (int32_t)rmax;
