@@ -90,7 +90,7 @@ NCU_TRAFFIC = {
     "chunglu250k_k3": {"bytes": 22770000000 + 95940000 + 52050000 + 256,
                        "kernels": "blocked_kernel + combine_kernel (one iteration)",
                        "profile": "profiles/launches_chunglu250k_k3.md",
-                       "sources_sha256": "af5dd63bc25fe85637205247caa701ded393c7731f2c6c72482eed20278b323e"},
+                       "sources_sha256": "d964e2dda58bc6193ea65451819df1da2a35d99127ba1e7465e223649a602e07"},
 }
 
 

@@ -9,19 +9,21 @@
 // that fall in tile j, in an order chosen so that the lanes of one gather
 // read distinct shared-memory banks; block starts are 16-byte aligned. An
 // entry is stored as a 16-bit id relative to the tile's first id (a tile
-// holds at most 32,767 positions), so the id stream, the only compulsory
+// holds at most 65,534 positions), so the id stream, the only compulsory
 // DRAM traffic of an iteration, is 2 bytes per entry instead of 4. One
 // CTA per block loads tile j and the block's row directory into shared
 // memory; each thread takes an equal, 8-aligned share of the block's
 // entries (stored so that a warp's 16-byte id loads of one step, eight ids
 // per lane, are contiguous), gathers positions from the tile and sums them
-// row by row on its own. A row wholly inside a share is stored by its thread; the parts of
-// rows cut by share bounds are added by a segmented scan across the warp,
-// and rows cut by warp bounds in warp order, then stored as the row's
-// partial for tile j. A second kernel adds each row's tile partials in tile
-// order, adds its attraction terms and applies the capped move. Every
-// partial has a fixed place and a fixed order of additions, so results do
-// not depend on scheduling.
+// row by row on its own. A row wholly inside a share is stored by its
+// thread; the parts of rows cut by share bounds are added by a segmented
+// scan across the warp, and rows cut by warp bounds by a second segmented
+// scan in warp order, then stored as the row's partial for tile j. A
+// second kernel adds each row's tile partials in tile order, adds its
+// attraction terms and applies the capped move. (Window mode, for banded
+// graphs: one window of positions per range instead of tiles, and the CTA
+// finishes its rows itself.) Every partial has a fixed place and a fixed
+// order of additions, so results do not depend on scheduling.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
