@@ -1,6 +1,7 @@
 """CPU checks of bench.py's host logic: the reference arm (the oracle on the
-host cores) at one rank and under a two-rank torchrun launch, and the
-max/sum-over-ranks reductions on a world-size-2 gloo process group."""
+host cores) at one rank and under a two-rank torchrun launch, the
+max/sum-over-ranks reductions on a world-size-2 gloo process group, and the
+roofline record's arithmetic."""
 import json
 import os
 import socket
@@ -96,3 +97,44 @@ def test_reductions_without_process_group():
     import bench
     assert bench.max_over_ranks(3.0, None, "cpu") == 3.0
     assert bench.sum_over_ranks(3.0, None, "cpu") == 3.0
+
+
+def test_roofline_record_arithmetic():
+    """The roofline record's compulsory bytes (2 B per k-hop entry on the
+    blocked path, 4 B on the plain path, 4 B per adjacency entry, 8 B offset
+    and two positions per vertex), the achieved bandwidth and fraction, and
+    the dominant kernel's own figures, on made-up sizes."""
+    import types
+    import bench
+    g = types.SimpleNamespace(n=1000)
+    nnzk, nnza = 50_000, 6_000
+    kern = {"name": "blocked_kernel", "ms": 2.0, "launches": 4}
+    r = bench.roofline_of(g, nnzk + nnza, nnzk, 8, 0.01, kern, 1000.0, "measured", None)
+    comp = 2 * nnzk + 4 * nnza + 8 * 1001 + 16 * 1000
+    assert r["alg_bytes_per_launch"] == comp
+    assert abs(r["achieved"] - comp / 1e-5 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 1000.0) < 1e-12
+    assert r["traffic"] is None
+    dk = r["dominant_kernel"]
+    assert dk["ms_per_launch"] == 0.5 and dk["compulsory_bytes"] == 2 * nnzk
+    assert abs(dk["frac"] - 2 * nnzk / 0.5e-3 / 1e9 / 1000.0) < 1e-12
+    plain = bench.roofline_of(g, nnzk + nnza, nnzk, 8, 0.01,
+                              {"name": "iteration_kernel", "ms": 1.0, "launches": 1},
+                              1000.0, "measured", None)
+    assert plain["alg_bytes_per_launch"] == comp + 2 * nnzk
+
+
+def test_traffic_record_follows_the_kernel_sources():
+    """A recorded ncu traffic figure is reported only while the kernel
+    sources hash to the value recorded with it."""
+    import bench
+    rec = dict(bench.NCU_TRAFFIC["chunglu250k_k3"])
+    saved = bench.NCU_TRAFFIC["chunglu250k_k3"]
+    try:
+        bench.NCU_TRAFFIC["chunglu250k_k3"] = dict(rec, sources_sha256=bench.kernel_sources_sha256())
+        assert bench.measured_traffic("chunglu250k_k3")["bytes"] == rec["bytes"]
+        bench.NCU_TRAFFIC["chunglu250k_k3"] = dict(rec, sources_sha256="0" * 64)
+        assert bench.measured_traffic("chunglu250k_k3") is None
+    finally:
+        bench.NCU_TRAFFIC["chunglu250k_k3"] = saved
+    assert bench.measured_traffic("no_such_workload") is None
