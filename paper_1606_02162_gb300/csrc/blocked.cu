@@ -1080,12 +1080,17 @@ cudaError_t launch_pair(gila_graph* g, const BlockedArgs& B, const CombineArgs& 
 // so the entries of row u in the tile are one contiguous run that starts
 // after the row's runs in earlier tiles (the plan's segment lengths), and
 // only the tile that holds u itself needs a binary search to drop the ids
-// up to u; a warp walks the run with
-// each term in double-float arithmetic (ff.cuh), sixteen terms per lane
+// up to u. The CTA takes its rows by batches: their runs are numbered by a
+// block scan and each warp takes an equal slice of the batch's entries (a
+// warp per row left the CTA's warps waiting on the one with a hub's row:
+// barrier stalls 5.1 per issue, 38% issue active on Chung-Lu n = 40,000).
+// Each term is in double-float arithmetic (ff.cuh), sixteen terms per lane
 // summed as a double-float, then added in FP64; the CTA's FP64 partial goes
 // to its own slot, and the partials are added in CTA order.
 constexpr int kMetThreads = 1024;
 constexpr int kMetWarps = kMetThreads / 32;
+constexpr int kMetBatch = 512;  // rows per batch (10.5 KB of shared memory beside the tile)
+constexpr int kMetSmemMax = kSmemCap - 12 * 1024;  // the tile's share of shared memory
 
 struct MetricArgs {
     const int64_t* krow;
@@ -1109,6 +1114,10 @@ __global__ void __launch_bounds__(kMetThreads, 1) khop_metric_kernel(const Metri
     __shared__ __align__(8) uint64_t tile_bar;
     __shared__ int tile_ok;
     __shared__ double s_part[kMetWarps];
+    __shared__ int s_wsum[kMetWarps];
+    __shared__ int s_pre[kMetBatch + 1];
+    __shared__ int64_t s_lo[kMetBatch];
+    __shared__ float2 s_q[kMetBatch];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int4 bd = A.bdesc[blockIdx.x];
     const int j = bd.z;
@@ -1137,54 +1146,107 @@ __global__ void __launch_bounds__(kMetThreads, 1) khop_metric_kernel(const Metri
     if (tile_ok) {
         mbar_wait(&tile_bar, 0, A.wait_ns);
         const Ff d2f = ff_from_double(A.d * A.d);
-        for (int64_t u = u0 + warp; u < u1; u += kMetWarps) {
-            if (tb + tn <= u + 1) continue;  // no id of this tile lies above u
-            // the row's entries in this tile: the whole row in window mode;
-            // in tile mode the segment after the row's segments in earlier
-            // tiles (their lengths, summed in order)
-            int64_t lo = A.krow[u], hi;
-            if (A.wbase) {
-                hi = A.krow[u + 1];
+        Ff s = {0.f, 0.f};
+        int cnt = 0;
+        // one pair {u, v}: d^2 / delta^q in double-float, sixteen terms of a
+        // lane summed as a double-float, then added to its FP64 sum
+        auto term = [&](float2 qu, uint32_t v) {
+            const float2 pv = tile[v - tb];
+            const Ff r2 = ff_dist2(qu.x, qu.y, pv.x, pv.y);
+            if (r2.hi >= 1e-30f && r2.hi <= 1e30f) {
+                s = ff_add(s, ff_mul(d2f, ff_rsqrt_pow(r2, A.q)));
             } else {
-                for (int jj = 0; jj < j; ++jj) lo += A.len[(int64_t)jj * A.n + u];
-                hi = lo + A.len[(int64_t)j * A.n + u];
-            }
-            if (tb <= u) {
-                // the tile holds u: keep the ids above it (binary search)
-                int64_t x = lo, y = hi;
-                while (x < y) {
-                    const int64_t mid = (x + y) >> 1;
-                    if (A.kcol[mid] <= (uint32_t)u) x = mid + 1; else y = mid;
+                const double dx = (double)qu.x - (double)pv.x;
+                const double dy = (double)qu.y - (double)pv.y;
+                const double dl = sqrt(dx * dx + dy * dy);
+                if (dl > 0.0) {
+                    double w = 1.0;
+                    for (int i = 0; i < A.q; ++i) w *= dl;
+                    part += A.d * A.d / w;
                 }
-                lo = x;
             }
-            if (lo >= hi) continue;
-            const float2 qu = A.pos[u];
-            Ff s = {0.f, 0.f};
-            int cnt = 0;
-            for (int64_t e = lo + lane; e < hi; e += 32) {
-                const float2 pv = tile[A.kcol[e] - tb];
-                const Ff r2 = ff_dist2(qu.x, qu.y, pv.x, pv.y);
-                if (r2.hi >= 1e-30f && r2.hi <= 1e30f) {
-                    s = ff_add(s, ff_mul(d2f, ff_rsqrt_pow(r2, A.q)));
+            if (++cnt == 16) {
+                part += (double)s.hi + (double)s.lo;
+                s = {0.f, 0.f};
+                cnt = 0;
+            }
+        };
+        // rows by batches of kMetBatch: thread t finds row r0 + t's run of
+        // ids above u in this tile; a block scan numbers the batch's entries;
+        // each warp then takes an equal slice of them (whatever the rows'
+        // lengths), lanes striding it and following the row boundaries
+        for (int64_t r0 = u0; r0 < u1; r0 += kMetBatch) {
+            const int64_t u = r0 + threadIdx.x;
+            int64_t lo = 0, hi = 0;
+            if (threadIdx.x < kMetBatch && u < u1 && tb + tn > u + 1) {
+                // the row's entries in this tile: the whole row in window
+                // mode; in tile mode the segment after the row's segments in
+                // earlier tiles (their lengths, summed in order)
+                lo = A.krow[u];
+                if (A.wbase) {
+                    hi = A.krow[u + 1];
                 } else {
-                    const double dx = (double)qu.x - (double)pv.x;
-                    const double dy = (double)qu.y - (double)pv.y;
-                    const double dl = sqrt(dx * dx + dy * dy);
-                    if (dl > 0.0) {
-                        double w = 1.0;
-                        for (int i = 0; i < A.q; ++i) w *= dl;
-                        part += A.d * A.d / w;
-                    }
+                    for (int jj = 0; jj < j; ++jj) lo += A.len[(int64_t)jj * A.n + u];
+                    hi = lo + A.len[(int64_t)j * A.n + u];
                 }
-                if (++cnt == 16) {
-                    part += (double)s.hi + (double)s.lo;
-                    s = {0.f, 0.f};
-                    cnt = 0;
+                if (tb <= u) {
+                    // the tile holds u: keep the ids above it (binary search)
+                    int64_t x = lo, y = hi;
+                    while (x < y) {
+                        const int64_t mid = (x + y) >> 1;
+                        if (A.kcol[mid] <= (uint32_t)u) x = mid + 1; else y = mid;
+                    }
+                    lo = x;
+                }
+                if (lo > hi) lo = hi;
+            }
+            const int len = (int)(hi - lo);
+            int incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int x = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += x;
+            }
+            if (lane == 31) s_wsum[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                const int x0 = s_wsum[lane];
+                int x = x0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, x, o);
+                    if (lane >= o) x += y;
+                }
+                s_wsum[lane] = x - x0;  // warps before this one
+                if (lane == 31) s_pre[kMetBatch] = x;
+            }
+            __syncthreads();
+            if (threadIdx.x < kMetBatch) {
+                s_pre[threadIdx.x] = s_wsum[warp] + incl - len;
+                s_lo[threadIdx.x] = lo;
+                float2 q = make_float2(0.f, 0.f);
+                if (u < u1) q = A.pos[u];
+                s_q[threadIdx.x] = q;
+            }
+            __syncthreads();
+            const int total = s_pre[kMetBatch];
+            const int beg = (int)((int64_t)total * warp / kMetWarps);
+            const int end = (int)((int64_t)total * (warp + 1) / kMetWarps);
+            if (beg + lane < end) {
+                // the row holding entry beg + lane: the last with s_pre <= it
+                int r = 0, hr = kMetBatch - 1;
+                while (r < hr) {
+                    const int mid = (r + hr + 1) >> 1;
+                    if (s_pre[mid] <= beg + lane) r = mid; else hr = mid - 1;
+                }
+                for (int i = beg + lane; i < end; i += 32) {
+                    while (s_pre[r + 1] <= i) ++r;
+                    term(s_q[r], A.kcol[s_lo[r] + (i - s_pre[r])]);
                 }
             }
-            part += (double)s.hi + (double)s.lo;
+            __syncthreads();  // the next batch reuses the arrays
         }
+        part += (double)s.hi + (double)s.lo;
     }
     // fixed-order block sum: lanes, then warps in order
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
@@ -1788,6 +1850,10 @@ gila_status blocked_khop_metric(gila_graph* g, const gila_params* prm, const voi
     const TilePlan& P = g->tplan[0];
     if (is_f64(prm->precision) || !P.ready || !P.use || g->n == 0 || g->wt64) return GILA_OK;
     if (((uintptr_t)pos & 15) != 0) return GILA_OK;
+    // the tile (or window) beside the kernel's own shared arrays; a larger
+    // window leaves the term to the generic reduction
+    const size_t smem = ((size_t)P.tv + 1) * sizeof(float2);
+    if (smem > (size_t)kMetSmemMax) return GILA_OK;
     const int grid = P.nb;
     gila_status s = ensure((void**)&g->red, &g->red_cap, sizeof(double) * ((size_t)grid + 8));
     if (s != GILA_OK) return s;
@@ -1806,13 +1872,12 @@ gila_status blocked_khop_metric(gila_graph* g, const gila_params* prm, const voi
     M.pos = reinterpret_cast<const float2*>(pos);
     M.partial = g->red;
     M.wait_ns = kWaitNs;
-    const size_t smem = ((size_t)P.tv + 1) * sizeof(float2);
     static std::atomic<uint64_t> configured{0};
     const uint64_t bit = 1ull << (g->device & 63);
     if (!(configured.load() & bit)) {
         GILA_CUDA(cudaFuncSetAttribute(khop_metric_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kSmemCap - 4096));
+                                       kMetSmemMax));
         configured.fetch_or(bit);
     }
     khop_metric_kernel<<<grid, kMetThreads, smem, g->stream>>>(M);
