@@ -1146,6 +1146,7 @@ __global__ void __launch_bounds__(kMetThreads, 1) khop_metric_kernel(const Metri
     if (tile_ok) {
         mbar_wait(&tile_bar, 0, A.wait_ns);
         const Ff d2f = ff_from_double(A.d * A.d);
+        const bool unit = A.d == 1.0 && A.q == 1;
         Ff s = {0.f, 0.f};
         int cnt = 0;
         // one pair {u, v}: d^2 / delta^q in double-float, sixteen terms of a
@@ -1154,7 +1155,9 @@ __global__ void __launch_bounds__(kMetThreads, 1) khop_metric_kernel(const Metri
             const float2 pv = tile[v - tb];
             const Ff r2 = ff_dist2(qu.x, qu.y, pv.x, pv.y);
             if (r2.hi >= 1e-30f && r2.hi <= 1e30f) {
-                s = ff_add(s, ff_mul(d2f, ff_rsqrt_pow(r2, A.q)));
+                // d = 1, q = 1 (the defaults): the products by 1 are exact
+                // and left out
+                s = ff_add(s, unit ? ff_rsqrt(r2) : ff_mul(d2f, ff_rsqrt_pow(r2, A.q)));
             } else {
                 const double dx = (double)qu.x - (double)pv.x;
                 const double dy = (double)qu.y - (double)pv.y;

@@ -73,13 +73,14 @@ __device__ __forceinline__ Ff ff_dist2(float ax, float ay, float bx, float by)
     return ff_fast_two_sum(s.hi, low);
 }
 
-// (1 / sqrt(r2))^q for r2 = hi + lo > 0 (q >= 0): the hardware's
-// approximate reciprocal square root y0 of hi (relative error below 2^-22)
-// refined by the series y = y0 (1 + e/2 + 3e^2/8) of y0 / sqrt(1 - e), with
-// e = 1 - r2 y0^2 formed exactly up to the rounding of its low parts (the
-// classical Newton step for the inverse square root carried one order
-// further); then q double-float products.
-__device__ __forceinline__ Ff ff_rsqrt_pow(Ff r2, int q)
+// 1 / sqrt(r2) for r2 = hi + lo > 0: the hardware's approximate reciprocal
+// square root y0 of hi (relative error below 2^-22) refined by the series
+// y = y0 (1 + e/2 + 3e^2/8) of y0 / sqrt(1 - e), with e = 1 - r2 y0^2 formed
+// exactly up to the rounding of its low parts (the classical Newton step for
+// the inverse square root carried one order further). ff_rsqrt_pow then
+// takes q double-float products, (1 / sqrt(r2))^q (q >= 0); for q = 1 its
+// product 1 * y equals y exactly (y is normalised).
+__device__ __forceinline__ Ff ff_rsqrt(Ff r2)
 {
     float y0;
     asm("rsqrt.approx.f32 %0, %1;" : "=f"(y0) : "f"(r2.hi));
@@ -88,7 +89,12 @@ __device__ __forceinline__ Ff ff_rsqrt_pow(Ff r2, int q)
     const float tl = __fadd_rn(t.lo, __fmaf_rn(r2.hi, y2.lo, __fmul_rn(r2.lo, y2.hi)));
     const float e = __fsub_rn(__fsub_rn(1.0f, t.hi), tl);  // 1 - t.hi is exact near 1
     const float corr = __fmul_rn(y0, __fmaf_rn(0.375f * e, e, 0.5f * e));
-    const Ff y = ff_fast_two_sum(y0, corr);
+    return ff_fast_two_sum(y0, corr);
+}
+
+__device__ __forceinline__ Ff ff_rsqrt_pow(Ff r2, int q)
+{
+    const Ff y = ff_rsqrt(r2);
     Ff r = {1.0f, 0.0f};
     for (int i = 0; i < q; ++i) r = ff_mul(r, y);
     return r;
