@@ -60,7 +60,11 @@ struct KhopScratch {
     int* qn = nullptr;          // 1
     uint32_t* bitmaps = nullptr;
     int32_t* lists = nullptr;
-    uint32_t* store = nullptr;  // tier-2 balls kept from count to fill (or null)
+    uint32_t* store = nullptr;  // tier-2 balls kept from count to fill (capacity kept
+    size_t store_cap = 0;       // across builds)
+    bool stored = false;        // the last count pass stored its balls
+    uint32_t* b2 = nullptr;     // radius-2 bitmaps of the k = 3 count (capacity kept)
+    size_t b2_cap = 0;
     bool keep_balls = true;     // allow the store (the server turns it off: it may wait
                                 // between count and fill, outside its memory accounting)
     int64_t bitmap_words = 0;   // per block

@@ -819,6 +819,7 @@ void free_khop(gila_graph* g)
     cudaFree(s.bitmaps);
     cudaFree(s.lists);
     cudaFree(s.store);
+    cudaFree(s.b2);
     s = KhopScratch();
     cudaFree(g->krow);
     cudaFree(g->kcol);
@@ -846,6 +847,7 @@ void release_khop_scratch(gila_graph* g)
     cudaFree(s.bitmaps);
     cudaFree(s.lists);
     cudaFree(s.store);
+    cudaFree(s.b2);
     const size_t cap = s.scratch_cap;
     const bool keep = s.keep_balls;
     s = KhopScratch();
@@ -951,24 +953,48 @@ gila_status build_khop_count_impl(gila_graph* g, int k)
             const size_t smem = (size_t)nwords * 4;
             // keep every tier-2 ball for the fill pass when they fit in
             // kStoreCap bytes of device memory (else the fill searches again)
+            // (the store and the radius-2 bitmaps below keep their capacity
+            // across builds: freeing 8 GB took 3-5 ms, and a layout loop
+            // rebuilds the lists every time)
             const size_t store_bytes = (size_t)nq * (size_t)nwords * 4;
-            cudaFree(S.store);
-            S.store = nullptr;
+            S.stored = false;
             if (S.keep_balls && store_bytes <= kStoreCap) {
-                void* p = nullptr;
-                if (cudaMalloc(&p, store_bytes) == cudaSuccess) S.store = (uint32_t*)p;
-                else cudaGetLastError();
+                if (S.store_cap < store_bytes) {
+                    cudaFree(S.store);
+                    S.store = nullptr;
+                    S.store_cap = 0;
+                    void* p = nullptr;
+                    if (cudaMalloc(&p, store_bytes) == cudaSuccess) {
+                        S.store = (uint32_t*)p;
+                        S.store_cap = store_bytes;
+                    } else {
+                        cudaGetLastError();
+                    }
+                }
+                S.stored = S.store != nullptr;
             }
+            uint32_t* const store = S.stored ? S.store : nullptr;
             // k = 3 with the balls stored and most sources in tier 2: the
             // balls as unions of the radius-2 balls (one n-bit bitmap per
-            // vertex, at most kB2Cap bytes, freed right after)
+            // vertex, at most kB2Cap bytes; given back if the fill cannot
+            // allocate its lists)
             uint32_t* b2 = nullptr;
             const size_t b2_bytes = (size_t)n * (size_t)nwords * 4;
-            if (k == 3 && S.store && nq >= n / 4 && b2_bytes <= kB2Cap &&
+            if (k == 3 && store && nq >= n / 4 && b2_bytes <= kB2Cap &&
                 dense_balls(g->row, n, st)) {
-                void* p = nullptr;
-                if (cudaMalloc(&p, b2_bytes) == cudaSuccess) b2 = (uint32_t*)p;
-                else cudaGetLastError();
+                if (S.b2_cap < b2_bytes) {
+                    cudaFree(S.b2);
+                    S.b2 = nullptr;
+                    S.b2_cap = 0;
+                    void* p = nullptr;
+                    if (cudaMalloc(&p, b2_bytes) == cudaSuccess) {
+                        S.b2 = (uint32_t*)p;
+                        S.b2_cap = b2_bytes;
+                    } else {
+                        cudaGetLastError();
+                    }
+                }
+                b2 = S.b2;
             }
             if (b2) {
                 GILA_CUDA(cudaFuncSetAttribute(ball2_kernel,
@@ -979,10 +1005,9 @@ gila_status build_khop_count_impl(gila_graph* g, int k)
                 count_launch();
                 ball3_or_kernel<<<(unsigned)std::min<int64_t>(nq, (int64_t)sms * 8), kT2Threads, 0,
                                   st>>>(S.queue, nq, g->row, g->col, nwords, b2, S.counts,
-                                        S.store);
+                                        store);
                 count_launch();
                 cudaError_t e = cudaStreamSynchronize(st);
-                cudaFree(b2);
                 if (e != cudaSuccess) return cuda_fail(e, "radius-3 balls");
             } else {
                 GILA_CUDA(cudaFuncSetAttribute(t2s_kernel<false>,
@@ -990,7 +1015,7 @@ gila_status build_khop_count_impl(gila_graph* g, int k)
                                                (int)smem));
                 t2s_kernel<false><<<t2_blocks, kT2Threads, smem, st>>>(
                     n, g->row, g->col, k, S.queue, nq, S.lists, nwords, S.counts, nullptr,
-                    nullptr, S.store);
+                    nullptr, store);
                 count_launch();
             }
         } else if (S.t2_blocks < t2_blocks || S.bitmap_words != nwords || !S.bitmaps) {
@@ -1041,7 +1066,16 @@ gila_status build_khop_fill(gila_graph* g, int k)
         g->cap_kcol = 0;
         // 4 spare entries: the blocked path's window mode reads kcol in
         // 16-byte steps that may end up to 12 bytes past the last row
-        if ((s = dev_alloc(&g->kcol, (size_t)nnz + 4)) != GILA_OK) return s;
+        s = dev_alloc(&g->kcol, (size_t)nnz + 4);
+        if (s != GILA_OK && S.b2) {
+            // the radius-2 bitmaps held for the next build give way to the lists
+            cudaFree(S.b2);
+            S.b2 = nullptr;
+            S.b2_cap = 0;
+            cudaGetLastError();
+            s = dev_alloc(&g->kcol, (size_t)nnz + 4);
+        }
+        if (s != GILA_OK) return s;
         g->cap_kcol = (size_t)nnz;
     }
     if (n > 0) {
@@ -1049,7 +1083,7 @@ gila_status build_khop_fill(gila_graph* g, int k)
                                                                       S.counts, g->krow, g->kcol);
         count_launch();
     }
-    if (nq > 0 && nwords <= kT2SmemWords && S.store) {
+    if (nq > 0 && nwords <= kT2SmemWords && S.stored) {
         t2_fill_stored_kernel<<<(unsigned)std::min<int64_t>(nq, (int64_t)sms * 8), kT2Threads, 0,
                                 st>>>(S.queue, nq, nwords, S.store, g->krow, g->kcol);
         count_launch();
@@ -1069,8 +1103,7 @@ gila_status build_khop_fill(gila_graph* g, int k)
     (void)sms;
     GILA_CUDA(cudaGetLastError());
     GILA_CUDA(cudaStreamSynchronize(st));
-    cudaFree(S.store);  // the stored balls served their one fill
-    S.store = nullptr;
+    S.stored = false;  // the stored balls served their one fill (the capacity stays)
     s = build_bins(g);
     if (s != GILA_OK) return s;
     g->nnz_khop = nnz;
