@@ -184,7 +184,11 @@ gila_status gila_graph_info(const gila_graph* g, int64_t* n, int64_t* nnz_adj,
  * breadth-first expansion to depth k, deduplicated, each list sorted by
  * ascending id, v itself excluded. Idempotent for the same k (a second call
  * returns at once); a different k rebuilds. *nnz_out (may be NULL) receives
- * the total list length. Synchronises the graph's stream. */
+ * the total list length. Synchronises the graph's stream. Memory: the lists
+ * (4 bytes per entry) belong to the graph; on graphs with large balls the
+ * build also keeps, for the graph's next build, the balls it stored between
+ * counting and filling and (k = 3) one n-bit bitmap per vertex, at most
+ * 16 GiB each, all freed with the graph. */
 gila_status gila_build_khop(gila_graph* g, int32_t k, int64_t* nnz_out);
 
 /* Drop the cached k-hop lists so the next build recomputes them (buffers
